@@ -1,0 +1,205 @@
+"""Oracle for the shifted pipelined CG hot path (arXiv 1706.05988).
+
+TEST INFRASTRUCTURE ONLY: a plain, slow, single-threaded FP64 CPU
+implementation used to check the CUDA path.  Only tests/,
+__graft_entry__.smoke() and bench.py's cpu_baseline / reference legs may
+import it.  It shares no code with the CUDA path; the only module both sides
+use is `synthetic` (seeded problem data, none of the solver's arithmetic).
+
+Contents
+  build()          compile pcg_oracle.c with gcc (-O2 -ffp-contract=off)
+  apply(P, x)      y = A x                         (operator of the model problem)
+  cg(...)          Algorithm 1, classic CG
+  pcg(...)         Algorithm 2, pipelined CG (written out without shift terms)
+  pcg_sh(...)      Algorithm 3, shifted pipelined CG
+  psi / select_sigma   Section 3.2, Eq. (functionpsi)        -> oracle.psi
+  exact rational CG / p-CG-sh for tiny systems               -> oracle.exact
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pcg_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lib = None
+
+OP_CSR, OP_STENCIL2D, OP_STENCIL3D = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (plain C, no vectorisation tricks)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                               "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Op(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n", ctypes.c_int64), ("nx", ctypes.c_int64), ("ny", ctypes.c_int64),
+                ("nz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p),
+                ("val", ctypes.c_void_p), ("diag", ctypes.c_void_p), ("ax", ctypes.c_void_p),
+                ("ay", ctypes.c_void_p), ("az", ctypes.c_void_p)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+
+class _State(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in ("x", "r", "u", "w", "z", "q", "s", "t", "p")]
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        vp, i32, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+        _lib.oracle_apply.argtypes = [vp, vp, vp]
+        _lib.oracle_cg.argtypes = [vp, vp, vp, vp, i32, f64, f64, i32, vp, vp, vp, vp, vp, vp]
+        _lib.oracle_pcg_sh.argtypes = [vp, vp, vp, vp, f64, i32, f64, f64, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        _lib.oracle_pcg.argtypes = [vp, vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp]
+        for f in (_lib.oracle_cg, _lib.oracle_pcg_sh, _lib.oracle_pcg):
+            f.restype = ctypes.c_int
+    return _lib
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data
+
+
+class _OpHolder:
+    """Keeps the numpy arrays referenced by the C struct alive."""
+
+    def __init__(self, P):
+        from synthetic import CSR32, STENCIL5_2D
+        self.keep = []
+
+        def c(a, dt):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=dt)
+            self.keep.append(a)
+            return a.ctypes.data
+
+        op = _Op()
+        if P.layout == CSR32:
+            op.kind, op.n = OP_CSR, P.n
+            op.row_ptr, op.col, op.val = c(P.row_ptr, np.int32), c(P.col, np.int32), c(P.val, np.float64)
+        else:
+            op.kind = OP_STENCIL2D if P.layout == STENCIL5_2D else OP_STENCIL3D
+            op.n, op.nx, op.ny, op.nz = P.n, P.nx, P.ny, P.nz
+            if not P.constant:
+                op.diag, op.ax, op.ay, op.az = (c(P.diag, np.float64), c(P.ax, np.float64),
+                                                c(P.ay, np.float64), c(P.az, np.float64))
+        self.op = op
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.op)
+
+
+@dataclass
+class Run:
+    """Output of one oracle solve.  Histories have length iters+1 (alpha/beta: iters)."""
+    x: np.ndarray
+    iters: int
+    status: int            # 0 maxit, 1 converged, 2 breakdown
+    alpha: np.ndarray
+    beta: np.ndarray
+    rec: np.ndarray        # ||r_i||
+    true: np.ndarray       # ||b - A x_i|| (NaN where not logged)
+    gap: np.ndarray        # ||(b - A x_i) - r_i||
+    gamma: Optional[np.ndarray] = None
+    delta: Optional[np.ndarray] = None
+    state: Optional[dict] = None
+
+
+def apply(P, x: np.ndarray) -> np.ndarray:
+    """y = A x with the oracle's own operator code."""
+    lib = _load()
+    h = _OpHolder(P)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty_like(x)
+    lib.oracle_apply(h.ref, x.ctypes.data, y.ctypes.data)
+    return y
+
+
+def _hist(maxit):
+    return [np.full(maxit + 1, np.nan) for _ in range(5)]
+
+
+def _minv(minv):
+    return None if minv is None else np.ascontiguousarray(minv, dtype=np.float64)
+
+
+def cg(P, b, x0=None, maxit=100, rtol=0.0, ttol=0.0, log_every=1, minv=None) -> Run:
+    """Algorithm 1 (classic preconditioned CG)."""
+    lib = _load()
+    h = _OpHolder(P)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(P.n) if x0 is None else np.array(x0, dtype=np.float64)
+    al, be, rec, tru, gap = _hist(maxit)
+    info = _Info()
+    mv = _minv(minv)
+    rc = lib.oracle_cg(h.ref, _ptr(mv), b.ctypes.data, x.ctypes.data, maxit, rtol, ttol, log_every,
+                       al.ctypes.data, be.ctypes.data, rec.ctypes.data, tru.ctypes.data, gap.ctypes.data,
+                       ctypes.byref(info))
+    if rc != 0:
+        raise MemoryError("oracle_cg allocation failed")
+    k = info.iters
+    return Run(x, k, info.status, al[:k], be[:k], rec[:k + 1], tru[:k + 1], gap[:k + 1])
+
+
+def pcg_sh(P, b, x0=None, sigma=0.0, maxit=100, rtol=0.0, ttol=0.0, log_every=1, minv=None,
+           want_state=False) -> Run:
+    """Algorithm 3 (shifted pipelined CG); sigma = 0 gives Algorithm 2's recurrences."""
+    lib = _load()
+    h = _OpHolder(P)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(P.n) if x0 is None else np.array(x0, dtype=np.float64)
+    al, be, rec, tru, gap = _hist(maxit)
+    ga = np.full(maxit + 1, np.nan)
+    de = np.full(maxit + 1, np.nan)
+    info = _Info()
+    st = None
+    stp = None
+    if want_state:
+        st = {k: np.zeros(P.n) for k in ("x", "r", "u", "w", "z", "q", "s", "t", "p")}
+        cs = _State(**{k: v.ctypes.data for k, v in st.items()})
+        stp = ctypes.byref(cs)
+    mv = _minv(minv)
+    rc = lib.oracle_pcg_sh(h.ref, _ptr(mv), b.ctypes.data, x.ctypes.data, float(sigma), maxit, rtol, ttol,
+                           log_every, al.ctypes.data, be.ctypes.data, rec.ctypes.data, tru.ctypes.data,
+                           gap.ctypes.data, ga.ctypes.data, de.ctypes.data, ctypes.byref(info), stp)
+    if rc != 0:
+        raise MemoryError("oracle_pcg_sh allocation failed")
+    k = info.iters
+    return Run(x, k, info.status, al[:k], be[:k], rec[:k + 1], tru[:k + 1], gap[:k + 1], ga[:k], de[:k], st)
+
+
+def pcg(P, b, x0=None, maxit=100, log_every=1, minv=None) -> Run:
+    """Algorithm 2 (pipelined CG), the separate unshifted code path."""
+    lib = _load()
+    h = _OpHolder(P)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(P.n) if x0 is None else np.array(x0, dtype=np.float64)
+    al, be, rec, tru, gap = _hist(maxit)
+    info = _Info()
+    mv = _minv(minv)
+    rc = lib.oracle_pcg(h.ref, _ptr(mv), b.ctypes.data, x.ctypes.data, maxit, log_every, al.ctypes.data,
+                        be.ctypes.data, rec.ctypes.data, tru.ctypes.data, gap.ctypes.data, ctypes.byref(info))
+    if rc != 0:
+        raise MemoryError("oracle_pcg allocation failed")
+    k = info.iters
+    return Run(x, k, info.status, al[:k], be[:k], rec[:k + 1], tru[:k + 1], gap[:k + 1])
