@@ -1,0 +1,299 @@
+"""Benchmark: shifted pipelined CG (arXiv 1706.05988, Algorithm 3) on the 256^3
+7-point Laplacian in FP64, through the C ABI of libpcg.
+
+One step = one solve of 1,000 p-CG-sh iterations (sigma = 6, b = A x*, x0 = 0).
+value = iterations/s over all ranks with the step's inputs resident in HBM;
+e2e = the same through pcg_solve with host buffers (pinned), H2D of b and D2H
+of x inside the timed region.  Each rank solves its own system (independent
+problems: no data-path collective).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "p-CG iters/s & HBM GB/s (256³ FP64)"
+UNIT = "iter/s"
+N_SIDE = 256
+ITERS_PER_STEP = 1000
+SIGMA = 6.0
+BYTES_PER_DOF = 96          # x, r, w, z, s, p: one FP64 read + one FP64 write each per iteration
+FP64_OPS_PER_DOF = 16       # 6 DADD + 1 DMUL + 9 DFMA per unknown per fused iteration
+FALLBACK_HBM_GBS = 6800.0
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_spcg_iter launch (ncu), keyed by the
+# SHA-256 of the kernel source it was measured on; a changed kernel reports null.
+NCU_TRAFFIC = {}
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("pcg_kernels.cuh", "pcg_kernels_3d.cu"):
+        with open(os.path.join(ROOT, "paper_1706_05988_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def workload_config(n: int) -> dict:
+    return {"workload": f"3D 7-point constant-coefficient Dirichlet Laplacian on {N_SIDE}^3 (n={n:,}), matrix-free "
+                        f"stencil; shifted p-CG (Alg. 3) sigma={SIGMA}, {ITERS_PER_STEP} iterations per step; "
+                        "b = A x*, x* ~ U[-1,1] (seed 0), x0 = 0",
+            "n": n, "iterations_per_step": ITERS_PER_STEP, "sigma": SIGMA,
+            "l2": "inputs larger than L2 (six 128 MiB FP64 vectors streamed per iteration)"}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), float(f[3]), f[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+def dist_setup(gpus: int):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v: float) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_rate(P, b, iters: int) -> tuple[float, float]:
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.pcg_sh(P, b, sigma=SIGMA, maxit=iters, log_every=0)
+    dt = time.perf_counter() - t0
+    return iters / dt, dt
+
+
+def run_reference(args):
+    """The oracle, as it stands, on the host: bounded samples of the same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import synthetic as S
+    P, b, _ = S.poisson3d_manufactured(N_SIDE)
+    k = args.ref_iters
+    for _ in range(args.warmup):
+        cpu_oracle_rate(P, b, k)
+    times = []
+    for _ in range(args.steps):
+        times.append(cpu_oracle_rate(P, b, k)[1])
+    total = sum(times)
+    value = args.steps * k / total
+    sample = (f"{k} iterations of the {N_SIDE}^3 shifted p-CG solve per step (setup of r0, w0 included), "
+              "single-threaded FP64 oracle")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(P.n),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    import paper_1706_05988_gb300 as pkg
+    from paper_1706_05988_gb300 import pcg as C
+    import synthetic as S
+
+    pkg.build.build()
+    P, b_host, _ = S.poisson3d_manufactured(N_SIDE)
+    n = P.n
+    solver = pkg.Solver(P, flags=C.PCG_PROFILE)
+    stream = torch.cuda.current_stream()
+    C.pcg_set_stream(solver.ctx, stream.cuda_stream)
+    b_dev = torch.from_numpy(b_host).cuda()
+    x_dev = torch.empty(n, dtype=torch.float64, device="cuda")
+
+    def step_device():
+        s = C.pcg_solve_device(solver.ctx, b_dev, None, C.PCG_SPCG, SIGMA, 0.0, ITERS_PER_STEP, C.PCG_FP64, x_dev,
+                               None)
+        if s != C.PCG_ENOTCONV:
+            raise C.PcgError(s, C.pcg_last_error(solver.ctx))
+
+    for _ in range(args.warmup):
+        step_device()
+    torch.cuda.synchronize()
+    C.pcg_kernel_stats_reset(solver.ctx)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step_device()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    ms = ev0.elapsed_time(ev1)
+    launches, iter_launches, iter_ms = C.pcg_kernel_stats(solver.ctx)
+    ms_max = max_over_ranks(world, ms)
+    total_iters = world * args.steps * ITERS_PER_STEP
+    value = total_iters / (ms_max / 1e3)
+
+    # roofline of the dominant kernel (the fused iteration), from its own CUDA events
+    avg_launch_s = iter_ms / max(iter_launches, 1) / 1e3
+    alg_bytes = BYTES_PER_DOF * n
+    achieved = alg_bytes / avg_launch_s / 1e9
+    peak, peak_kind = measured_peaks()
+    sha = kernel_source_sha()
+    traffic = NCU_TRAFFIC.get(sha)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_source": peak_kind, "kernel": "k_spcg_iter (fused SpMV + recurrences + dots)",
+                "kernel_avg_ms": avg_launch_s * 1e3, "algorithmic_bytes_per_launch": alg_bytes,
+                "kernel_source_sha": sha}
+    fp64_tflops = FP64_OPS_PER_DOF * n / avg_launch_s / 1e12
+
+    # end to end: host buffers through pcg_solve (pinned), copies inside the timed region
+    b_pin = torch.from_numpy(b_host).pin_memory()
+    x_pin = torch.empty(n, dtype=torch.float64).pin_memory()
+    res = C.pcg_result()
+
+    def step_host():
+        s = C.pcg_solve(solver.ctx, b_pin.data_ptr(), None, C.PCG_SPCG, SIGMA, 0.0, ITERS_PER_STEP, C.PCG_FP64,
+                        x_pin.data_ptr(), res)
+        if s != C.PCG_ENOTCONV:
+            raise C.PcgError(s, C.pcg_last_error(solver.ctx))
+
+    step_host()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_host()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(world, time.perf_counter() - t0)
+    e2e = {"value": total_iters / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
+           "final_true_relres": res.final_true_relres}
+
+    # the oracle on this host, bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, dt = cpu_oracle_rate(P, b_host, args.ref_iters)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{args.ref_iters} iterations of the same {N_SIDE}^3 shifted p-CG solve, single-threaded "
+                         f"FP64 oracle ({dt:.1f} s)"}
+
+    solver.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": workload_config(n),
+                "hbm_gbs_effective": alg_bytes * ITERS_PER_STEP * args.steps * world / (ms_max / 1e3) / 1e9 / world,
+                "roofline": roofline,
+                "fp64_pipe": {"achieved_tflops": fp64_tflops, "ops_per_dof": FP64_OPS_PER_DOF,
+                              "note": "FP64 instructions per unknown per iteration (FMA counted once)"},
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--ref-iters", type=int, default=10, help="oracle iterations per sample")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timing")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    return run_reference(args) if args.impl == "reference" else run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

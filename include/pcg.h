@@ -1,0 +1,164 @@
+/*
+ * pcg.h -- C ABI of libpcg: shifted pipelined Conjugate Gradients on one GB300.
+ *
+ * Method: S. Cools, W. Vanroose, "Numerically stable variants of the
+ * communication-hiding pipelined Conjugate Gradients algorithm for the
+ * parallel solution of large scale symmetric linear systems", arXiv 1706.05988.
+ *   PCG_CG    Algorithm 1 (classic CG), Section 1.
+ *   PCG_PCG   Algorithm 2 (pipelined CG), Section 2.1 -- run as Algorithm 3
+ *             with sigma = 0, which is the same recurrence (end of Section 2.2).
+ *   PCG_SPCG  Algorithm 3 (shifted pipelined CG), Section 2.2.
+ * The problem is A x = b with A real symmetric positive definite (Section 2.1);
+ * M^{-1} = I (the paper's Poisson experiments are unpreconditioned, Table 1).
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns a pcg_status and never aborts the process.
+ *   - Vectors are contiguous binary64 arrays of length n.  Stencil unknowns
+ *     are ordered x fastest, then y, then z.
+ *   - Host pointers unless the entry point says "device"; device pointers
+ *     must come from the CUDA device that was current when the context was
+ *     created and stay owned by the caller.
+ *   - All output buffers are caller-owned.  NULL history pointers are allowed.
+ *   - A context is not thread-safe: serialise calls on one context.  Distinct
+ *     contexts are independent.
+ *   - All GPU work of a context runs on one CUDA stream (its own, or the one
+ *     given to pcg_set_stream); solve calls return after that work finished.
+ */
+#ifndef PCG_H
+#define PCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pcg_ctx pcg_ctx;
+
+typedef enum {
+  PCG_OK = 0,
+  PCG_EINVAL = 1,      /* bad argument; nothing was changed                        */
+  PCG_ENOMEM = 2,      /* device or host allocation failed                          */
+  PCG_ECUDA = 3,       /* a CUDA call failed; see pcg_last_error                    */
+  PCG_EBREAKDOWN = 4,  /* delta <= 0, or a non-finite / non-positive 1/alpha: the
+                          iteration stopped; x and histories hold the last iterate */
+  PCG_ENOTCONV = 5,    /* maxit reached before tol; x and histories are valid       */
+  PCG_ETIMEOUT = 6,    /* a bounded device wait gave up                            */
+  PCG_PENDING = 7,
+  PCG_ENOTIMPL = 8
+} pcg_status;
+
+typedef enum { PCG_STENCIL5_2D = 0, PCG_STENCIL7_3D = 1, PCG_CSR32 = 2 } pcg_layout;
+typedef enum { PCG_CG = 0, PCG_PCG = 1, PCG_SPCG = 2 } pcg_method;
+typedef enum { PCG_FP64 = 0, PCG_MIXED_IR = 1 } pcg_precision;
+
+/* pcg_create flags */
+#define PCG_DEVICE_PTRS 0x1u   /* every array in pcg_matrix is a device pointer          */
+#define PCG_PROFILE 0x2u       /* time every launch of the fused iteration kernel with
+                                  CUDA events (read back with pcg_kernel_stats)          */
+
+/*
+ * The operator A.
+ *  PCG_STENCIL5_2D / PCG_STENCIL7_3D: matrix-free cell-centred operator on an
+ *    nx x ny (x nz) grid with Dirichlet boundary.  With diag == NULL it is the
+ *    unscaled Laplacian (4 resp. 6 on the diagonal, -1 to each grid neighbour),
+ *    the operator of the paper's lapl200 and Poisson experiments (Section 5).
+ *    Otherwise (variable coefficients) row c is
+ *        diag[c] x_c - ax[c] x_{c-1} - ax[c+1] x_{c+1} - ay[c] x_{c-nx}
+ *                    - ay[c+nx] x_{c+nx} - az[c] x_{c-nx*ny} - az[c+nx*ny] x_{c+nx*ny}
+ *    where ax/ay/az[c] is the coefficient of the face between c and its lower
+ *    neighbour and must be 0 where that neighbour is outside the grid.  nz = 1
+ *    and az unused in 2D.  n is ignored (n = nx*ny*nz).
+ *  PCG_CSR32: n x n matrix, nnz entries, row_ptr[n+1] / col[nnz] int32, val[nnz];
+ *    columns need not be sorted; every index must lie in [0, n).
+ * The caller must pass an SPD matrix; symmetry is not checked.
+ */
+typedef struct {
+  int32_t layout;
+  int64_t nx, ny, nz;
+  const double *diag, *ax, *ay, *az;
+  int64_t n, nnz;
+  const int32_t *row_ptr, *col;
+  const double *val;
+} pcg_matrix;
+
+/*
+ * Solve report.  History arrays (caller-owned, host, length maxit+1, may be
+ * NULL) follow the index convention of Algorithm 3: alpha_hist[i], beta_hist[i]
+ * are the scalars of iteration i (beta_hist[0] = 0), for i < iters;
+ * rec_hist[i] = ||r_i||_2, the recursive residual, for i <= iters;
+ * true_hist[i] = ||b - A x_i||_2 for i a multiple of true_every and i = iters
+ * (other entries NaN; true_every <= 0 logs only i = iters).
+ * gap_hist[i] = ||(b - A x_i) - r_i||_2, the residual gap f_i of Section 3.1,
+ * logged with true_hist.
+ */
+typedef struct {
+  int32_t iters;                /* out: iterations performed                       */
+  int32_t status;               /* out: same value as the return code              */
+  double final_true_relres;     /* out: ||b - A x|| / ||b|| at exit                */
+  double final_rec_relres;      /* out: ||r_iters|| / ||b||                        */
+  double *rec_hist, *true_hist, *gap_hist, *alpha_hist, *beta_hist;
+  int32_t true_every;           /* in                                              */
+} pcg_result;
+
+/* Create a context for operator A: copies A to the device (or, with
+ * PCG_DEVICE_PTRS, references the caller's device arrays, which must outlive
+ * the context).  Device work vectors are allocated by the first solve.
+ * Errors: PCG_EINVAL for a NULL/inconsistent description (non-positive sizes,
+ * nx*ny*nz or nnz beyond int32 indexing, missing arrays); PCG_ENOMEM; PCG_ECUDA. */
+pcg_status pcg_create(const pcg_matrix *A, uint32_t flags, pcg_ctx **out);
+
+/* Release every device and host resource of the context.  NULL is a no-op. */
+void pcg_destroy(pcg_ctx *ctx);
+
+/* Last error message of the context ("" if none); valid until the next call. */
+const char *pcg_last_error(const pcg_ctx *ctx);
+
+/* Run all later GPU work of this context on `stream` (a cudaStream_t of the
+ * context's device; NULL = the context's own stream). */
+pcg_status pcg_set_stream(pcg_ctx *ctx, void *stream);
+
+/* Solve A x = b.  b, x0 (NULL = zero) and x_out are host arrays of length n.
+ * method: pcg_method; sigma: the shift of Algorithm 3 (must be >= 0; ignored
+ * by PCG_CG and forced to 0 by PCG_PCG).  tol: stop once the recursive
+ * residual satisfies ||r_i|| <= tol ||b|| (the scaled criterion of the
+ * paper's Section 5.2); tol = 0 runs exactly maxit iterations.  maxit >= 0.
+ * precision must be PCG_FP64 (PCG_MIXED_IR is not implemented: PCG_ENOTIMPL).
+ * Returns PCG_OK on convergence, PCG_ENOTCONV at maxit (always when tol = 0),
+ * PCG_EBREAKDOWN; res may be NULL.  x_out is written in every non-error case. */
+pcg_status pcg_solve(pcg_ctx *ctx, const double *b, const double *x0, int32_t method, double sigma, double tol,
+                     int32_t maxit, int32_t precision, double *x_out, pcg_result *res);
+
+/* pcg_solve with b, x0 (NULL = zero) and x_out given as device pointers. */
+pcg_status pcg_solve_device(pcg_ctx *ctx, const double *b, const double *x0, int32_t method, double sigma,
+                            double tol, int32_t maxit, int32_t precision, double *x_out, pcg_result *res);
+
+/* Shift selection (Section 3.2, Eq. (functionpsi); Section 5.1): runs
+ * Algorithm 2 (sigma = 0) for `iters` iterations on (A, b) -- b a host array --
+ * and evaluates psi_i(sigma) = max_{1<=j<=i} ||P_i(sigma) ... P_j(sigma)||_2 on
+ * the device for every shift of grid[ngrid] (host), with i the last iteration
+ * whose alpha/beta exist.  sigma_out receives the smallest grid shift whose psi
+ * is within a factor 2 of the grid minimum; psi_out (host, ngrid, may be NULL)
+ * the psi values.  Errors: PCG_EINVAL (iters < 2, ngrid < 1, a negative shift). */
+pcg_status pcg_select_sigma(pcg_ctx *ctx, const double *b, int32_t iters, const double *grid, int32_t ngrid,
+                            double *sigma_out, double *psi_out);
+
+/* psi_i(sigma) for given coefficient histories alpha[0..i], beta[0..i] (host)
+ * and shifts grid[ngrid] (host), evaluated on the device; psi_out[ngrid] host. */
+pcg_status pcg_psi(pcg_ctx *ctx, const double *alpha, const double *beta, int32_t i, const double *grid,
+                   int32_t ngrid, double *psi_out);
+
+/* Kernel accounting of the context since creation (or the last reset):
+ * total launches of every kernel of this library, and -- with PCG_PROFILE --
+ * the launches and summed CUDA-event time (ms) of the fused iteration kernel. */
+pcg_status pcg_kernel_stats(pcg_ctx *ctx, int64_t *launches_total, int64_t *iter_launches, double *iter_ms);
+pcg_status pcg_kernel_stats_reset(pcg_ctx *ctx);
+
+/* Version string of the library build. */
+const char *pcg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PCG_H */

@@ -1,0 +1,500 @@
+// C ABI of libpcg (declared in include/pcg.h): context management, argument
+// checking, device memory, and the launch sequence of one solve.  Every
+// arithmetic step of a solve runs in the kernels of pcg_kernels.cuh.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/pcg.h"
+#include "pcg_internal.h"
+
+using namespace pcgk;
+
+struct pcg_ctx {
+  int device = 0;
+  uint32_t flags = 0;
+  OpDesc op{};
+  int64_t n = 0, nnz = 0;
+  std::vector<void*> owned;             // device allocations owned by the context
+  cudaStream_t own_stream = nullptr, stream = nullptr;
+  // work vectors: x, r, w0, w1, z, s, p, b (internal copy) in one allocation
+  double* vec_base = nullptr;
+  size_t vec_stride = 0;                // doubles between consecutive vectors
+  Vecs v{};
+  double* d_b = nullptr;
+  State* d_state = nullptr;
+  State* h_state = nullptr;             // pinned mirror
+  double* d_hist = nullptr;
+  int hist_cap = 0;
+  Hist h{};
+  double* d_partials = nullptr;
+  double* d_small = nullptr;            // psi workspace
+  int small_cap = 0;
+  int grid[K_NKINDS] = {0};
+  int64_t launches = 0, iter_launches = 0;
+  double iter_ms = 0.0;
+  std::vector<cudaEvent_t> ev;          // PCG_PROFILE: pairs around iteration launches
+  std::string err;
+};
+
+namespace {
+
+const char* kVersion = "libpcg 0.1 (sm_103a, FP64 shifted pipelined CG)";
+
+pcg_status fail(pcg_ctx* c, pcg_status s, const char* msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+#define CUDA_TRY(ctx, call)                                                                    \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
+      (ctx)->err = std::string(#call) + ": " + cudaGetErrorString(e_);                          \
+      return e_ == cudaErrorMemoryAllocation ? PCG_ENOMEM : PCG_ECUDA;                         \
+    }                                                                                          \
+  } while (0)
+
+pcg_status dev_alloc(pcg_ctx* c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    c->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? PCG_ENOMEM : PCG_ECUDA;
+  }
+  c->owned.push_back(*p);
+  return PCG_OK;
+}
+
+// Copies a matrix array to the device (or references it with PCG_DEVICE_PTRS).
+template <class T>
+pcg_status place(pcg_ctx* c, const T* src, size_t count, const T** dst) {
+  if (c->flags & PCG_DEVICE_PTRS) {
+    *dst = src;
+    return PCG_OK;
+  }
+  void* p;
+  pcg_status s = dev_alloc(c, &p, count * sizeof(T));
+  if (s != PCG_OK) return s;
+  CUDA_TRY(c, cudaMemcpy(p, src, count * sizeof(T), cudaMemcpyHostToDevice));
+  *dst = (const T*)p;
+  return PCG_OK;
+}
+
+pcg_status ensure_vectors(pcg_ctx* c) {
+  if (c->vec_base) return PCG_OK;
+  const size_t stride = ((size_t)c->n + 31) & ~(size_t)31;   // 256-byte aligned vectors
+  void* p;
+  pcg_status s = dev_alloc(c, &p, 8 * stride * sizeof(double));
+  if (s != PCG_OK) return s;
+  c->vec_base = (double*)p;
+  c->vec_stride = stride;
+  double* b = c->vec_base;
+  c->v.x = b + 0 * stride;
+  c->v.r = b + 1 * stride;
+  c->v.w0 = b + 2 * stride;
+  c->v.w1 = b + 3 * stride;
+  c->v.z = b + 4 * stride;
+  c->v.s = b + 5 * stride;
+  c->v.p = b + 6 * stride;
+  c->d_b = b + 7 * stride;
+  c->v.b = c->d_b;
+  return PCG_OK;
+}
+
+pcg_status ensure_hist(pcg_ctx* c, int entries) {
+  if (c->hist_cap >= entries) return PCG_OK;
+  if (c->d_hist) {
+    cudaFree(c->d_hist);
+    c->owned.erase(std::find(c->owned.begin(), c->owned.end(), (void*)c->d_hist));
+    c->d_hist = nullptr;
+    c->hist_cap = 0;
+  }
+  const int cap = std::max(entries, 1024);
+  void* p;
+  pcg_status s = dev_alloc(c, &p, 7 * (size_t)cap * sizeof(double));
+  if (s != PCG_OK) return s;
+  c->d_hist = (double*)p;
+  c->hist_cap = cap;
+  double* b = c->d_hist;
+  c->h.alpha = b;
+  c->h.beta = b + cap;
+  c->h.gamma = b + 2 * cap;
+  c->h.delta = b + 3 * cap;
+  c->h.rec = b + 4 * cap;
+  c->h.tru = b + 5 * cap;
+  c->h.gap = b + 6 * cap;
+  return PCG_OK;
+}
+
+pcg_status ensure_events(pcg_ctx* c, size_t pairs) {
+  while (c->ev.size() < 2 * pairs) {
+    cudaEvent_t e;
+    CUDA_TRY(c, cudaEventCreate(&e));
+    c->ev.push_back(e);
+  }
+  return PCG_OK;
+}
+
+Launch launch_of(pcg_ctx* c, int kind) { return Launch{c->grid[kind], kBlockThreads, c->stream}; }
+
+}  // namespace
+
+extern "C" {
+
+const char* pcg_version(void) { return kVersion; }
+
+const char* pcg_last_error(const pcg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+pcg_status pcg_create(const pcg_matrix* A, uint32_t flags, pcg_ctx** out) {
+  if (!out) return PCG_EINVAL;
+  *out = nullptr;
+  if (!A) return PCG_EINVAL;
+  if (flags & ~(PCG_DEVICE_PTRS | PCG_PROFILE)) return PCG_EINVAL;
+  OpDesc op{};
+  op.layout = A->layout;
+  int64_t n = 0, nnz = 0;
+  if (A->layout == PCG_STENCIL5_2D || A->layout == PCG_STENCIL7_3D) {
+    const int64_t nz = A->layout == PCG_STENCIL7_3D ? A->nz : 1;
+    if (A->nx < 1 || A->ny < 1 || nz < 1) return PCG_EINVAL;
+    if (A->nx > INT32_MAX || A->ny > INT32_MAX || nz > INT32_MAX) return PCG_EINVAL;
+    n = A->nx * A->ny * nz;
+    if (n > (int64_t)INT32_MAX - 64) return PCG_EINVAL;
+    const bool var = A->diag != nullptr;
+    if (var && (!A->ax || !A->ay || (A->layout == PCG_STENCIL7_3D && !A->az))) return PCG_EINVAL;
+    if (!var && (A->ax || A->ay || A->az)) return PCG_EINVAL;
+    op.nx = (int)A->nx;
+    op.ny = (int)A->ny;
+    op.nz = (int)nz;
+  } else if (A->layout == PCG_CSR32) {
+    if (A->n < 1 || A->n > (int64_t)INT32_MAX - 64 || A->nnz < 0 || A->nnz > INT32_MAX) return PCG_EINVAL;
+    if (!A->row_ptr || (A->nnz > 0 && (!A->col || !A->val))) return PCG_EINVAL;
+    n = A->n;
+    nnz = A->nnz;
+    if (!(flags & PCG_DEVICE_PTRS)) {   // host arrays can be validated here
+      if (A->row_ptr[0] != 0 || A->row_ptr[n] != nnz) return PCG_EINVAL;
+      for (int64_t i = 0; i < n; ++i)
+        if (A->row_ptr[i + 1] < A->row_ptr[i]) return PCG_EINVAL;
+      for (int64_t k = 0; k < nnz; ++k)
+        if (A->col[k] < 0 || A->col[k] >= n) return PCG_EINVAL;
+    }
+  } else {
+    return PCG_EINVAL;
+  }
+  op.n = (int)n;
+
+  pcg_ctx* c = new (std::nothrow) pcg_ctx();
+  if (!c) return PCG_ENOMEM;
+  c->flags = flags;
+  c->n = n;
+  c->nnz = nnz;
+  pcg_status s = PCG_OK;
+  auto bail = [&](pcg_status st) {
+    pcg_destroy(c);
+    return st;
+  };
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(PCG_ECUDA);
+  }
+  if (A->layout == PCG_CSR32) {
+    if ((s = place<int32_t>(c, A->row_ptr, n + 1, &op.row_ptr)) != PCG_OK) return bail(s);
+    if ((s = place<int32_t>(c, A->col, nnz, &op.col)) != PCG_OK) return bail(s);
+    if ((s = place<double>(c, A->val, nnz, &op.val)) != PCG_OK) return bail(s);
+  } else if (A->diag) {
+    if ((s = place<double>(c, A->diag, n, &op.diag)) != PCG_OK) return bail(s);
+    if ((s = place<double>(c, A->ax, n, &op.ax)) != PCG_OK) return bail(s);
+    if ((s = place<double>(c, A->ay, n, &op.ay)) != PCG_OK) return bail(s);
+    if (A->layout == PCG_STENCIL7_3D && (s = place<double>(c, A->az, n, &op.az)) != PCG_OK) return bail(s);
+  }
+  c->op = op;
+  if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(PCG_ECUDA);
+  }
+  c->stream = c->own_stream;
+  void* p;
+  if ((s = dev_alloc(c, &p, sizeof(State))) != PCG_OK) return bail(s);
+  c->d_state = (State*)p;
+  if ((s = dev_alloc(c, &p, (size_t)kMaxPartialBlocks * kPartialsPerBlock * sizeof(double))) != PCG_OK) return bail(s);
+  c->d_partials = (double*)p;
+  if (cudaMallocHost(&p, sizeof(State)) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(PCG_ENOMEM);
+  }
+  c->h_state = (State*)p;
+  for (int k = 0; k < K_NKINDS; ++k) {
+    c->grid[k] = grid_for(c->op, k, kBlockThreads);
+    if (c->grid[k] <= 0) {
+      cudaGetLastError();
+      return bail(fail(c, PCG_ECUDA, "could not size the kernel grids"));
+    }
+  }
+  *out = c;
+  return PCG_OK;
+}
+
+void pcg_destroy(pcg_ctx* c) {
+  if (!c) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(c->device);
+  if (c->own_stream) cudaStreamSynchronize(c->own_stream);
+  for (void* p : c->owned) cudaFree(p);
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  if (c->h_state) cudaFreeHost(c->h_state);
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  cudaGetLastError();
+  cudaSetDevice(prev);
+  delete c;
+}
+
+pcg_status pcg_set_stream(pcg_ctx* c, void* stream) {
+  if (!c) return PCG_EINVAL;
+  c->stream = stream ? (cudaStream_t)stream : c->own_stream;
+  return PCG_OK;
+}
+
+pcg_status pcg_kernel_stats(pcg_ctx* c, int64_t* launches_total, int64_t* iter_launches, double* iter_ms) {
+  if (!c) return PCG_EINVAL;
+  if (launches_total) *launches_total = c->launches;
+  if (iter_launches) *iter_launches = c->iter_launches;
+  if (iter_ms) *iter_ms = c->iter_ms;
+  return PCG_OK;
+}
+
+pcg_status pcg_kernel_stats_reset(pcg_ctx* c) {
+  if (!c) return PCG_EINVAL;
+  c->launches = c->iter_launches = 0;
+  c->iter_ms = 0.0;
+  return PCG_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// The launch sequence of one solve.  b (device, 16-byte aligned or the
+// context's copy), x0 already placed in v.x when has_x0.
+pcg_status run_solve(pcg_ctx* c, bool has_x0, int method, double sigma, double tol, int maxit, int true_every,
+                     int* iters_out, int* status_out) {
+  const bool profile = (c->flags & PCG_PROFILE) != 0;
+  State st{};
+  st.iter = 0;
+  st.status = ST_RUNNING;
+  st.maxit = maxit;
+  st.sigma = method == PCG_SPCG ? sigma : 0.0;
+  st.tol_abs = tol;   // relative until the residual kernel scales it by ||b||
+  *c->h_state = st;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_state, c->h_state, sizeof(State), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_hist, 0xff, 7 * (size_t)c->hist_cap * sizeof(double), c->stream));  // NaN
+  if (profile) {
+    pcg_status s = ensure_events(c, (size_t)maxit);
+    if (s != PCG_OK) return s;
+  }
+  auto L = [&](int kind) { return launch_of(c, kind); };
+  CUDA_TRY(c, launch_residual(c->op, L(K_RESIDUAL), c->v.b, has_x0 ? c->v.x : nullptr, c->v.x, c->v.r, c->d_state,
+                              c->d_partials));
+  ++c->launches;
+  const bool cg = method == PCG_CG;
+  if (cg) {
+    CUDA_TRY(c, launch_cg_p0(c->op, L(K_CG_P0), c->v, c->d_state, c->h, c->d_partials));
+  } else {
+    CUDA_TRY(c, launch_spcg_w0(c->op, L(K_SPCG_W0), c->v, c->d_state, c->h, c->d_partials));
+  }
+  ++c->launches;
+  if (true_every > 0) {
+    CUDA_TRY(c, launch_true_res(c->op, L(K_TRUE_RES), c->v, c->d_state, c->h, c->d_partials));
+    ++c->launches;
+  }
+  int done = 0;            // iteration launches issued
+  int prof_pairs = 0;
+  int chunk = 16;
+  while (done < maxit) {
+    const int todo = tol > 0.0 ? std::min(chunk, maxit - done) : maxit - done;
+    for (int k = 0; k < todo; ++k) {
+      if (cg) {
+        CUDA_TRY(c, launch_cg_spmv(c->op, L(K_CG_SPMV), c->v, c->d_state, c->h, c->d_partials));
+        CUDA_TRY(c, launch_cg_update(c->op, L(K_CG_UPDATE), c->v, c->d_state, c->h, c->d_partials));
+        CUDA_TRY(c, launch_cg_p(c->op, L(K_CG_P), c->v, c->d_state, c->h));
+        c->launches += 3;
+      } else {
+        if (profile) CUDA_TRY(c, cudaEventRecord(c->ev[2 * prof_pairs], c->stream));
+        CUDA_TRY(c, launch_spcg_iter(c->op, L(K_SPCG_ITER), c->v, c->d_state, c->h, c->d_partials));
+        if (profile) CUDA_TRY(c, cudaEventRecord(c->ev[2 * prof_pairs + 1], c->stream));
+        prof_pairs += profile;
+        ++c->launches;
+        ++c->iter_launches;
+      }
+      ++done;
+      if (true_every > 0 && done % true_every == 0) {
+        CUDA_TRY(c, launch_true_res(c->op, L(K_TRUE_RES), c->v, c->d_state, c->h, c->d_partials));
+        ++c->launches;
+      }
+    }
+    if (tol > 0.0 && done < maxit) {
+      CUDA_TRY(c, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(State), cudaMemcpyDeviceToHost, c->stream));
+      CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+      if (c->h_state->status != ST_RUNNING) break;
+      chunk = std::min(chunk * 2, 256);
+    }
+  }
+  // true residual at the final iterate
+  CUDA_TRY(c, launch_true_res(c->op, L(K_TRUE_RES), c->v, c->d_state, c->h, c->d_partials));
+  ++c->launches;
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(State), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (profile) {
+    for (int k = 0; k < prof_pairs; ++k) {
+      float ms = 0.f;
+      CUDA_TRY(c, cudaEventElapsedTime(&ms, c->ev[2 * k], c->ev[2 * k + 1]));
+      c->iter_ms += ms;
+    }
+  }
+  *iters_out = c->h_state->iter;
+  *status_out = c->h_state->status;
+  return PCG_OK;
+}
+
+pcg_status solve_common(pcg_ctx* c, const double* b, const double* x0, int32_t method, double sigma, double tol,
+                        int32_t maxit, int32_t precision, double* x_out, pcg_result* res, bool host) {
+  if (!c) return PCG_EINVAL;
+  c->err.clear();
+  if (!b || !x_out) return fail(c, PCG_EINVAL, "b and x_out must not be NULL");
+  if (method < PCG_CG || method > PCG_SPCG) return fail(c, PCG_EINVAL, "unknown method");
+  if (!(sigma >= 0.0) || !isfinite(sigma)) return fail(c, PCG_EINVAL, "sigma must be finite and >= 0");
+  if (!(tol >= 0.0) || !isfinite(tol)) return fail(c, PCG_EINVAL, "tol must be finite and >= 0");
+  if (maxit < 0 || maxit > (1 << 28)) return fail(c, PCG_EINVAL, "maxit out of range");
+  if (precision == PCG_MIXED_IR) return fail(c, PCG_ENOTIMPL, "PCG_MIXED_IR is not implemented");
+  if (precision != PCG_FP64) return fail(c, PCG_EINVAL, "unknown precision");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  pcg_status s;
+  if ((s = ensure_vectors(c)) != PCG_OK) return s;
+  if ((s = ensure_hist(c, maxit + 1)) != PCG_OK) return s;
+  const size_t bytes = (size_t)c->n * sizeof(double);
+  const cudaMemcpyKind in = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const cudaMemcpyKind outk = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (!host && ((uintptr_t)b % 16) == 0) {
+    c->v.b = b;                                   // aligned caller buffer: read in place
+  } else {
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_b, b, bytes, in, c->stream));
+    c->v.b = c->d_b;
+  }
+  if (x0) CUDA_TRY(c, cudaMemcpyAsync(c->v.x, x0, bytes, in, c->stream));
+  const int true_every = res ? res->true_every : 0;
+  int iters = 0, st = ST_RUNNING;
+  s = run_solve(c, x0 != nullptr, method, sigma, tol, maxit, true_every, &iters, &st);
+  c->v.b = c->d_b;
+  if (s != PCG_OK) return s;
+  CUDA_TRY(c, cudaMemcpyAsync(x_out, c->v.x, bytes, outk, c->stream));
+  pcg_status ret = st == ST_CONVERGED ? PCG_OK : st == ST_BREAKDOWN ? PCG_EBREAKDOWN : PCG_ENOTCONV;
+  if (res) {
+    const size_t k = (size_t)iters + 1;
+    auto get = [&](double* dst, const double* src) -> cudaError_t {
+      if (!dst) return cudaSuccess;
+      return cudaMemcpyAsync(dst, src, k * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    };
+    CUDA_TRY(c, get(res->rec_hist, c->h.rec));
+    CUDA_TRY(c, get(res->true_hist, c->h.tru));
+    CUDA_TRY(c, get(res->gap_hist, c->h.gap));
+    CUDA_TRY(c, get(res->alpha_hist, c->h.alpha));
+    CUDA_TRY(c, get(res->beta_hist, c->h.beta));
+    double fin[2] = {NAN, NAN};
+    CUDA_TRY(c, cudaMemcpyAsync(&fin[0], c->h.tru + iters, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(&fin[1], c->h.rec + iters, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    const double bn = c->h_state->bnorm;
+    res->iters = iters;
+    res->status = ret;
+    res->final_true_relres = bn > 0 ? fin[0] / bn : fin[0];
+    res->final_rec_relres = bn > 0 ? fin[1] / bn : fin[1];
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (ret == PCG_EBREAKDOWN) c->err = "breakdown: non-positive or non-finite curvature (delta or 1/alpha)";
+  return ret;
+}
+
+}  // namespace
+
+extern "C" {
+
+pcg_status pcg_solve(pcg_ctx* c, const double* b, const double* x0, int32_t method, double sigma, double tol,
+                     int32_t maxit, int32_t precision, double* x_out, pcg_result* res) {
+  return solve_common(c, b, x0, method, sigma, tol, maxit, precision, x_out, res, true);
+}
+
+pcg_status pcg_solve_device(pcg_ctx* c, const double* b, const double* x0, int32_t method, double sigma, double tol,
+                            int32_t maxit, int32_t precision, double* x_out, pcg_result* res) {
+  return solve_common(c, b, x0, method, sigma, tol, maxit, precision, x_out, res, false);
+}
+
+pcg_status pcg_psi(pcg_ctx* c, const double* alpha, const double* beta, int32_t i, const double* grid, int32_t ngrid,
+                   double* psi_out) {
+  if (!c) return PCG_EINVAL;
+  c->err.clear();
+  if (!alpha || !beta || !grid || !psi_out || i < 1 || ngrid < 1) return fail(c, PCG_EINVAL, "bad psi arguments");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  const int need = 2 * (i + 1) + 2 * ngrid;
+  if (c->small_cap < need) {
+    if (c->d_small) {
+      cudaFree(c->d_small);
+      c->owned.erase(std::find(c->owned.begin(), c->owned.end(), (void*)c->d_small));
+      c->d_small = nullptr;
+    }
+    void* p;
+    pcg_status s = dev_alloc(c, &p, (size_t)need * sizeof(double));
+    if (s != PCG_OK) return s;
+    c->d_small = (double*)p;
+    c->small_cap = need;
+  }
+  double* da = c->d_small;
+  double* db = da + (i + 1);
+  double* dg = db + (i + 1);
+  double* dp = dg + ngrid;
+  CUDA_TRY(c, cudaMemcpyAsync(da, alpha, (i + 1) * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(db, beta, (i + 1) * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(dg, grid, ngrid * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, launch_psi(da, db, i, dg, ngrid, dp, c->stream));
+  ++c->launches;
+  CUDA_TRY(c, cudaMemcpyAsync(psi_out, dp, ngrid * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return PCG_OK;
+}
+
+pcg_status pcg_select_sigma(pcg_ctx* c, const double* b, int32_t iters, const double* grid, int32_t ngrid,
+                            double* sigma_out, double* psi_out) {
+  if (!c) return PCG_EINVAL;
+  if (!b || !grid || !sigma_out || iters < 2 || ngrid < 1) return fail(c, PCG_EINVAL, "bad select_sigma arguments");
+  for (int k = 0; k < ngrid; ++k)
+    if (!(grid[k] >= 0.0) || !isfinite(grid[k])) return fail(c, PCG_EINVAL, "negative or non-finite shift");
+  std::vector<double> al(iters + 1), be(iters + 1), ps(ngrid);
+  std::vector<double> x(c->n);
+  pcg_result r{};
+  r.alpha_hist = al.data();
+  r.beta_hist = be.data();
+  pcg_status s = pcg_solve(c, b, nullptr, PCG_PCG, 0.0, 0.0, iters, PCG_FP64, x.data(), &r);
+  if (s != PCG_OK && s != PCG_ENOTCONV && s != PCG_EBREAKDOWN) return s;
+  const int i = r.iters - 1;   // alpha/beta exist for iterations 0 .. iters-1
+  if (i < 1) return fail(c, PCG_EINVAL, "pilot run too short for psi");
+  s = pcg_psi(c, al.data(), be.data(), i, grid, ngrid, ps.data());
+  if (s != PCG_OK) return s;
+  double mn = INFINITY;
+  for (double v : ps)
+    if (v < mn) mn = v;
+  double best = NAN;
+  for (int k = 0; k < ngrid; ++k)
+    if (ps[k] <= 2.0 * mn && !(grid[k] >= best)) best = grid[k];
+  *sigma_out = best;
+  if (psi_out) memcpy(psi_out, ps.data(), ngrid * sizeof(double));
+  return PCG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,112 @@
+// Maps a runtime operator description onto the compiled kernel instance.
+#include <utility>
+
+#include "pcg_kernels.cuh"
+
+namespace pcgk {
+namespace {
+
+template <int DIM, bool VAR, int VEC>
+StencilOp<DIM, VAR, VEC> make_stencil(const OpDesc& d) {
+  StencilOp<DIM, VAR, VEC> o;
+  o.n = d.n;
+  o.nx = d.nx;
+  o.ny = d.ny;
+  o.nz = d.nz;
+  o.nxny = d.nx * d.ny;
+  o.diag = d.diag;
+  o.ax = d.ax;
+  o.ay = d.ay;
+  o.az = d.az;
+  return o;
+}
+
+template <int DIM, class F>
+cudaError_t with_stencil(const OpDesc& d, F&& f) {
+  const bool var = d.diag != nullptr;
+  if (op_vec(d) == 2) {
+    if (var) return f(make_stencil<DIM, true, 2>(d));
+    return f(make_stencil<DIM, false, 2>(d));
+  }
+  if (var) return f(make_stencil<DIM, true, 1>(d));
+  return f(make_stencil<DIM, false, 1>(d));
+}
+
+template <class F>
+cudaError_t with_op(const OpDesc& d, F&& f) {
+  switch (d.layout) {
+    case 0: return with_stencil<2>(d, std::forward<F>(f));
+    case 1: return with_stencil<3>(d, std::forward<F>(f));
+    case 2: {
+      CsrOp o;
+      o.n = d.n;
+      o.row_ptr = d.row_ptr;
+      o.col = d.col;
+      o.val = d.val;
+      return f(o);
+    }
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <class Op>
+using K = Kernels<std::decay_t<Op>>;
+
+}  // namespace
+
+int op_vec(const OpDesc& d) {
+  if (d.layout == 2) return 1;
+  if (d.nx % 2 != 0) return 1;
+  if (d.diag != nullptr) {
+    const uintptr_t m = (uintptr_t)d.diag | (uintptr_t)d.ax | (uintptr_t)d.ay | (d.layout == 1 ? (uintptr_t)d.az : 0);
+    if (m % 16 != 0) return 1;
+  }
+  return 2;
+}
+
+int grid_for(const OpDesc& d, int kind, int block) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  int per_sm = 0;
+  with_op(d, [&](auto op) {
+    per_sm = K<decltype(op)>::blocks_per_sm(kind);
+    return cudaSuccess;
+  });
+  if (per_sm <= 0) return 0;
+  const long long units = d.n / op_vec(d);
+  long long g = (long long)sms * per_sm;
+  const long long need = (units + block - 1) / block;
+  if (need < g) g = need;
+  if (g < 1) g = 1;
+  if (g > kMaxPartialBlocks) g = kMaxPartialBlocks;
+  return (int)g;
+}
+
+cudaError_t launch_residual(const OpDesc& d, const Launch& L, const double* b, const double* x0, double* x, double* r,
+                            State* st, double* partials) {
+  return with_op(d, [&](auto op) { return K<decltype(op)>::residual(op, L, b, x0, x, r, st, partials); });
+}
+cudaError_t launch_spcg_w0(const OpDesc& d, const Launch& L, Vecs v, State* st, Hist h, double* partials) {
+  return with_op(d, [&](auto op) { return K<decltype(op)>::spcg_w0(op, L, v, st, h, partials); });
+}
+cudaError_t launch_spcg_iter(const OpDesc& d, const Launch& L, Vecs v, State* st, Hist h, double* partials) {
+  return with_op(d, [&](auto op) { return K<decltype(op)>::spcg_iter(op, L, v, st, h, partials); });
+}
+cudaError_t launch_true_res(const OpDesc& d, const Launch& L, Vecs v, State* st, Hist h, double* partials) {
+  return with_op(d, [&](auto op) { return K<decltype(op)>::true_res(op, L, v, st, h, partials); });
+}
+cudaError_t launch_cg_p0(const OpDesc& d, const Launch& L, Vecs v, State* st, Hist h, double* partials) {
+  return with_op(d, [&](auto op) { return K<decltype(op)>::cg_p0(op, L, v, st, h, partials); });
+}
+cudaError_t launch_cg_spmv(const OpDesc& d, const Launch& L, Vecs v, State* st, Hist h, double* partials) {
+  return with_op(d, [&](auto op) { return K<decltype(op)>::cg_spmv(op, L, v, st, h, partials); });
+}
+cudaError_t launch_cg_update(const OpDesc& d, const Launch& L, Vecs v, State* st, Hist h, double* partials) {
+  return with_op(d, [&](auto op) { return K<decltype(op)>::cg_update(op, L, v, st, h, partials); });
+}
+cudaError_t launch_cg_p(const OpDesc& d, const Launch& L, Vecs v, State* st, Hist h) {
+  return with_op(d, [&](auto op) { return K<decltype(op)>::cg_p(op, L, v, st, h); });
+}
+
+}  // namespace pcgk

@@ -1,0 +1,77 @@
+// Internal interface between the C-ABI layer (pcg_capi.cu) and the kernels
+// (pcg_kernels.cu, pcg_psi.cu).  Plain structs shared by host and device code.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pcgk {
+
+// Run state of one solve (device memory).
+enum : int { ST_RUNNING = 0, ST_CONVERGED = 1, ST_BREAKDOWN = 2, ST_MAXIT = 3 };
+
+struct State {
+  int iter;              // index i of the next iteration to execute (or of the last iterate once stopped)
+  int status;            // ST_*
+  int maxit;
+  int pad0;
+  double sigma;          // shift of Algorithm 3 (0 for Algorithms 1 and 2)
+  double tol_abs;        // stop once ||r_i|| <= tol_abs (0: never)
+  double bnorm;          // ||b||_2
+  unsigned int ticket;   // last-block ticket of the running reduction (reset to 0 by its finisher)
+  unsigned int pad1;
+};
+
+// Per-iteration histories (device arrays of maxit + 1 entries).
+struct Hist {
+  double *alpha, *beta, *gamma, *delta, *rec, *tru, *gap;
+};
+
+// The operator: a cell-centred stencil (2D 5-point / 3D 7-point, constant or
+// variable coefficients) or a CSR matrix.  Device pointers.
+struct OpDesc {
+  int layout;            // 0 = 2D stencil, 1 = 3D stencil, 2 = CSR
+  int n, nx, ny, nz;
+  const double *diag, *ax, *ay, *az;   // variable coefficients; diag == nullptr: Laplacian
+  const int *row_ptr, *col;
+  const double *val;
+};
+
+// Solver vectors (device, n entries each, 256-byte aligned).
+struct Vecs {
+  const double* b;
+  double *x, *r, *w0, *w1, *z, *s, *p;
+};
+
+struct Launch {
+  int grid, block;
+  cudaStream_t stream;
+};
+
+// Number of vector lanes per thread the kernels use for this operator
+// (2 = 128-bit loads; needs an even row length for stencils).
+int op_vec(const OpDesc& op);
+
+// Resident-grid size of each kernel family for this operator (0 on error).
+int grid_for(const OpDesc& op, int kind, int block);
+enum { K_RESIDUAL = 0, K_SPCG_W0, K_SPCG_ITER, K_TRUE_RES, K_CG_P0, K_CG_SPMV, K_CG_UPDATE, K_CG_P, K_NKINDS };
+
+// Kernel launchers (asynchronous; return the launch error).
+cudaError_t launch_residual(const OpDesc& op, const Launch& L, const double* b, const double* x0, double* x, double* r,
+                            State* st, double* partials);
+cudaError_t launch_spcg_w0(const OpDesc& op, const Launch& L, Vecs v, State* st, Hist h, double* partials);
+cudaError_t launch_spcg_iter(const OpDesc& op, const Launch& L, Vecs v, State* st, Hist h, double* partials);
+cudaError_t launch_true_res(const OpDesc& op, const Launch& L, Vecs v, State* st, Hist h, double* partials);
+cudaError_t launch_cg_p0(const OpDesc& op, const Launch& L, Vecs v, State* st, Hist h, double* partials);
+cudaError_t launch_cg_spmv(const OpDesc& op, const Launch& L, Vecs v, State* st, Hist h, double* partials);
+cudaError_t launch_cg_update(const OpDesc& op, const Launch& L, Vecs v, State* st, Hist h, double* partials);
+cudaError_t launch_cg_p(const OpDesc& op, const Launch& L, Vecs v, State* st, Hist h);
+
+// psi_i(sigma) for every shift of sig[ngrid]; alpha/beta device arrays (>= i+1 entries).
+cudaError_t launch_psi(const double* alpha, const double* beta, int i, const double* sig, int ngrid, double* psi,
+                       cudaStream_t stream);
+
+constexpr int kBlockThreads = 256;        // block size of every solver kernel
+constexpr int kMaxPartialBlocks = 8192;   // capacity of the per-block partial-sum buffer
+constexpr int kPartialsPerBlock = 2;
+
+}  // namespace pcgk

@@ -1,0 +1,629 @@
+// Device code of the solver: operators, the two-level reduction with its
+// finishers, and the kernels of Algorithms 1 and 3 (arXiv 1706.05988).
+//
+// Layout: every vector is a contiguous binary64 array; a thread handles VEC
+// consecutive unknowns (VEC = 2 -> 128-bit loads/stores) of a grid-stride loop
+// over "units" of VEC unknowns.  The grid is sized to the resident capacity of
+// the GPU so that each block accumulates its dot-product partials over many
+// units and the global reduction reads only one partial per block.
+//
+// Definitions are compiled only where PCG_KERNELS_IMPL is defined (one
+// translation unit per operator family); other units see declarations.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "pcg_internal.h"
+
+namespace pcgk {
+
+constexpr int kBlock = kBlockThreads;
+constexpr int kWarps = kBlock / 32;
+
+// ---------------------------------------------------------------- operators
+
+// Cell-centred stencil on an nx x ny (x nz) grid with Dirichlet boundary.
+// Constant coefficients: (A w)_c = C w_c - sum of the in-grid neighbours,
+// C = 4 (2D) / 6 (3D).  Variable coefficients: see pcg_matrix in pcg.h.
+template <int DIM, bool VAR, int VEC_>
+struct StencilOp {
+  static constexpr int VEC = VEC_;
+  int n, nx, ny, nz, nxny;
+  const double *diag, *ax, *ay, *az;
+
+  __host__ __device__ int units() const { return n / VEC; }
+
+#ifdef PCG_KERNELS_IMPL
+  // wc[e] = w at the unit's own unknowns, aw[e] = (A w) there.
+  __device__ __forceinline__ void apply(const double* __restrict__ w, int u, double (&wc)[VEC],
+                                        double (&aw)[VEC]) const {
+    const unsigned c0 = (unsigned)u * VEC;
+    const unsigned i0 = c0 % (unsigned)nx;
+    const unsigned t = c0 / (unsigned)nx;
+    const unsigned j = t % (unsigned)ny;
+    const unsigned k = t / (unsigned)ny;
+    const bool has_ym = j > 0, has_yp = j + 1 < (unsigned)ny;
+    const bool has_zm = DIM == 3 && k > 0, has_zp = DIM == 3 && k + 1 < (unsigned)nz;
+    double c[VEC], ym[VEC], yp[VEC], zm[VEC], zp[VEC];
+    ldg<VEC>(w + c0, c);
+    ldg_if<VEC>(has_ym, w + c0 - nx, ym);
+    ldg_if<VEC>(has_yp, w + c0 + nx, yp);
+    if (DIM == 3) {
+      ldg_if<VEC>(has_zm, w + c0 - nxny, zm);
+      ldg_if<VEC>(has_zp, w + c0 + nxny, zp);
+    }
+    // x neighbours of the unit: left of the first, right of the last unknown
+    const double xl = i0 > 0 ? __ldg(w + c0 - 1) : 0.0;
+    const double xr = i0 + VEC < (unsigned)nx ? __ldg(w + c0 + VEC) : 0.0;
+    double xm[VEC], xp[VEC];
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) {
+      xm[e] = e == 0 ? xl : c[e - 1];
+      xp[e] = e == VEC - 1 ? xr : c[e + 1];
+      wc[e] = c[e];
+    }
+    if (!VAR) {
+      constexpr double C = DIM == 3 ? 6.0 : 4.0;
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        double s = (xm[e] + xp[e]) + (ym[e] + yp[e]);
+        if (DIM == 3) s += zm[e] + zp[e];
+        aw[e] = fma(C, c[e], -s);
+      }
+    } else {
+      double d[VEC], fx[VEC], fy[VEC], fyp[VEC], fz[VEC], fzp[VEC];
+      ldg<VEC>(diag + c0, d);
+      ldg<VEC>(ax + c0, fx);
+      ldg<VEC>(ay + c0, fy);
+      ldg_if<VEC>(has_yp, ay + c0 + nx, fyp);
+      if (DIM == 3) {
+        ldg<VEC>(az + c0, fz);
+        ldg_if<VEC>(has_zp, az + c0 + nxny, fzp);
+      }
+      const double fxr = i0 + VEC < (unsigned)nx ? __ldg(ax + c0 + VEC) : 0.0;
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        const double fxp = e == VEC - 1 ? fxr : fx[e + 1];
+        double a = d[e] * c[e];
+        a = fma(-fx[e], xm[e], a);
+        a = fma(-fxp, xp[e], a);
+        a = fma(-fy[e], ym[e], a);
+        a = fma(-fyp[e], yp[e], a);
+        if (DIM == 3) {
+          a = fma(-fz[e], zm[e], a);
+          a = fma(-fzp[e], zp[e], a);
+        }
+        aw[e] = a;
+      }
+    }
+  }
+
+  template <int V>
+  __device__ __forceinline__ static void ldg(const double* p, double (&o)[V]) {
+    if constexpr (V == 2) {
+      const double2 t = __ldg(reinterpret_cast<const double2*>(p));
+      o[0] = t.x;
+      o[1] = t.y;
+    } else {
+      o[0] = __ldg(p);
+    }
+  }
+  template <int V>
+  __device__ __forceinline__ static void ldg_if(bool ok, const double* p, double (&o)[V]) {
+    if (ok) {
+      ldg<V>(p, o);
+    } else {
+#pragma unroll
+      for (int e = 0; e < V; ++e) o[e] = 0.0;
+    }
+  }
+#endif
+};
+
+// CSR matrix, one row per unit.
+struct CsrOp {
+  static constexpr int VEC = 1;
+  int n;
+  const int *row_ptr, *col;
+  const double* val;
+
+  __host__ __device__ int units() const { return n; }
+
+#ifdef PCG_KERNELS_IMPL
+  __device__ __forceinline__ void apply(const double* __restrict__ w, int u, double (&wc)[1], double (&aw)[1]) const {
+    const int beg = __ldg(row_ptr + u), end = __ldg(row_ptr + u + 1);
+    double a = 0.0;
+    for (int k = beg; k < end; ++k) a = fma(__ldg(val + k), __ldg(w + __ldg(col + k)), a);
+    aw[0] = a;
+    wc[0] = __ldg(w + u);
+  }
+#endif
+};
+
+// ---------------------------------------------------------------- launch table
+
+template <class Op>
+struct Kernels {
+  static cudaError_t residual(const Op& op, const Launch& L, const double* b, const double* x0, double* x,
+                              double* r, State* st, double* partials);
+  static cudaError_t spcg_w0(const Op& op, const Launch& L, Vecs v, State* st, Hist h, double* partials);
+  static cudaError_t spcg_iter(const Op& op, const Launch& L, Vecs v, State* st, Hist h, double* partials);
+  static cudaError_t true_res(const Op& op, const Launch& L, Vecs v, State* st, Hist h, double* partials);
+  static cudaError_t cg_p0(const Op& op, const Launch& L, Vecs v, State* st, Hist h, double* partials);
+  static cudaError_t cg_spmv(const Op& op, const Launch& L, Vecs v, State* st, Hist h, double* partials);
+  static cudaError_t cg_update(const Op& op, const Launch& L, Vecs v, State* st, Hist h, double* partials);
+  static cudaError_t cg_p(const Op& op, const Launch& L, Vecs v, State* st, Hist h);
+  static int blocks_per_sm(int kind);
+};
+
+#ifdef PCG_KERNELS_IMPL
+
+// ---------------------------------------------------------------- vector access
+
+template <int V>
+__device__ __forceinline__ void ld_stream(const double* p, double (&o)[V]) {
+  if constexpr (V == 2) {
+    const double2 t = __ldcs(reinterpret_cast<const double2*>(p));
+    o[0] = t.x;
+    o[1] = t.y;
+  } else {
+    o[0] = __ldcs(p);
+  }
+}
+template <int V>
+__device__ __forceinline__ void st_stream(double* p, const double (&o)[V]) {
+  if constexpr (V == 2) {
+    __stcs(reinterpret_cast<double2*>(p), make_double2(o[0], o[1]));
+  } else {
+    __stcs(p, o[0]);
+  }
+}
+template <int V>
+__device__ __forceinline__ void st_plain(double* p, const double (&o)[V]) {
+  if constexpr (V == 2) {
+    *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
+  } else {
+    *p = o[0];
+  }
+}
+
+// ---------------------------------------------------------------- reductions
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sums of NV values -> one partial per block; the last block to arrive
+// (atomic ticket) sums all partials in block order and returns true with the
+// totals in thread 0's `tot`.  Deterministic: the summation order depends only
+// on the grid size.  No block waits for another.
+template <int NV>
+__device__ __forceinline__ bool reduce_last_block(double (&v)[NV], double* __restrict__ partials,
+                                                  unsigned* ticket, double (&tot)[NV]) {
+  __shared__ double sh[kWarps][NV];
+  __shared__ int s_last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sh[wid][q] = v[q];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double a = 0.0;
+      for (int k = 0; k < kWarps; ++k) a += sh[k][q];
+      partials[blockIdx.x * NV + q] = a;
+    }
+    __threadfence();
+    const unsigned t = atomicAdd(ticket, 1u);
+    s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  double a[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) a[q] = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += kBlock) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) a[q] += __ldcg(partials + b * NV + q);
+  }
+#pragma unroll
+  for (int q = 0; q < NV; ++q) a[q] = warp_sum(a[q]);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sh[wid][q] = a[q];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double s = 0.0;
+      for (int k = 0; k < kWarps; ++k) s += sh[k][q];
+      tot[q] = s;
+    }
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------- finishers (one thread)
+
+// Scalars of Algorithm 3 for iteration i from gamma_i = (r_i, r_i) and
+// omega_i = (w_i, r_i); delta = (w_i + sigma r_i, r_i) = omega_i + sigma gamma_i.
+// i = 0: beta_0 = 0, alpha_0 = gamma_0 / delta.  i > 0: beta_i = gamma_i / gamma_{i-1},
+// alpha_i = 1 / (delta / gamma_i - beta_i / alpha_{i-1}).
+// Stop tests in the oracle's order: tolerance, maxit, exact zero, breakdown.
+__device__ __forceinline__ void finish_spcg(State* st, Hist h, double gamma, double omega, bool init) {
+  const int i = init ? 0 : st->iter + 1;
+  const double delta = omega + st->sigma * gamma;
+  const double rn = sqrt(gamma);
+  h.gamma[i] = gamma;
+  h.delta[i] = delta;
+  h.rec[i] = rn;
+  int status = ST_RUNNING;
+  if (st->tol_abs > 0.0 && rn <= st->tol_abs) {
+    status = ST_CONVERGED;
+  } else if (i >= st->maxit) {
+    status = ST_MAXIT;
+  } else if (gamma == 0.0) {
+    status = ST_CONVERGED;
+  } else if (init) {
+    if (!(delta > 0.0) || !isfinite(delta)) {
+      status = ST_BREAKDOWN;
+    } else {
+      h.alpha[0] = gamma / delta;
+      h.beta[0] = 0.0;
+    }
+  } else {
+    const double beta = gamma / h.gamma[i - 1];
+    const double den = delta / gamma - beta / h.alpha[i - 1];
+    if (!(den > 0.0) || !isfinite(den)) {
+      status = ST_BREAKDOWN;
+    } else {
+      h.alpha[i] = 1.0 / den;
+      h.beta[i] = beta;
+    }
+  }
+  st->iter = i;
+  st->status = status;
+  st->ticket = 0;
+}
+
+// Algorithm 1 after (r_i, r_i): stop tests, beta_i = gamma_i / gamma_{i-1}.
+__device__ __forceinline__ void finish_cg_gamma(State* st, Hist h, double gamma, bool init) {
+  const int i = init ? 0 : st->iter + 1;
+  const double rn = sqrt(gamma);
+  h.gamma[i] = gamma;
+  h.rec[i] = rn;
+  int status = ST_RUNNING;
+  if (st->tol_abs > 0.0 && rn <= st->tol_abs) {
+    status = ST_CONVERGED;
+  } else if (i >= st->maxit) {
+    status = ST_MAXIT;
+  } else if (gamma == 0.0) {
+    status = ST_CONVERGED;
+  } else {
+    h.beta[i] = init ? 0.0 : gamma / h.gamma[i - 1];
+  }
+  st->iter = i;
+  st->status = status;
+  st->ticket = 0;
+}
+
+// ---------------------------------------------------------------- kernels
+
+// r = b - A x0 (x0 given) or r = b, x = 0; ||b|| -> bnorm, tol_abs = tol_rel * ||b||.
+template <class Op>
+__global__ void __launch_bounds__(kBlock) k_residual(Op op, const double* __restrict__ b, int has_x0,
+                                                     double* __restrict__ x, double* __restrict__ r, State* st,
+                                                     double* partials) {
+  constexpr int VEC = Op::VEC;
+  double bb = 0.0;
+  const int nu = op.units();
+  for (int u = blockIdx.x * kBlock + threadIdx.x; u < nu; u += gridDim.x * kBlock) {
+    const int c0 = u * VEC;
+    double bv[VEC], rv[VEC];
+    ld_stream<VEC>(b + c0, bv);
+    if (has_x0) {
+      double xc[VEC], ax[VEC];
+      op.apply(x, u, xc, ax);
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) rv[e] = bv[e] - ax[e];
+    } else {
+      double zero[VEC];
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        rv[e] = bv[e];
+        zero[e] = 0.0;
+      }
+      st_plain<VEC>(x + c0, zero);
+    }
+    st_plain<VEC>(r + c0, rv);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) bb = fma(bv[e], bv[e], bb);
+  }
+  double v[1] = {bb}, tot[1];
+  if (!reduce_last_block<1>(v, partials, &st->ticket, tot)) return;
+  if (threadIdx.x == 0) {
+    st->bnorm = sqrt(tot[0]);
+    st->tol_abs = st->tol_abs * st->bnorm;   // tol_abs holds the relative tolerance until here
+    st->ticket = 0;
+  }
+}
+
+// Algorithm 3, line 1 (M = I): w_0 = A r_0 - sigma r_0; z, s, p := 0 (so that
+// beta_0 z_{-1} etc. vanish); gamma_0, delta_0 -> alpha_0.
+template <class Op>
+__global__ void __launch_bounds__(kBlock) k_spcg_w0(Op op, Vecs v, State* st, Hist h, double* partials) {
+  constexpr int VEC = Op::VEC;
+  if (st->status != ST_RUNNING) return;
+  const double sigma = st->sigma;
+  double g = 0.0, o = 0.0;
+  const int nu = op.units();
+  for (int u = blockIdx.x * kBlock + threadIdx.x; u < nu; u += gridDim.x * kBlock) {
+    const int c0 = u * VEC;
+    double rc[VEC], ar[VEC], w[VEC], zero[VEC];
+    op.apply(v.r, u, rc, ar);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) {
+      w[e] = fma(-sigma, rc[e], ar[e]);
+      zero[e] = 0.0;
+      g = fma(rc[e], rc[e], g);
+      o = fma(w[e], rc[e], o);
+    }
+    st_plain<VEC>(v.w0 + c0, w);
+    st_plain<VEC>(v.z + c0, zero);
+    st_plain<VEC>(v.s + c0, zero);
+    st_plain<VEC>(v.p + c0, zero);
+  }
+  double vals[2] = {g, o}, tot[2];
+  if (!reduce_last_block<2>(vals, partials, &st->ticket, tot)) return;
+  if (threadIdx.x == 0) finish_spcg(st, h, tot[0], tot[1], true);
+}
+
+// One iteration of Algorithm 3 with M = I (u = r, q = s, t = p, m = w), fused:
+//   n_i = A w_i;  z_i = n_i + beta_i z_{i-1};  s_i = w_i + beta_i s_{i-1};
+//   p_i = r_i + beta_i p_{i-1};  x_{i+1} = x_i + alpha_i p_i;
+//   r_{i+1} = r_i - (alpha_i s_i + alpha_i sigma p_i);  w_{i+1} = w_i - alpha_i z_i;
+// and, in the same sweep, the partials of gamma_{i+1} = (r_{i+1}, r_{i+1}) and
+// (w_{i+1}, r_{i+1}); the last block turns them into alpha_{i+1}, beta_{i+1}.
+// w is double-buffered (neighbours read w_i while w_{i+1} is written).
+template <class Op>
+__global__ void __launch_bounds__(kBlock) k_spcg_iter(Op op, Vecs v, State* st, Hist h, double* partials) {
+  constexpr int VEC = Op::VEC;
+  if (st->status != ST_RUNNING) return;
+  const int it = st->iter;
+  const double alpha = h.alpha[it], beta = h.beta[it];
+  const double asg = alpha * st->sigma;
+  const double* __restrict__ w = (it & 1) ? v.w1 : v.w0;
+  double* __restrict__ wn = (it & 1) ? v.w0 : v.w1;
+  double g = 0.0, o = 0.0;
+  const int nu = op.units();
+  for (int u = blockIdx.x * kBlock + threadIdx.x; u < nu; u += gridDim.x * kBlock) {
+    const int c0 = u * VEC;
+    double wc[VEC], nv[VEC], z[VEC], s[VEC], p[VEC], x[VEC], r[VEC], w1[VEC];
+    op.apply(w, u, wc, nv);
+    ld_stream<VEC>(v.z + c0, z);
+    ld_stream<VEC>(v.s + c0, s);
+    ld_stream<VEC>(v.p + c0, p);
+    ld_stream<VEC>(v.x + c0, x);
+    ld_stream<VEC>(v.r + c0, r);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) {
+      z[e] = fma(beta, z[e], nv[e]);
+      s[e] = fma(beta, s[e], wc[e]);
+      p[e] = fma(beta, p[e], r[e]);
+      x[e] = fma(alpha, p[e], x[e]);
+      const double rn = r[e] - fma(asg, p[e], alpha * s[e]);
+      const double wv = fma(-alpha, z[e], wc[e]);
+      r[e] = rn;
+      w1[e] = wv;
+      g = fma(rn, rn, g);
+      o = fma(wv, rn, o);
+    }
+    st_stream<VEC>(v.z + c0, z);
+    st_stream<VEC>(v.s + c0, s);
+    st_stream<VEC>(v.p + c0, p);
+    st_stream<VEC>(v.x + c0, x);
+    st_stream<VEC>(v.r + c0, r);
+    st_plain<VEC>(wn + c0, w1);
+  }
+  double vals[2] = {g, o}, tot[2];
+  if (!reduce_last_block<2>(vals, partials, &st->ticket, tot)) return;
+  if (threadIdx.x == 0) finish_spcg(st, h, tot[0], tot[1], false);
+}
+
+// True residual and gap at the current iterate: ||b - A x||, ||(b - A x) - r||
+// (Section 3.1, the gap f_i), written at index st->iter.
+template <class Op>
+__global__ void __launch_bounds__(kBlock) k_true_res(Op op, Vecs v, State* st, Hist h, double* partials) {
+  constexpr int VEC = Op::VEC;
+  double t2 = 0.0, f2 = 0.0;
+  const int nu = op.units();
+  for (int u = blockIdx.x * kBlock + threadIdx.x; u < nu; u += gridDim.x * kBlock) {
+    const int c0 = u * VEC;
+    double xc[VEC], ax[VEC], bv[VEC], rv[VEC];
+    op.apply(v.x, u, xc, ax);
+    ld_stream<VEC>(v.b + c0, bv);
+    ld_stream<VEC>(v.r + c0, rv);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) {
+      const double t = bv[e] - ax[e];
+      const double f = t - rv[e];
+      t2 = fma(t, t, t2);
+      f2 = fma(f, f, f2);
+    }
+  }
+  double vals[2] = {t2, f2}, tot[2];
+  if (!reduce_last_block<2>(vals, partials, &st->ticket, tot)) return;
+  if (threadIdx.x == 0) {
+    const int i = st->iter;
+    h.tru[i] = sqrt(tot[0]);
+    h.gap[i] = sqrt(tot[1]);
+    st->ticket = 0;
+  }
+}
+
+// Algorithm 1, line 1: p_0 = r_0 (M = I), gamma_0 = (r_0, r_0).
+template <int VEC>
+__global__ void __launch_bounds__(kBlock) k_cg_p0(int n, Vecs v, State* st, Hist h, double* partials) {
+  if (st->status != ST_RUNNING) return;
+  double g = 0.0;
+  const int nu = n / VEC;
+  for (int u = blockIdx.x * kBlock + threadIdx.x; u < nu; u += gridDim.x * kBlock) {
+    const int c0 = u * VEC;
+    double r[VEC];
+    ld_stream<VEC>(v.r + c0, r);
+    st_plain<VEC>(v.p + c0, r);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) g = fma(r[e], r[e], g);
+  }
+  double vals[1] = {g}, tot[1];
+  if (!reduce_last_block<1>(vals, partials, &st->ticket, tot)) return;
+  if (threadIdx.x == 0) finish_cg_gamma(st, h, tot[0], true);
+}
+
+// Algorithm 1: s_i = A p_i and (s_i, p_i) -> alpha_i = gamma_i / (s_i, p_i).
+template <class Op>
+__global__ void __launch_bounds__(kBlock) k_cg_spmv(Op op, Vecs v, State* st, Hist h, double* partials) {
+  constexpr int VEC = Op::VEC;
+  if (st->status != ST_RUNNING) return;
+  double sp = 0.0;
+  const int nu = op.units();
+  for (int u = blockIdx.x * kBlock + threadIdx.x; u < nu; u += gridDim.x * kBlock) {
+    const int c0 = u * VEC;
+    double pc[VEC], s[VEC];
+    op.apply(v.p, u, pc, s);
+    st_plain<VEC>(v.s + c0, s);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) sp = fma(s[e], pc[e], sp);
+  }
+  double vals[1] = {sp}, tot[1];
+  if (!reduce_last_block<1>(vals, partials, &st->ticket, tot)) return;
+  if (threadIdx.x == 0) {
+    const int i = st->iter;
+    if (!(tot[0] > 0.0) || !isfinite(tot[0])) {
+      st->status = ST_BREAKDOWN;
+    } else {
+      h.alpha[i] = h.gamma[i] / tot[0];
+    }
+    st->ticket = 0;
+  }
+}
+
+// Algorithm 1: x_{i+1} = x_i + alpha_i p_i, r_{i+1} = r_i - alpha_i s_i, gamma_{i+1}.
+template <int VEC>
+__global__ void __launch_bounds__(kBlock) k_cg_update(int n, Vecs v, State* st, Hist h, double* partials) {
+  if (st->status != ST_RUNNING) return;
+  const double alpha = h.alpha[st->iter];
+  double g = 0.0;
+  const int nu = n / VEC;
+  for (int u = blockIdx.x * kBlock + threadIdx.x; u < nu; u += gridDim.x * kBlock) {
+    const int c0 = u * VEC;
+    double x[VEC], r[VEC], p[VEC], s[VEC];
+    ld_stream<VEC>(v.x + c0, x);
+    ld_stream<VEC>(v.r + c0, r);
+    ld_stream<VEC>(v.p + c0, p);
+    ld_stream<VEC>(v.s + c0, s);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) {
+      x[e] = fma(alpha, p[e], x[e]);
+      r[e] = fma(-alpha, s[e], r[e]);
+      g = fma(r[e], r[e], g);
+    }
+    st_stream<VEC>(v.x + c0, x);
+    st_stream<VEC>(v.r + c0, r);
+  }
+  double vals[1] = {g}, tot[1];
+  if (!reduce_last_block<1>(vals, partials, &st->ticket, tot)) return;
+  if (threadIdx.x == 0) finish_cg_gamma(st, h, tot[0], false);
+}
+
+// Algorithm 1: p_{i+1} = u_{i+1} + beta_{i+1} p_i (u = r).
+template <int VEC>
+__global__ void __launch_bounds__(kBlock) k_cg_p(int n, Vecs v, State* st, Hist h) {
+  if (st->status != ST_RUNNING) return;
+  const double beta = h.beta[st->iter];
+  const int nu = n / VEC;
+  for (int u = blockIdx.x * kBlock + threadIdx.x; u < nu; u += gridDim.x * kBlock) {
+    const int c0 = u * VEC;
+    double r[VEC], p[VEC];
+    ld_stream<VEC>(v.r + c0, r);
+    ld_stream<VEC>(v.p + c0, p);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) p[e] = fma(beta, p[e], r[e]);
+    st_plain<VEC>(v.p + c0, p);
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+
+template <class Op>
+cudaError_t Kernels<Op>::residual(const Op& op, const Launch& L, const double* b, const double* x0, double* x,
+                                  double* r, State* st, double* partials) {
+  k_residual<Op><<<L.grid, L.block, 0, L.stream>>>(op, b, x0 != nullptr, x, r, st, partials);
+  return cudaGetLastError();
+}
+template <class Op>
+cudaError_t Kernels<Op>::spcg_w0(const Op& op, const Launch& L, Vecs v, State* st, Hist h, double* partials) {
+  k_spcg_w0<Op><<<L.grid, L.block, 0, L.stream>>>(op, v, st, h, partials);
+  return cudaGetLastError();
+}
+template <class Op>
+cudaError_t Kernels<Op>::spcg_iter(const Op& op, const Launch& L, Vecs v, State* st, Hist h, double* partials) {
+  k_spcg_iter<Op><<<L.grid, L.block, 0, L.stream>>>(op, v, st, h, partials);
+  return cudaGetLastError();
+}
+template <class Op>
+cudaError_t Kernels<Op>::true_res(const Op& op, const Launch& L, Vecs v, State* st, Hist h, double* partials) {
+  k_true_res<Op><<<L.grid, L.block, 0, L.stream>>>(op, v, st, h, partials);
+  return cudaGetLastError();
+}
+template <class Op>
+cudaError_t Kernels<Op>::cg_p0(const Op& op, const Launch& L, Vecs v, State* st, Hist h, double* partials) {
+  k_cg_p0<Op::VEC><<<L.grid, L.block, 0, L.stream>>>(op.n, v, st, h, partials);
+  return cudaGetLastError();
+}
+template <class Op>
+cudaError_t Kernels<Op>::cg_spmv(const Op& op, const Launch& L, Vecs v, State* st, Hist h, double* partials) {
+  k_cg_spmv<Op><<<L.grid, L.block, 0, L.stream>>>(op, v, st, h, partials);
+  return cudaGetLastError();
+}
+template <class Op>
+cudaError_t Kernels<Op>::cg_update(const Op& op, const Launch& L, Vecs v, State* st, Hist h, double* partials) {
+  k_cg_update<Op::VEC><<<L.grid, L.block, 0, L.stream>>>(op.n, v, st, h, partials);
+  return cudaGetLastError();
+}
+template <class Op>
+cudaError_t Kernels<Op>::cg_p(const Op& op, const Launch& L, Vecs v, State* st, Hist h) {
+  k_cg_p<Op::VEC><<<L.grid, L.block, 0, L.stream>>>(op.n, v, st, h);
+  return cudaGetLastError();
+}
+template <class Op>
+int Kernels<Op>::blocks_per_sm(int kind) {
+  int nb = 0;
+  cudaError_t e = cudaSuccess;
+  switch (kind) {
+    case K_RESIDUAL: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_residual<Op>, kBlock, 0); break;
+    case K_SPCG_W0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spcg_w0<Op>, kBlock, 0); break;
+    case K_SPCG_ITER: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spcg_iter<Op>, kBlock, 0); break;
+    case K_TRUE_RES: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_true_res<Op>, kBlock, 0); break;
+    case K_CG_P0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cg_p0<Op::VEC>, kBlock, 0); break;
+    case K_CG_SPMV: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cg_spmv<Op>, kBlock, 0); break;
+    case K_CG_UPDATE: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cg_update<Op::VEC>, kBlock, 0); break;
+    case K_CG_P: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cg_p<Op::VEC>, kBlock, 0); break;
+    default: return 0;
+  }
+  return e == cudaSuccess ? nb : 0;
+}
+
+#endif  // PCG_KERNELS_IMPL
+
+}  // namespace pcgk

@@ -1,0 +1,269 @@
+"""ctypes binding of libpcg (C ABI in include/pcg.h): argument marshalling only.
+
+Every function named pcg_* here calls the C function of the same name.  The
+library must have been built (build.build()); loading fails loudly otherwise,
+and there is no fallback path of any kind.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpcg.so")
+
+# pcg_status
+PCG_OK, PCG_EINVAL, PCG_ENOMEM, PCG_ECUDA, PCG_EBREAKDOWN, PCG_ENOTCONV, PCG_ETIMEOUT, PCG_PENDING, PCG_ENOTIMPL = range(9)
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EBREAKDOWN", 5: "ENOTCONV", 6: "ETIMEOUT",
+                7: "PENDING", 8: "ENOTIMPL"}
+# pcg_layout / pcg_method / pcg_precision
+PCG_STENCIL5_2D, PCG_STENCIL7_3D, PCG_CSR32 = 0, 1, 2
+PCG_CG, PCG_PCG, PCG_SPCG = 0, 1, 2
+PCG_FP64, PCG_MIXED_IR = 0, 1
+# pcg_create flags
+PCG_DEVICE_PTRS = 0x1
+PCG_PROFILE = 0x2
+
+METHODS = {"cg": PCG_CG, "pcg": PCG_PCG, "spcg": PCG_SPCG}
+
+
+class PcgError(RuntimeError):
+    def __init__(self, status: int, msg: str = ""):
+        super().__init__(f"pcg status {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class pcg_matrix(ctypes.Structure):
+    _fields_ = [("layout", ctypes.c_int32), ("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64),
+                ("diag", ctypes.c_void_p), ("ax", ctypes.c_void_p), ("ay", ctypes.c_void_p), ("az", ctypes.c_void_p),
+                ("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class pcg_result(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("final_true_relres", ctypes.c_double),
+                ("final_rec_relres", ctypes.c_double), ("rec_hist", ctypes.c_void_p),
+                ("true_hist", ctypes.c_void_p), ("gap_hist", ctypes.c_void_p), ("alpha_hist", ctypes.c_void_p),
+                ("beta_hist", ctypes.c_void_p), ("true_every", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libpcg (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libpcg.so not found at {LIB_PATH}: run __graft_entry__.build() first "
+                               "(there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, f64, st = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+        L.pcg_create.argtypes = [ctypes.POINTER(pcg_matrix), ctypes.c_uint32, ctypes.POINTER(vp)]
+        L.pcg_destroy.argtypes = [vp]
+        L.pcg_destroy.restype = None
+        L.pcg_last_error.argtypes = [vp]
+        L.pcg_last_error.restype = ctypes.c_char_p
+        L.pcg_set_stream.argtypes = [vp, vp]
+        solve_args = [vp, vp, vp, i32, f64, f64, i32, i32, vp, ctypes.POINTER(pcg_result)]
+        L.pcg_solve.argtypes = solve_args
+        L.pcg_solve_device.argtypes = solve_args
+        L.pcg_select_sigma.argtypes = [vp, vp, i32, vp, i32, ctypes.POINTER(f64), vp]
+        L.pcg_psi.argtypes = [vp, vp, vp, i32, vp, i32, vp]
+        L.pcg_kernel_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(f64)]
+        L.pcg_kernel_stats_reset.argtypes = [vp]
+        L.pcg_version.argtypes = []
+        L.pcg_version.restype = ctypes.c_char_p
+        for f in ("pcg_create", "pcg_set_stream", "pcg_solve", "pcg_solve_device", "pcg_select_sigma", "pcg_psi",
+                  "pcg_kernel_stats", "pcg_kernel_stats_reset"):
+            getattr(L, f).restype = st
+        _lib = L
+    return _lib
+
+
+def _p(a) -> Optional[int]:
+    """Address of a numpy array / torch tensor / int (None stays None)."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    raise TypeError(type(a))
+
+
+# ---------------------------------------------------------------- same-name wrappers
+
+def pcg_version() -> str:
+    return lib().pcg_version().decode()
+
+
+def pcg_last_error(ctx) -> str:
+    return lib().pcg_last_error(ctx).decode()
+
+
+def pcg_create(A: pcg_matrix, flags: int = 0) -> int:
+    out = ctypes.c_void_p()
+    s = lib().pcg_create(ctypes.byref(A), flags, ctypes.byref(out))
+    if s != PCG_OK:
+        raise PcgError(s, "pcg_create")
+    return out.value
+
+
+def pcg_destroy(ctx) -> None:
+    lib().pcg_destroy(ctx)
+
+
+def pcg_set_stream(ctx, stream_ptr: int) -> int:
+    return lib().pcg_set_stream(ctx, stream_ptr)
+
+
+def pcg_solve(ctx, b, x0, method, sigma, tol, maxit, precision, x_out, res) -> int:
+    return lib().pcg_solve(ctx, _p(b), _p(x0), method, sigma, tol, maxit, precision, _p(x_out),
+                           ctypes.byref(res) if res is not None else None)
+
+
+def pcg_solve_device(ctx, b, x0, method, sigma, tol, maxit, precision, x_out, res) -> int:
+    return lib().pcg_solve_device(ctx, _p(b), _p(x0), method, sigma, tol, maxit, precision, _p(x_out),
+                                  ctypes.byref(res) if res is not None else None)
+
+
+def pcg_psi(ctx, alpha: np.ndarray, beta: np.ndarray, i: int, grid: np.ndarray) -> np.ndarray:
+    alpha = np.ascontiguousarray(alpha, dtype=np.float64)
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    grid = np.ascontiguousarray(grid, dtype=np.float64)
+    out = np.empty(grid.size)
+    s = lib().pcg_psi(ctx, _p(alpha), _p(beta), i, _p(grid), grid.size, _p(out))
+    if s != PCG_OK:
+        raise PcgError(s, pcg_last_error(ctx))
+    return out
+
+
+def pcg_select_sigma(ctx, b: np.ndarray, iters: int, grid) -> tuple[float, np.ndarray]:
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    grid = np.ascontiguousarray(grid, dtype=np.float64)
+    sig = ctypes.c_double()
+    psi = np.empty(grid.size)
+    s = lib().pcg_select_sigma(ctx, _p(b), iters, _p(grid), grid.size, ctypes.byref(sig), _p(psi))
+    if s != PCG_OK:
+        raise PcgError(s, pcg_last_error(ctx))
+    return sig.value, psi
+
+
+def pcg_kernel_stats(ctx) -> tuple[int, int, float]:
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+    s = lib().pcg_kernel_stats(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    if s != PCG_OK:
+        raise PcgError(s)
+    return a.value, b.value, c.value
+
+
+def pcg_kernel_stats_reset(ctx) -> None:
+    lib().pcg_kernel_stats_reset(ctx)
+
+
+# ---------------------------------------------------------------- convenience
+
+class Matrix:
+    """pcg_matrix built from a problem description (duck-typed: layout, nx, ny,
+    nz, diag/ax/ay/az or row_ptr/col/val), keeping its arrays alive."""
+
+    def __init__(self, P, device_arrays: Optional[dict] = None):
+        self.keep = []
+        m = pcg_matrix()
+        m.layout = P.layout
+
+        def arr(a, dt):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=dt)
+            self.keep.append(a)
+            return a.ctypes.data
+
+        if device_arrays is not None:      # torch tensors on the GPU
+            self.keep.append(device_arrays)
+            arr = lambda a, dt: None if a is None else _p(a)  # noqa: E731
+            src = device_arrays
+        else:
+            src = {k: getattr(P, k) for k in ("diag", "ax", "ay", "az", "row_ptr", "col", "val")}
+        if P.layout == PCG_CSR32:
+            m.n, m.nnz = P.n, int(P.row_ptr[-1])
+            m.row_ptr, m.col, m.val = arr(src["row_ptr"], np.int32), arr(src["col"], np.int32), arr(src["val"], np.float64)
+        else:
+            m.nx, m.ny, m.nz = P.nx, P.ny, P.nz
+            if src.get("diag") is not None:
+                m.diag, m.ax, m.ay = arr(src["diag"], np.float64), arr(src["ax"], np.float64), arr(src["ay"], np.float64)
+                if P.layout == PCG_STENCIL7_3D:
+                    m.az = arr(src["az"], np.float64)
+        self.m = m
+
+
+@dataclass
+class SolveResult:
+    x: object
+    iters: int
+    status: int
+    final_true_relres: float
+    final_rec_relres: float
+    rec: np.ndarray
+    true: np.ndarray
+    gap: np.ndarray
+    alpha: np.ndarray
+    beta: np.ndarray
+
+
+class Solver:
+    """One pcg_ctx for one operator."""
+
+    def __init__(self, P, flags: int = 0, device_arrays: Optional[dict] = None):
+        self.P = P
+        self.n = P.n
+        self.mat = Matrix(P, device_arrays)
+        self.ctx = pcg_create(self.mat.m, flags | (PCG_DEVICE_PTRS if device_arrays is not None else 0))
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            pcg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def solve(self, b, x0=None, method="spcg", sigma=0.0, tol=0.0, maxit=100, true_every=0, device=False,
+              x_out=None, raise_on_error=True) -> SolveResult:
+        """b/x0/x_out: numpy arrays (host) or, with device=True, CUDA tensors."""
+        m = METHODS[method] if isinstance(method, str) else method
+        k = maxit + 1
+        hist = {name: np.full(k, np.nan) for name in ("rec", "true", "gap", "alpha", "beta")}
+        res = pcg_result()
+        res.rec_hist, res.true_hist, res.gap_hist = _p(hist["rec"]), _p(hist["true"]), _p(hist["gap"])
+        res.alpha_hist, res.beta_hist = _p(hist["alpha"]), _p(hist["beta"])
+        res.true_every = true_every
+        if device:
+            if x_out is None:
+                import torch
+                x_out = torch.empty(self.n, dtype=torch.float64, device=b.device)
+            s = pcg_solve_device(self.ctx, b, x0, m, sigma, tol, maxit, PCG_FP64, x_out, res)
+        else:
+            b = np.ascontiguousarray(b, dtype=np.float64)
+            x0 = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
+            if x_out is None:
+                x_out = np.empty(self.n)
+            s = pcg_solve(self.ctx, b, x0, m, sigma, tol, maxit, PCG_FP64, x_out, res)
+        if s not in (PCG_OK, PCG_ENOTCONV, PCG_EBREAKDOWN) and raise_on_error:
+            raise PcgError(s, pcg_last_error(self.ctx))
+        it = res.iters
+        return SolveResult(x_out, it, s, res.final_true_relres, res.final_rec_relres, hist["rec"][:it + 1],
+                           hist["true"][:it + 1], hist["gap"][:it + 1], hist["alpha"][:it], hist["beta"][:it])

@@ -1,0 +1,78 @@
+"""The C-ABI library builds, loads and exports every symbol include/pcg.h declares;
+argument checks that run before any CUDA call behave as documented (CPU only)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pcg.h")
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1706_05988_gb300 import build
+    return build.build()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(pcg_[a-z_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("pcg_create", "pcg_solve", "pcg_solve_device", "pcg_destroy", "pcg_select_sigma",
+                     "pcg_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.check_output(["nm", "-D", "--defined-only", libpath]).decode()
+    exported = set(re.findall(r"\sT\s(pcg_[a-z_]+)$", out, flags=re.M))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    lib = ctypes.CDLL(libpath)
+    for n in declared_functions():
+        assert getattr(lib, n) is not None
+
+
+def test_header_compiles_as_c(tmp_path):
+    c = tmp_path / "t.c"
+    c.write_text('#include "pcg.h"\nint main(void){pcg_result r; pcg_matrix m; (void)r; (void)m; return 0;}\n')
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.dirname(HEADER), "-c", str(c),
+                           "-o", str(tmp_path / "t.o")])
+
+
+def test_argument_errors_without_gpu(libpath):
+    from paper_1706_05988_gb300 import pcg as B
+    L = B.lib()
+    assert "libpcg" in B.pcg_version()
+    out = ctypes.c_void_p(1)
+    assert L.pcg_create(None, 0, ctypes.byref(out)) == B.PCG_EINVAL and out.value is None
+    m = B.pcg_matrix()
+    m.layout = 7
+    assert L.pcg_create(ctypes.byref(m), 0, ctypes.byref(out)) == B.PCG_EINVAL
+    m.layout = B.PCG_STENCIL5_2D
+    m.nx, m.ny, m.nz = 0, 4, 1
+    assert L.pcg_create(ctypes.byref(m), 0, ctypes.byref(out)) == B.PCG_EINVAL
+    m.nx, m.ny, m.nz = 1 << 16, 1 << 16, 1
+    assert L.pcg_create(ctypes.byref(m), 0, ctypes.byref(out)) == B.PCG_EINVAL      # beyond int32 indexing
+    m.nx, m.ny = 4, 4
+    assert L.pcg_create(ctypes.byref(m), 0x100, ctypes.byref(out)) == B.PCG_EINVAL  # unknown flag
+    m.layout = B.PCG_CSR32
+    m.n, m.nnz = 3, 2
+    rp = (ctypes.c_int32 * 4)(0, 1, 1, 2)
+    col = (ctypes.c_int32 * 2)(0, 5)                                                 # column out of range
+    val = (ctypes.c_double * 2)(1.0, 1.0)
+    m.row_ptr, m.col, m.val = ctypes.addressof(rp), ctypes.addressof(col), ctypes.addressof(val)
+    assert L.pcg_create(ctypes.byref(m), 0, ctypes.byref(out)) == B.PCG_EINVAL
+    assert L.pcg_solve(None, None, None, 2, 0.0, 0.0, 1, 0, None, None) == B.PCG_EINVAL
+    assert L.pcg_select_sigma(None, None, 10, None, 1, None, None) == B.PCG_EINVAL
+    assert L.pcg_kernel_stats(None, None, None, None) == B.PCG_EINVAL
+    L.pcg_destroy(None)
+    assert B.pcg_last_error(None) == "null context"

@@ -1,0 +1,342 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (GB300 only).
+
+Tolerances (fixed by the method's target): alpha_i, beta_i within 1e-10
+relative over the first 20 iterations; final true relative residual within a
+factor 10 of the oracle's.  The two sides sum in different orders (the GPU
+uses FMA and a two-level tree reduction), so nothing is compared bit for bit
+except properties that are exact on the GPU side itself (determinism, the
+sigma = 0 path, host vs device entry points).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+TOL_SCALARS = 1e-10
+N_SCALARS = 20
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1706_05988_gb300 import build
+    build.build()
+    import paper_1706_05988_gb300 as pkg
+    return pkg
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300))
+
+
+def check_scalars(g, o, k=N_SCALARS, tol=TOL_SCALARS):
+    k = min(k, len(o.alpha), len(g.alpha))
+    assert k > 0
+    assert rel(g.alpha[:k], o.alpha[:k]) <= tol, (g.alpha[:k], o.alpha[:k])
+    assert rel(g.beta[1:k], o.beta[1:k]) <= tol
+    assert g.beta[0] == 0.0
+
+
+def check_final(g, o, bnorm):
+    gt = g.final_true_relres
+    ot = o.true[-1] / bnorm
+    assert 0.1 * ot <= gt <= 10 * ot, (gt, ot)
+
+
+def run_both(B, P, b, method, sigma, maxit, tol=0.0, x0=None):
+    with B.Solver(P) as s:
+        g = s.solve(b, x0=x0, method=method, sigma=sigma, tol=tol, maxit=maxit, true_every=1)
+    if method == "cg":
+        o = oracle.cg(P, b, x0=x0, maxit=maxit, rtol=tol, log_every=1)
+    else:
+        o = oracle.pcg_sh(P, b, x0=x0, sigma=sigma if method == "spcg" else 0.0, maxit=maxit, rtol=tol, log_every=1)
+    return g, o
+
+
+# ---------------------------------------------------------------- 2D Poisson 100x100 (n = 10,000)
+
+@pytest.mark.parametrize("method,sigma", [("cg", 0.0), ("pcg", 0.0), ("spcg", 4.0)])
+def test_poisson2d_100(B, method, sigma):
+    P, b, xs = S.poisson2d_manufactured(100)
+    g, o = run_both(B, P, b, method, sigma, maxit=600)
+    assert g.iters == o.iters == 600
+    check_scalars(g, o)
+    check_final(g, o, np.linalg.norm(b))
+    # recursive residual history follows the oracle's while far above rounding level
+    m = o.rec > 1e-6 * o.rec[0]
+    assert rel(g.rec[m], o.rec[m]) < 1e-4
+    # true residual and gap histories are logged at every iteration
+    assert np.all(np.isfinite(g.true)) and np.all(np.isfinite(g.gap))
+
+
+def test_poisson2d_100_accuracy_ordering(B):
+    """Attainable accuracy: CG and p-CG-sh reach ~1e-13 relative; the gap of p-CG-sh stays CG-like."""
+    P, b, xs = S.poisson2d_manufactured(100)
+    bn = np.linalg.norm(b)
+    with B.Solver(P) as s:
+        cg = s.solve(b, method="cg", maxit=2000, true_every=10)
+        sh = s.solve(b, method="spcg", sigma=4.0, maxit=2000, true_every=10)
+        pc = s.solve(b, method="pcg", maxit=2000, true_every=10)
+    assert cg.final_true_relres < 1e-13
+    assert sh.final_true_relres < 10 * cg.final_true_relres
+    assert np.nanmax(sh.gap) / bn < 1e-12
+    assert pc.final_true_relres > 3 * cg.final_true_relres   # p-CG loses accuracy (or breaks down)
+
+
+# ---------------------------------------------------------------- lapl200 (Table 1)
+
+def test_lapl200_table1(B):
+    P, b = S.lapl200()
+    with B.Solver(P) as s:
+        cg = s.solve(b, method="cg", maxit=500)
+        sh = s.solve(b, method="spcg", sigma=4.0, maxit=500)
+    for r in (cg, sh):
+        assert r.iters == 500
+        assert 3e-12 <= r.final_true_relres <= 1.4e-11       # Table 1: 6.8e-12 (||b|| = 1)
+    o = oracle.pcg_sh(P, b, sigma=4.0, maxit=500, log_every=0)
+    check_scalars(sh, o)
+
+
+# ---------------------------------------------------------------- operators and shapes
+
+SHAPES = [
+    ("2d_odd", lambda: S.laplacian_2d(37, 23)),
+    ("2d_row", lambda: S.laplacian_2d(1, 9)),
+    ("2d_col", lambda: S.laplacian_2d(64, 1)),
+    ("3d_even", lambda: S.laplacian_3d(20, 18, 16)),
+    ("3d_odd", lambda: S.laplacian_3d(15, 17, 9)),
+    ("3d_flat", lambda: S.laplacian_3d(12, 10, 1)),
+    ("var2d", lambda: S.varcoef_2d(48, 40, seed=1)),
+    ("var2d_odd", lambda: S.varcoef_2d(33, 21, seed=2)),
+    ("var3d", lambda: S.varcoef_3d(24, block=8, seed=3)),
+    ("var3d_odd", lambda: S.varcoef_3d(17, block=4, seed=4)),
+    ("csr_lapl3d", lambda: S.to_csr(S.laplacian_3d(18, 14, 10))),
+    ("csr_var2d", lambda: S.to_csr(S.varcoef_2d(30, 26, seed=5))),
+]
+
+
+def shift_for(P):
+    """A shift inside the spectrum: half the median diagonal entry."""
+    c = S.to_csr(P)
+    rows = np.repeat(np.arange(c.n), np.diff(c.row_ptr))
+    return 0.5 * float(np.median(c.val[c.col == rows]))
+
+
+@pytest.mark.parametrize("name,maker", SHAPES, ids=[s[0] for s in SHAPES])
+@pytest.mark.parametrize("method", ["cg", "spcg"])
+def test_shapes_vs_oracle(B, name, maker, method):
+    P = maker()
+    b = S.normal(7, P.n)
+    bn = np.linalg.norm(b)
+    sigma = shift_for(P) if method == "spcg" else 0.0
+    maxit = min(60, P.n)
+    g, o = run_both(B, P, b, method, sigma, maxit)
+    assert g.iters == o.iters
+    # tiny systems reach rounding level quickly: compare scalars while the residual is well above it
+    live = int(np.sum(o.rec[:min(N_SCALARS, o.iters)] > 1e-9 * o.rec[0]))
+    if live > 0:
+        check_scalars(g, o, k=live)
+    if o.true[-1] > 1e-12 * bn:
+        check_final(g, o, bn)
+    else:
+        assert g.final_true_relres < 1e-11
+    assert np.linalg.norm(g.x - o.x) <= 1e-8 * np.linalg.norm(o.x)
+
+
+def test_random_sdd_csr(B):
+    rng = np.random.default_rng(3)
+    n = 5000
+    rows, cols = [], []
+    for i in range(n):
+        k = rng.integers(3, 13)
+        js = rng.integers(0, n, size=k)
+        js = js[js != i]
+        rows += [i] * len(js)
+        cols += list(js)
+    import scipy.sparse as sp
+    U = sp.coo_matrix((-rng.random(len(rows)), (rows, cols)), shape=(n, n)).tocsr()
+    A = (U + U.T).tocsr()
+    A.sum_duplicates()
+    d = np.asarray(np.abs(A).sum(axis=1)).ravel() * 1.01 + 1e-3
+    A = (A + sp.diags(d)).tocsr()
+    A.sort_indices()
+    P = S.Problem(S.CSR32, row_ptr=A.indptr.astype(np.int32), col=A.indices.astype(np.int32),
+                  val=A.data.astype(np.float64), n_csr=n)
+    b = S.normal(9, n)
+    g, o = run_both(B, P, b, "spcg", float(np.median(d)) * 0.5, maxit=80)
+    check_scalars(g, o)
+    check_final(g, o, np.linalg.norm(b))
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_single_unknown(B):
+    P = S.laplacian_2d(1, 1)            # A = [4]
+    b = np.array([3.0])
+    with B.Solver(P) as s:
+        r = s.solve(b, method="spcg", sigma=1.0, tol=1e-15, maxit=5)
+    assert r.status == B.PCG_OK and r.iters == 1
+    assert abs(r.x[0] - 0.75) <= 1e-15
+
+
+def test_zero_rhs_converges_immediately(B):
+    P = S.laplacian_3d(8)
+    with B.Solver(P) as s:
+        r = s.solve(np.zeros(P.n), method="spcg", sigma=6.0, tol=1e-10, maxit=50)
+    assert r.status == B.PCG_OK and r.iters == 0 and np.all(r.x == 0)
+
+
+def test_maxit_zero(B):
+    P, b, _ = S.poisson2d_manufactured(16)
+    with B.Solver(P) as s:
+        r = s.solve(b, method="spcg", sigma=4.0, maxit=0)
+    assert r.status == B.PCG_ENOTCONV and r.iters == 0 and np.all(r.x == 0)
+    assert abs(r.final_true_relres - 1.0) < 1e-15
+
+
+def test_nonzero_initial_guess(B):
+    P, b, xs = S.poisson2d_manufactured(40)
+    x0 = S.uniform_pm1(3, P.n)
+    g, o = run_both(B, P, b, "spcg", 4.0, maxit=50, x0=x0)
+    check_scalars(g, o)
+    np.testing.assert_allclose(g.x, o.x, rtol=1e-9, atol=1e-12)
+
+
+def test_tolerance_stop_matches_oracle(B):
+    P, b, xs = S.poisson2d_manufactured(64)
+    g, o = run_both(B, P, b, "spcg", 4.0, maxit=2000, tol=1e-9)
+    assert g.status == B.PCG_OK and o.status == 1
+    assert abs(g.iters - o.iters) <= 1
+    assert g.final_rec_relres <= 1e-9
+
+
+def test_breakdown_on_indefinite(B):
+    """An indefinite matrix gives non-positive curvature: the solve stops with EBREAKDOWN."""
+    n = 64
+    d = np.ones(n)
+    d[::2] = -1.0
+    P = S.Problem(S.CSR32, row_ptr=np.arange(n + 1, dtype=np.int32), col=np.arange(n, dtype=np.int32),
+                  val=d, n_csr=n)
+    b = np.ones(n)
+    with B.Solver(P) as s:
+        r = s.solve(b, method="spcg", sigma=0.5, maxit=10)
+        c = s.solve(b, method="cg", maxit=10)
+    assert r.status == B.PCG_EBREAKDOWN
+    assert c.status == B.PCG_EBREAKDOWN
+    o = oracle.pcg_sh(P, b, sigma=0.5, maxit=10)
+    assert o.status == 2 and o.iters == r.iters
+
+
+def test_invalid_arguments(B):
+    P, b, _ = S.poisson2d_manufactured(8)
+    from paper_1706_05988_gb300 import pcg as C
+    with B.Solver(P) as s:
+        x = np.empty(P.n)
+        assert C.pcg_solve(s.ctx, b, None, 2, -1.0, 0.0, 5, 0, x, None) == C.PCG_EINVAL       # sigma < 0
+        assert C.pcg_solve(s.ctx, b, None, 2, float("nan"), 0.0, 5, 0, x, None) == C.PCG_EINVAL
+        assert C.pcg_solve(s.ctx, b, None, 9, 0.0, 0.0, 5, 0, x, None) == C.PCG_EINVAL
+        assert C.pcg_solve(s.ctx, b, None, 2, 0.0, -1.0, 5, 0, x, None) == C.PCG_EINVAL
+        assert C.pcg_solve(s.ctx, b, None, 2, 0.0, 0.0, -1, 0, x, None) == C.PCG_EINVAL
+        assert C.pcg_solve(s.ctx, b, None, 2, 0.0, 0.0, 5, 1, x, None) == C.PCG_ENOTIMPL
+        # the context stays usable after rejected calls
+        r = s.solve(b, method="spcg", sigma=4.0, maxit=5)
+        assert r.iters == 5
+
+
+# ---------------------------------------------------------------- properties of the GPU path itself
+
+def test_deterministic_and_pcg_is_sigma0(B):
+    P, b, _ = S.poisson3d_manufactured(32)
+    with B.Solver(P) as s:
+        a = s.solve(b, method="spcg", sigma=0.0, maxit=100)
+        a2 = s.solve(b, method="spcg", sigma=0.0, maxit=100)
+        p = s.solve(b, method="pcg", sigma=3.0, maxit=100)      # sigma ignored by p-CG
+    assert np.array_equal(a.x, a2.x) and np.array_equal(a.alpha, a2.alpha)
+    assert np.array_equal(a.x, p.x) and np.array_equal(a.rec, p.rec)
+
+
+def test_device_entry_point_matches_host(B):
+    import torch
+    P, b, _ = S.poisson3d_manufactured(24)
+    with B.Solver(P) as s:
+        h = s.solve(b, method="spcg", sigma=6.0, maxit=40)
+        db = torch.from_numpy(b).cuda()
+        d = s.solve(db, method="spcg", sigma=6.0, maxit=40, device=True)
+        # a misaligned device b (offset by one element) is copied internally
+        buf = torch.empty(P.n + 1, dtype=torch.float64, device="cuda")
+        buf[1:] = db
+        d2 = s.solve(buf[1:], method="spcg", sigma=6.0, maxit=40, device=True)
+    assert np.array_equal(h.x, d.x.cpu().numpy())
+    assert np.array_equal(h.x, d2.x.cpu().numpy())
+
+
+def test_device_matrix_pointers(B):
+    import torch
+    P = S.varcoef_3d(16, block=4, seed=8)
+    dev = {k: torch.from_numpy(getattr(P, k)).cuda() for k in ("diag", "ax", "ay", "az")}
+    b = S.normal(4, P.n)
+    with B.Solver(P) as s1, B.Solver(P, device_arrays=dev) as s2:
+        r1 = s1.solve(b, method="spcg", sigma=1.0, maxit=30)
+        r2 = s2.solve(b, method="spcg", sigma=1.0, maxit=30)
+    assert np.array_equal(r1.x, r2.x)
+
+
+# ---------------------------------------------------------------- shift selection
+
+def test_psi_matches_oracle(B):
+    from oracle import psi as PS
+    P, b = S.lapl200()
+    o = oracle.pcg_sh(P, b, sigma=4.0, maxit=301, log_every=0)
+    grid = np.array([0.0, 1.0, 2.0, 4.0, 6.0, 7.5, 9.0])
+    with B.Solver(P) as s:
+        from paper_1706_05988_gb300 import pcg as C
+        g = C.pcg_psi(s.ctx, o.alpha, o.beta, 300, grid)
+    ref = np.array([PS.psi(o.alpha, o.beta, 300, sg) for sg in grid])
+    fin = np.isfinite(ref) & (ref < 1e100)
+    assert rel(g[fin], ref[fin]) < 1e-9
+    assert np.all(g[~fin] > 1e100)
+
+
+def test_select_sigma_lapl200(B):
+    P, b = S.lapl200()
+    with B.Solver(P) as s:
+        from paper_1706_05988_gb300 import pcg as C
+        sg, psi = C.pcg_select_sigma(s.ctx, b, 300, np.linspace(0.5, 8.0, 16))
+    assert sg == 4.0
+
+
+# ---------------------------------------------------------------- full size: 256^3 stencil (n = 16.8M)
+
+@pytest.fixture(scope="module")
+def big():
+    P, b, xs = S.poisson3d_manufactured(256)
+    return P, b
+
+
+def test_full_size_first_iterations_vs_oracle(B, big):
+    """Same launch configuration as the benchmark; the oracle runs 4 iterations at full size."""
+    P, b = big
+    with B.Solver(P) as s:
+        g = s.solve(b, method="spcg", sigma=6.0, maxit=4, true_every=0)
+    o = oracle.pcg_sh(P, b, sigma=6.0, maxit=4, log_every=0)
+    check_scalars(g, o, k=4)
+    idx = np.random.default_rng(0).integers(0, P.n, 20000)
+    np.testing.assert_allclose(g.x[idx], o.x[idx], rtol=1e-11, atol=1e-13 * np.abs(o.x).max())
+
+
+def test_full_size_1000_iterations_properties(B, big):
+    """1,000 iterations at 256^3: the residual falls steadily and the gap stays at rounding level."""
+    P, b = big
+    with B.Solver(P) as s:
+        g = s.solve(b, method="spcg", sigma=6.0, maxit=1000, true_every=250)
+    assert g.iters == 1000
+    assert np.all(np.diff(g.rec[::50]) < 0)
+    assert g.final_true_relres < 1e-3
+    bn = np.linalg.norm(b)
+    assert np.nanmax(g.gap) / bn < 1e-12
+    assert abs(g.final_true_relres - g.final_rec_relres) < 1e-10
