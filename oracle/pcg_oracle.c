@@ -31,7 +31,8 @@
  * Index conventions (both methods): alpha[i], beta[i] are the scalars used in
  * iteration i (beta[0] = 0); rec[i] = ||r_i||_2 (recursive residual);
  * tru[i] = ||b - A x_i||_2 and gap[i] = ||(b - A x_i) - r_i||_2 when i is a
- * multiple of log_every (NaN otherwise; log_every <= 0 disables them).
+ * multiple of log_every and at the final iterate (NaN otherwise; log_every <= 0
+ * disables them).
  */
 #include <math.h>
 #include <stdint.h>
@@ -169,8 +170,8 @@ int oracle_cg(const oracle_op *A, const double *minv, const double *b, double *x
     if (want_log(i, log_every)) log_true(A, b, x, r, work, tru ? &tru[i] : NULL, gap ? &gap[i] : NULL);
     if (rtol > 0 && oracle_nrm2(n, r) <= rtol * bnorm) { status = 1; break; }
     if (ttol > 0 && want_log(i, log_every) && tru && tru[i] <= ttol * bnorm) { status = 1; break; }
-    if (gamma == 0.0) { status = 1; break; }
     if (i >= maxit) break;
+    if (gamma == 0.0) { status = 1; break; }
     oracle_apply(A, p, s);                          /* s_i := A p_i */
     const double sp = oracle_dot(n, s, p);
     if (!(sp > 0.0) || !isfinite(sp)) { status = 2; break; }
@@ -185,6 +186,8 @@ int oracle_cg(const oracle_op *A, const double *minv, const double *b, double *x
     for (int64_t j = 0; j < n; ++j) p[j] = u[j] + bt * p[j];
     gamma = gamma_new;
   }
+  if (log_every > 0 && !want_log(i, log_every))   /* the final iterate is always logged */
+    log_true(A, b, x, r, work, tru ? &tru[i] : NULL, gap ? &gap[i] : NULL);
   if (info) { info->iters = i; info->status = status; }
   free(r); free(u); free(p); free(s); free(work);
   return 0;
@@ -253,6 +256,8 @@ int oracle_pcg_sh(const oracle_op *A, const double *minv, const double *b, doubl
     gamma_prev = gamma;
     alpha_prev = a;
   }
+  if (log_every > 0 && !want_log(i, log_every))   /* the final iterate is always logged */
+    log_true(A, b, x, r, work, tru ? &tru[i] : NULL, gap ? &gap[i] : NULL);
   if (info) { info->iters = i; info->status = status; }
   if (state) {
     const size_t bytes = (size_t)n * sizeof(double);
@@ -321,6 +326,8 @@ int oracle_pcg(const oracle_op *A, const double *minv, const double *b, double *
     gamma_prev = gamma;
     alpha_prev = a;
   }
+  if (log_every > 0 && !want_log(i, log_every))   /* the final iterate is always logged */
+    log_true(A, b, x, r, work, tru ? &tru[i] : NULL, gap ? &gap[i] : NULL);
   if (info) { info->iters = i; info->status = status; }
   free(r); free(u); free(w); free(m); free(nn); free(z); free(q); free(s); free(t); free(p); free(work);
   return 0;

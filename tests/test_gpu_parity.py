@@ -64,12 +64,19 @@ def run_both(B, P, b, method, sigma, maxit, tol=0.0, x0=None):
 def test_poisson2d_100(B, method, sigma):
     P, b, xs = S.poisson2d_manufactured(100)
     g, o = run_both(B, P, b, method, sigma, maxit=600)
-    assert g.iters == o.iters == 600
+    if method == "pcg":
+        # unshifted p-CG loses its way after stagnating and stops on a non-positive 1/alpha; where exactly
+        # depends on rounding (the oracle stops at 415), so compare the outcome, not the iteration count
+        assert g.status == B.PCG_EBREAKDOWN and o.status == 2
+        assert abs(g.iters - o.iters) <= 100
+    else:
+        assert g.iters == o.iters == 600
     check_scalars(g, o)
     check_final(g, o, np.linalg.norm(b))
     # recursive residual history follows the oracle's while far above rounding level
-    m = o.rec > 1e-6 * o.rec[0]
-    assert rel(g.rec[m], o.rec[m]) < 1e-4
+    k = min(len(g.rec), len(o.rec))
+    m = o.rec[:k] > 1e-6 * o.rec[0]
+    assert rel(g.rec[:k][m], o.rec[:k][m]) < 1e-4
     # true residual and gap histories are logged at every iteration
     assert np.all(np.isfinite(g.true)) and np.all(np.isfinite(g.gap))
 
@@ -130,15 +137,18 @@ def shift_for(P):
 @pytest.mark.parametrize("name,maker", SHAPES, ids=[s[0] for s in SHAPES])
 @pytest.mark.parametrize("method", ["cg", "spcg"])
 def test_shapes_vs_oracle(B, name, maker, method):
+    """20 iterations: scalars and iterates.  High-contrast coefficients amplify rounding
+    differences later on (the oracle against itself with b perturbed in the last bit moves
+    x by ~1e-11 relative after 20 iterations but by up to 5e-3 after 60), so the iterate is
+    compared at 20 iterations."""
     P = maker()
     b = S.normal(7, P.n)
     bn = np.linalg.norm(b)
     sigma = shift_for(P) if method == "spcg" else 0.0
-    maxit = min(60, P.n)
+    maxit = min(20, P.n)
     g, o = run_both(B, P, b, method, sigma, maxit)
     assert g.iters == o.iters
-    # tiny systems reach rounding level quickly: compare scalars while the residual is well above it
-    live = int(np.sum(o.rec[:min(N_SCALARS, o.iters)] > 1e-9 * o.rec[0]))
+    live = int(np.sum(o.rec[:o.iters] > 1e-9 * o.rec[0]))
     if live > 0:
         check_scalars(g, o, k=live)
     if o.true[-1] > 1e-12 * bn:
@@ -146,6 +156,20 @@ def test_shapes_vs_oracle(B, name, maker, method):
     else:
         assert g.final_true_relres < 1e-11
     assert np.linalg.norm(g.x - o.x) <= 1e-8 * np.linalg.norm(o.x)
+
+
+@pytest.mark.parametrize("name,maker", [s for s in SHAPES if s[0] in ("2d_odd", "var2d_odd", "3d_odd", "csr_var2d")],
+                         ids=["2d_odd", "var2d_odd", "3d_odd", "csr_var2d"])
+def test_shapes_converged(B, name, maker):
+    """Run to ||r|| <= 1e-10 ||b||: same stopping iteration (to a few percent) and true residual."""
+    P = maker()
+    b = S.normal(7, P.n)
+    bn = np.linalg.norm(b)
+    sigma = shift_for(P)
+    g, o = run_both(B, P, b, "spcg", sigma, maxit=5000, tol=1e-10)
+    assert g.status == B.PCG_OK and o.status == 1
+    assert abs(g.iters - o.iters) <= 0.05 * o.iters + 2
+    check_final(g, o, bn)
 
 
 def test_random_sdd_csr(B):
