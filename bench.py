@@ -25,7 +25,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "p-CG iters/s & HBM GB/s (256³ FP64)"
 UNIT = "iter/s"
-N_SIDE = 256
+N_SIDE = 256                # overridable with --size (profiling captures use a smaller grid)
 ITERS_PER_STEP = 1000
 SIGMA = 6.0
 BYTES_PER_DOF = 96          # x, r, w, z, s, p: one FP64 read + one FP64 write each per iteration
@@ -289,7 +289,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--ref-iters", type=int, default=10, help="oracle iterations per sample")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timing")
+    ap.add_argument("--size", type=int, default=N_SIDE, help="grid side (default: the 256^3 workload)")
     args = ap.parse_args()
+    globals()["N_SIDE"] = args.size
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     return run_reference(args) if args.impl == "reference" else run_ours(args)
