@@ -57,6 +57,13 @@ typedef enum { PCG_FP64 = 0, PCG_MIXED_IR = 1 } pcg_precision;
 #define PCG_DEVICE_PTRS 0x1u   /* every array in pcg_matrix is a device pointer          */
 #define PCG_PROFILE 0x2u       /* time every launch of the fused iteration kernel with
                                   CUDA events (read back with pcg_kernel_stats)          */
+#define PCG_STENCIL_FP64_SUM 0x4u  /* constant-coefficient stencils: sum each row with FP64
+                                  additions instead of the default fixed-point row sum.
+                                  Default: the row C*w_c - sum(neighbours) is summed exactly
+                                  in 64-bit fixed point with 6 guard bits below the largest
+                                  term and rounded once to binary64; its error is at most
+                                  0.5 ulp of the result plus 6 * 2^-6 ulp of the largest
+                                  term, below the worst case of FP64 left-to-right summation */
 
 /*
  * The operator A.
@@ -133,6 +140,12 @@ pcg_status pcg_solve(pcg_ctx *ctx, const double *b, const double *x0, int32_t me
 /* pcg_solve with b, x0 (NULL = zero) and x_out given as device pointers. */
 pcg_status pcg_solve_device(pcg_ctx *ctx, const double *b, const double *x0, int32_t method, double sigma,
                             double tol, int32_t maxit, int32_t precision, double *x_out, pcg_result *res);
+
+/* y = A x with the context's operator, evaluated exactly as inside the solver
+ * (the SpMV of Algorithm 3, line "n_i := A m_i").  x and y are device arrays of
+ * n doubles that must not overlap (any alignment).  Errors: PCG_EINVAL for
+ * NULL pointers. */
+pcg_status pcg_apply(pcg_ctx *ctx, const double *x, double *y);
 
 /* Shift selection (Section 3.2, Eq. (functionpsi); Section 5.1): runs
  * Algorithm 2 (sigma = 0) for `iters` iterations on (A, b) -- b a host array --

@@ -158,9 +158,10 @@ pcg_status pcg_create(const pcg_matrix* A, uint32_t flags, pcg_ctx** out) {
   if (!out) return PCG_EINVAL;
   *out = nullptr;
   if (!A) return PCG_EINVAL;
-  if (flags & ~(PCG_DEVICE_PTRS | PCG_PROFILE)) return PCG_EINVAL;
+  if (flags & ~(PCG_DEVICE_PTRS | PCG_PROFILE | PCG_STENCIL_FP64_SUM)) return PCG_EINVAL;
   OpDesc op{};
   op.layout = A->layout;
+  op.fixed_sum = (flags & PCG_STENCIL_FP64_SUM) ? 0 : 1;
   int64_t n = 0, nnz = 0;
   if (A->layout == PCG_STENCIL5_2D || A->layout == PCG_STENCIL7_3D) {
     const int64_t nz = A->layout == PCG_STENCIL7_3D ? A->nz : 1;
@@ -434,6 +435,22 @@ pcg_status pcg_solve(pcg_ctx* c, const double* b, const double* x0, int32_t meth
 pcg_status pcg_solve_device(pcg_ctx* c, const double* b, const double* x0, int32_t method, double sigma, double tol,
                             int32_t maxit, int32_t precision, double* x_out, pcg_result* res) {
   return solve_common(c, b, x0, method, sigma, tol, maxit, precision, x_out, res, false);
+}
+
+pcg_status pcg_apply(pcg_ctx* c, const double* x, double* y) {
+  if (!c) return PCG_EINVAL;
+  c->err.clear();
+  if (!x || !y) return fail(c, PCG_EINVAL, "x and y must not be NULL");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  pcg_status s = ensure_vectors(c);
+  if (s != PCG_OK) return s;
+  const size_t bytes = (size_t)c->n * sizeof(double);
+  CUDA_TRY(c, cudaMemcpyAsync(c->v.w0, x, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  CUDA_TRY(c, launch_apply(c->op, launch_of(c, K_APPLY), c->v.w0, c->v.w1));
+  ++c->launches;
+  CUDA_TRY(c, cudaMemcpyAsync(y, c->v.w1, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return PCG_OK;
 }
 
 pcg_status pcg_psi(pcg_ctx* c, const double* alpha, const double* beta, int32_t i, const double* grid, int32_t ngrid,

@@ -6,9 +6,9 @@
 namespace pcgk {
 namespace {
 
-template <int DIM, bool VAR, int VEC>
-StencilOp<DIM, VAR, VEC> make_stencil(const OpDesc& d) {
-  StencilOp<DIM, VAR, VEC> o;
+template <int DIM, int MODE, int VEC>
+StencilOp<DIM, MODE, VEC> make_stencil(const OpDesc& d) {
+  StencilOp<DIM, MODE, VEC> o;
   o.n = d.n;
   o.nx = d.nx;
   o.ny = d.ny;
@@ -25,11 +25,13 @@ template <int DIM, class F>
 cudaError_t with_stencil(const OpDesc& d, F&& f) {
   const bool var = d.diag != nullptr;
   if (op_vec(d) == 2) {
-    if (var) return f(make_stencil<DIM, true, 2>(d));
-    return f(make_stencil<DIM, false, 2>(d));
+    if (var) return f(make_stencil<DIM, ST_VAR, 2>(d));
+    if (d.fixed_sum) return f(make_stencil<DIM, ST_LAP_FIXED, 2>(d));
+    return f(make_stencil<DIM, ST_LAP_FP64, 2>(d));
   }
-  if (var) return f(make_stencil<DIM, true, 1>(d));
-  return f(make_stencil<DIM, false, 1>(d));
+  if (var) return f(make_stencil<DIM, ST_VAR, 1>(d));
+  if (d.fixed_sum) return f(make_stencil<DIM, ST_LAP_FIXED, 1>(d));
+  return f(make_stencil<DIM, ST_LAP_FP64, 1>(d));
 }
 
 template <class F>
@@ -107,6 +109,9 @@ cudaError_t launch_cg_update(const OpDesc& d, const Launch& L, Vecs v, State* st
 }
 cudaError_t launch_cg_p(const OpDesc& d, const Launch& L, Vecs v, State* st, Hist h) {
   return with_op(d, [&](auto op) { return K<decltype(op)>::cg_p(op, L, v, st, h); });
+}
+cudaError_t launch_apply(const OpDesc& d, const Launch& L, const double* x, double* y) {
+  return with_op(d, [&](auto op) { return K<decltype(op)>::apply(op, L, x, y); });
 }
 
 }  // namespace pcgk

@@ -30,6 +30,7 @@ struct Hist {
 // variable coefficients) or a CSR matrix.  Device pointers.
 struct OpDesc {
   int layout;            // 0 = 2D stencil, 1 = 3D stencil, 2 = CSR
+  int fixed_sum;         // constant-coefficient stencil rows in fixed point (pcg_fixedsum.cuh)
   int n, nx, ny, nz;
   const double *diag, *ax, *ay, *az;   // variable coefficients; diag == nullptr: Laplacian
   const int *row_ptr, *col;
@@ -53,7 +54,7 @@ int op_vec(const OpDesc& op);
 
 // Resident-grid size of each kernel family for this operator (0 on error).
 int grid_for(const OpDesc& op, int kind, int block);
-enum { K_RESIDUAL = 0, K_SPCG_W0, K_SPCG_ITER, K_TRUE_RES, K_CG_P0, K_CG_SPMV, K_CG_UPDATE, K_CG_P, K_NKINDS };
+enum { K_RESIDUAL = 0, K_SPCG_W0, K_SPCG_ITER, K_TRUE_RES, K_CG_P0, K_CG_SPMV, K_CG_UPDATE, K_CG_P, K_APPLY, K_NKINDS };
 
 // Kernel launchers (asynchronous; return the launch error).
 cudaError_t launch_residual(const OpDesc& op, const Launch& L, const double* b, const double* x0, double* x, double* r,
@@ -65,6 +66,7 @@ cudaError_t launch_cg_p0(const OpDesc& op, const Launch& L, Vecs v, State* st, H
 cudaError_t launch_cg_spmv(const OpDesc& op, const Launch& L, Vecs v, State* st, Hist h, double* partials);
 cudaError_t launch_cg_update(const OpDesc& op, const Launch& L, Vecs v, State* st, Hist h, double* partials);
 cudaError_t launch_cg_p(const OpDesc& op, const Launch& L, Vecs v, State* st, Hist h);
+cudaError_t launch_apply(const OpDesc& op, const Launch& L, const double* x, double* y);
 
 // psi_i(sigma) for every shift of sig[ngrid]; alpha/beta device arrays (>= i+1 entries).
 cudaError_t launch_psi(const double* alpha, const double* beta, int i, const double* sig, int ngrid, double* psi,

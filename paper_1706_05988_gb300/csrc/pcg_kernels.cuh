@@ -14,6 +14,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "pcg_fixedsum.cuh"
 #include "pcg_internal.h"
 
 namespace pcgk {
@@ -26,9 +27,13 @@ constexpr int kWarps = kBlock / 32;
 // Cell-centred stencil on an nx x ny (x nz) grid with Dirichlet boundary.
 // Constant coefficients: (A w)_c = C w_c - sum of the in-grid neighbours,
 // C = 4 (2D) / 6 (3D).  Variable coefficients: see pcg_matrix in pcg.h.
-template <int DIM, bool VAR, int VEC_>
+// MODE: how a row is evaluated (see StencilMode).
+enum StencilMode { ST_LAP_FP64 = 0, ST_LAP_FIXED = 1, ST_VAR = 2 };
+
+template <int DIM, int MODE, int VEC_>
 struct StencilOp {
   static constexpr int VEC = VEC_;
+  static constexpr bool VAR = MODE == ST_VAR;
   int n, nx, ny, nz, nxny;
   const double *diag, *ax, *ay, *az;
 
@@ -63,7 +68,48 @@ struct StencilOp {
       xp[e] = e == VEC - 1 ? xr : c[e + 1];
       wc[e] = c[e];
     }
-    if (!VAR) {
+    if (MODE == ST_LAP_FIXED) {
+      // integer-pipe fixed-point rows (pcg_fixedsum.cuh); FP64 additions only as a fallback
+      FxRaw rc[VEC], rym[VEC], ryp[VEC], rzm[VEC], rzp[VEC];
+      const FxRaw rxl = fx_raw(xl), rxr = fx_raw(xr);
+      int special = rxl.special | rxr.special;
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        rc[e] = fx_raw(c[e]);
+        rym[e] = fx_raw(ym[e]);
+        ryp[e] = fx_raw(yp[e]);
+        special |= rc[e].special | rym[e].special | ryp[e].special;
+        if (DIM == 3) {
+          rzm[e] = fx_raw(zm[e]);
+          rzp[e] = fx_raw(zp[e]);
+          special |= rzm[e].special | rzp[e].special;
+        }
+      }
+      bool ok = !special;
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        FxTerm t[DIM == 3 ? 7 : 5];
+        t[0] = fx_centre<DIM>(rc[e]);
+        t[1] = fx_minus(e == 0 ? rxl : rc[e - 1]);
+        t[2] = fx_minus(e == VEC - 1 ? rxr : rc[e + 1]);
+        t[3] = fx_minus(rym[e]);
+        t[4] = fx_minus(ryp[e]);
+        if constexpr (DIM == 3) {
+          t[5] = fx_minus(rzm[e]);
+          t[6] = fx_minus(rzp[e]);
+        }
+        aw[e] = fx_sum(t, ok);
+      }
+      if (!ok) {
+        constexpr double C = DIM == 3 ? 6.0 : 4.0;
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+          double s = (xm[e] + xp[e]) + (ym[e] + yp[e]);
+          if (DIM == 3) s += zm[e] + zp[e];
+          aw[e] = fma(C, c[e], -s);
+        }
+      }
+    } else if (MODE == ST_LAP_FP64) {
       constexpr double C = DIM == 3 ? 6.0 : 4.0;
 #pragma unroll
       for (int e = 0; e < VEC; ++e) {
@@ -154,6 +200,7 @@ struct Kernels {
   static cudaError_t cg_spmv(const Op& op, const Launch& L, Vecs v, State* st, Hist h, double* partials);
   static cudaError_t cg_update(const Op& op, const Launch& L, Vecs v, State* st, Hist h, double* partials);
   static cudaError_t cg_p(const Op& op, const Launch& L, Vecs v, State* st, Hist h);
+  static cudaError_t apply(const Op& op, const Launch& L, const double* x, double* y);
   static int blocks_per_sm(int kind);
 };
 
@@ -391,7 +438,8 @@ __global__ void __launch_bounds__(kBlock) k_spcg_w0(Op op, Vecs v, State* st, Hi
 // One iteration of Algorithm 3 with M = I (u = r, q = s, t = p, m = w), fused:
 //   n_i = A w_i;  z_i = n_i + beta_i z_{i-1};  s_i = w_i + beta_i s_{i-1};
 //   p_i = r_i + beta_i p_{i-1};  x_{i+1} = x_i + alpha_i p_i;
-//   r_{i+1} = r_i - (alpha_i s_i + alpha_i sigma p_i);  w_{i+1} = w_i - alpha_i z_i;
+//   r_{i+1} = r_i - alpha_i s_i - alpha_i sigma p_i  (two fused multiply-adds, the shift
+//   term first);  w_{i+1} = w_i - alpha_i z_i;
 // and, in the same sweep, the partials of gamma_{i+1} = (r_{i+1}, r_{i+1}) and
 // (w_{i+1}, r_{i+1}); the last block turns them into alpha_{i+1}, beta_{i+1}.
 // w is double-buffered (neighbours read w_i while w_{i+1} is written).
@@ -421,7 +469,7 @@ __global__ void __launch_bounds__(kBlock) k_spcg_iter(Op op, Vecs v, State* st, 
       s[e] = fma(beta, s[e], wc[e]);
       p[e] = fma(beta, p[e], r[e]);
       x[e] = fma(alpha, p[e], x[e]);
-      const double rn = r[e] - fma(asg, p[e], alpha * s[e]);
+      const double rn = fma(-alpha, s[e], fma(-asg, p[e], r[e]));
       const double wv = fma(-alpha, z[e], wc[e]);
       r[e] = rn;
       w1[e] = wv;
@@ -563,6 +611,18 @@ __global__ void __launch_bounds__(kBlock) k_cg_p(int n, Vecs v, State* st, Hist 
   }
 }
 
+// y = A x (the row evaluation the solver kernels use).
+template <class Op>
+__global__ void __launch_bounds__(kBlock) k_apply(Op op, const double* __restrict__ x, double* __restrict__ y) {
+  constexpr int VEC = Op::VEC;
+  const int nu = op.units();
+  for (int u = blockIdx.x * kBlock + threadIdx.x; u < nu; u += gridDim.x * kBlock) {
+    double xc[VEC], ax[VEC];
+    op.apply(x, u, xc, ax);
+    st_plain<VEC>(y + u * VEC, ax);
+  }
+}
+
 // ---------------------------------------------------------------- launchers
 
 template <class Op>
@@ -607,6 +667,11 @@ cudaError_t Kernels<Op>::cg_p(const Op& op, const Launch& L, Vecs v, State* st, 
   return cudaGetLastError();
 }
 template <class Op>
+cudaError_t Kernels<Op>::apply(const Op& op, const Launch& L, const double* x, double* y) {
+  k_apply<Op><<<L.grid, L.block, 0, L.stream>>>(op, x, y);
+  return cudaGetLastError();
+}
+template <class Op>
 int Kernels<Op>::blocks_per_sm(int kind) {
   int nb = 0;
   cudaError_t e = cudaSuccess;
@@ -619,6 +684,7 @@ int Kernels<Op>::blocks_per_sm(int kind) {
     case K_CG_SPMV: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cg_spmv<Op>, kBlock, 0); break;
     case K_CG_UPDATE: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cg_update<Op::VEC>, kBlock, 0); break;
     case K_CG_P: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cg_p<Op::VEC>, kBlock, 0); break;
+    case K_APPLY: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_apply<Op>, kBlock, 0); break;
     default: return 0;
   }
   return e == cudaSuccess ? nb : 0;

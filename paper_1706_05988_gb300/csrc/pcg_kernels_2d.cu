@@ -1,10 +1,13 @@
-// Kernel instantiations for the 2D 5-point stencil operators.
+// Kernel instantiations for the 2D 5-point stencil operators (FP64-sum, fixed-point-sum and
+// variable-coefficient rows; one or two unknowns per thread).
 #define PCG_KERNELS_IMPL
 #include "pcg_kernels.cuh"
 
 namespace pcgk {
-template struct Kernels<StencilOp<2, false, 1>>;
-template struct Kernels<StencilOp<2, false, 2>>;
-template struct Kernels<StencilOp<2, true, 1>>;
-template struct Kernels<StencilOp<2, true, 2>>;
+template struct Kernels<StencilOp<2, ST_LAP_FP64, 1>>;
+template struct Kernels<StencilOp<2, ST_LAP_FP64, 2>>;
+template struct Kernels<StencilOp<2, ST_LAP_FIXED, 1>>;
+template struct Kernels<StencilOp<2, ST_LAP_FIXED, 2>>;
+template struct Kernels<StencilOp<2, ST_VAR, 1>>;
+template struct Kernels<StencilOp<2, ST_VAR, 2>>;
 }  // namespace pcgk

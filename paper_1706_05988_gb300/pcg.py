@@ -27,6 +27,7 @@ PCG_FP64, PCG_MIXED_IR = 0, 1
 # pcg_create flags
 PCG_DEVICE_PTRS = 0x1
 PCG_PROFILE = 0x2
+PCG_STENCIL_FP64_SUM = 0x4
 
 METHODS = {"cg": PCG_CG, "pcg": PCG_PCG, "spcg": PCG_SPCG}
 
@@ -74,11 +75,13 @@ def lib() -> ctypes.CDLL:
         L.pcg_solve_device.argtypes = solve_args
         L.pcg_select_sigma.argtypes = [vp, vp, i32, vp, i32, ctypes.POINTER(f64), vp]
         L.pcg_psi.argtypes = [vp, vp, vp, i32, vp, i32, vp]
+        L.pcg_apply.argtypes = [vp, vp, vp]
         L.pcg_kernel_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(f64)]
         L.pcg_kernel_stats_reset.argtypes = [vp]
         L.pcg_version.argtypes = []
         L.pcg_version.restype = ctypes.c_char_p
         for f in ("pcg_create", "pcg_set_stream", "pcg_solve", "pcg_solve_device", "pcg_select_sigma", "pcg_psi",
+                  "pcg_apply",
                   "pcg_kernel_stats", "pcg_kernel_stats_reset"):
             getattr(L, f).restype = st
         _lib = L
@@ -132,6 +135,11 @@ def pcg_solve(ctx, b, x0, method, sigma, tol, maxit, precision, x_out, res) -> i
 def pcg_solve_device(ctx, b, x0, method, sigma, tol, maxit, precision, x_out, res) -> int:
     return lib().pcg_solve_device(ctx, _p(b), _p(x0), method, sigma, tol, maxit, precision, _p(x_out),
                                   ctypes.byref(res) if res is not None else None)
+
+
+def pcg_apply(ctx, x, y) -> int:
+    """y = A x on the device (x, y: CUDA tensors or device addresses)."""
+    return lib().pcg_apply(ctx, _p(x), _p(y))
 
 
 def pcg_psi(ctx, alpha: np.ndarray, beta: np.ndarray, i: int, grid: np.ndarray) -> np.ndarray:

@@ -48,8 +48,8 @@ def check_final(g, o, bnorm):
     assert 0.1 * ot <= gt <= 10 * ot, (gt, ot)
 
 
-def run_both(B, P, b, method, sigma, maxit, tol=0.0, x0=None):
-    with B.Solver(P) as s:
+def run_both(B, P, b, method, sigma, maxit, tol=0.0, x0=None, flags=0):
+    with B.Solver(P, flags=flags) as s:
         g = s.solve(b, x0=x0, method=method, sigma=sigma, tol=tol, maxit=maxit, true_every=1)
     if method == "cg":
         o = oracle.cg(P, b, x0=x0, maxit=maxit, rtol=tol, log_every=1)
@@ -170,6 +170,17 @@ def test_shapes_converged(B, name, maker):
     assert g.status == B.PCG_OK and o.status == 1
     assert abs(g.iters - o.iters) <= 0.05 * o.iters + 2
     check_final(g, o, bn)
+
+
+@pytest.mark.parametrize("maker", [lambda: S.laplacian_3d(20, 18, 16), lambda: S.laplacian_2d(37, 23)],
+                         ids=["3d", "2d_odd"])
+def test_fp64_sum_rows_vs_oracle(B, maker):
+    """The FP64-addition stencil rows (PCG_STENCIL_FP64_SUM) against the oracle."""
+    P = maker()
+    b = S.normal(3, P.n)
+    g, o = run_both(B, P, b, "spcg", shift_for(P), 20, flags=B.PCG_STENCIL_FP64_SUM)
+    check_scalars(g, o)
+    assert np.linalg.norm(g.x - o.x) <= 1e-8 * np.linalg.norm(o.x)
 
 
 def test_random_sdd_csr(B):
