@@ -29,7 +29,7 @@ N_SIDE = 256                # overridable with --size (profiling captures use a 
 ITERS_PER_STEP = 1000
 SIGMA = 6.0
 BYTES_PER_DOF = 96          # x, r, w, z, s, p: one FP64 read + one FP64 write each per iteration
-FP64_OPS_PER_DOF = 16       # 6 DADD + 1 DMUL + 9 DFMA per unknown per fused iteration
+FP64_OPS_PER_DOF = 9        # DFMA per unknown per fused iteration (the stencil row runs on the integer pipe)
 FALLBACK_HBM_GBS = 6800.0
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_spcg_iter launch (ncu), keyed by the
@@ -271,8 +271,11 @@ def run_ours(args):
                 "config": workload_config(n),
                 "hbm_gbs_effective": alg_bytes * ITERS_PER_STEP * args.steps * world / (ms_max / 1e3) / 1e9 / world,
                 "roofline": roofline,
-                "fp64_pipe": {"achieved_tflops": fp64_tflops, "ops_per_dof": FP64_OPS_PER_DOF,
-                              "note": "FP64 instructions per unknown per iteration (FMA counted once)"},
+                "fp64_pipe": {"achieved_tinst_per_s": fp64_tflops, "ops_per_dof": FP64_OPS_PER_DOF,
+                              "peak_tinst_per_s": 2 * 152 * 2.07e9 / 1e12,
+                              "note": "FP64 thread-instructions per unknown per iteration; peak = 2 per cycle "
+                                      "per SM x 152 SMs x 2.07 GHz (ncu sm__sass_thread_inst_executed_op_dfma "
+                                      "peak_sustained)"},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -2,8 +2,8 @@
 flags) against exact rational arithmetic, and the FP64-addition row (flag
 PCG_STENCIL_FP64_SUM) against its textbook error bound (GB300 only).
 
-Exact reference: each row C*x_c - sum(neighbours) in Fractions; float(Fraction)
-is the correctly rounded binary64 value.  Bound for the fixed-point row:
+Exact reference: each row C*x_c - sum(neighbours) in Fractions (C*x_c exact);
+float(Fraction) is the correctly rounded binary64 value.  Bound for the fixed-point row:
 |y - exact| <= 0.5 ulp(y) + 6 * 2^-6 * ulp(largest term).  Bound for FP64
 left-to-right summation of k terms: (k - 1) * eps * sum |terms| (plus one rounding).
 """
@@ -33,19 +33,20 @@ def ulp(v: float) -> float:
 
 
 def rows(P, x):
-    """For every unknown: list of exact terms (C*x_c, -x_nb...) as floats (each exact)."""
-    C = 6.0 if P.is_3d else 4.0
+    """For every unknown: its exact terms C*x_c, -x_nb... as Fractions (C*x_c is not a
+    binary64 number in general, so it must not be formed in floating point)."""
+    C = 6 if P.is_3d else 4
     shape = (P.nz, P.ny, P.nx)
     X = x.reshape(shape)
     out = []
     for k in range(P.nz):
         for j in range(P.ny):
             for i in range(P.nx):
-                t = [C * X[k, j, i]]
+                t = [C * F(X[k, j, i])]
                 for dk, dj, di in ((0, 0, -1), (0, 0, 1), (0, -1, 0), (0, 1, 0), (-1, 0, 0), (1, 0, 0)):
                     kk, jj, ii = k + dk, j + dj, i + di
                     if 0 <= kk < P.nz and 0 <= jj < P.ny and 0 <= ii < P.nx:
-                        t.append(-X[kk, jj, ii])
+                        t.append(-F(X[kk, jj, ii]))
                 out.append(t)
     return out
 
@@ -90,9 +91,9 @@ def test_fixed_point_rows_vs_exact(B, gname, maker, kind):
     y = apply_gpu(B, P, x)
     exact_hits = 0
     for c, terms in enumerate(rows(P, x)):
-        ex = sum((F(t) for t in terms), F(0))
+        ex = sum(terms, F(0))
         rounded = float(ex)
-        big = max(abs(t) for t in terms)
+        big = float(max(abs(t) for t in terms))
         bound = F(0.5 * ulp(rounded)) + F(6) * F(2) ** -6 * F(ulp(big) if big > 0 else 0.0)
         if abs(rounded) < 2.2250738585072014e-308 * 4 or big > 1e300:
             bound += F(ulp(big)) * 8           # fallback rows: FP64 additions
@@ -109,9 +110,9 @@ def test_fp64_sum_rows_within_bound(B, gname, maker):
     y = apply_gpu(B, P, x, flags=B.PCG_STENCIL_FP64_SUM)
     eps = 2.0 ** -53
     for c, terms in enumerate(rows(P, x)):
-        ex = sum((F(t) for t in terms), F(0))
+        ex = sum(terms, F(0))
         k = len(terms)
-        bound = F((k - 1) * eps * 1.01) * sum((abs(F(t)) for t in terms), F(0)) + F(0.5 * ulp(float(ex)))
+        bound = F((k - 1) * eps * 1.01) * sum((abs(t) for t in terms), F(0)) + F(0.5 * ulp(float(ex)))
         assert abs(F(y[c]) - ex) <= bound
 
 
