@@ -264,6 +264,32 @@ def run_ours(args):
                          f"FP64 oracle ({dt:.1f} s)"}
 
     solver.close()
+
+    # the same workload as CSR (int32 indices): config's second form, one timed step
+    csr = None
+    if not args.no_csr:
+        Pc = S.to_csr(P)
+        bytes_csr = BYTES_PER_DOF * n + 12 * Pc.nnz + 4 * (n + 1)
+        with pkg.Solver(Pc, flags=C.PCG_PROFILE) as sc:
+            C.pcg_set_stream(sc.ctx, stream.cuda_stream)
+            for _ in range(2):
+                s = C.pcg_solve_device(sc.ctx, b_dev, None, C.PCG_SPCG, SIGMA, 0.0, ITERS_PER_STEP, C.PCG_FP64,
+                                       x_dev, None)
+                assert s == C.PCG_ENOTCONV, C.pcg_last_error(sc.ctx)
+            C.pcg_kernel_stats_reset(sc.ctx)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            s = C.pcg_solve_device(sc.ctx, b_dev, None, C.PCG_SPCG, SIGMA, 0.0, ITERS_PER_STEP, C.PCG_FP64, x_dev, None)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            assert s == C.PCG_ENOTCONV
+            _, il, ims = C.pcg_kernel_stats(sc.ctx)
+            k_s = ims / il / 1e3
+            csr = {"value": ITERS_PER_STEP / (ev0.elapsed_time(ev1) / 1e3), "unit": UNIT, "nnz": Pc.nnz,
+                   "kernel_avg_ms": k_s * 1e3, "algorithmic_bytes_per_launch": bytes_csr,
+                   "achieved_gbs": bytes_csr / k_s / 1e9, "frac": bytes_csr / k_s / 1e9 / peak}
+        del Pc
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -276,7 +302,8 @@ def run_ours(args):
                               "note": "FP64 thread-instructions per unknown per iteration; peak = 2 per cycle "
                                       "per SM x 152 SMs x 2.07 GHz (ncu sm__sass_thread_inst_executed_op_dfma "
                                       "peak_sustained)"},
-                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary()}
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
+                "csr_int32": csr}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -292,6 +319,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--ref-iters", type=int, default=10, help="oracle iterations per sample")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timing")
+    ap.add_argument("--no-csr", action="store_true", help="skip the CSR form of the workload")
     ap.add_argument("--size", type=int, default=N_SIDE, help="grid side (default: the 256^3 workload)")
     args = ap.parse_args()
     globals()["N_SIDE"] = args.size

@@ -209,42 +209,38 @@ def to_csr(p: Problem) -> Problem:
         return p
     nx, ny, nz = p.nx, p.ny, p.nz
     n = nx * ny * nz
-    idx = np.arange(n, dtype=np.int64).reshape(nz, ny, nx)
-    iz, iy, ix = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
-    rows, cols, vals = [], [], []
+    c = np.arange(n, dtype=np.int64)
+    i = c % nx
+    j = (c // nx) % ny
+    k = c // (nx * ny)
     if p.constant:
-        center = 6.0 if p.is_3d else 4.0
-        diag = np.full(n, center)
-        ax = np.where(ix.ravel() > 0, 1.0, 0.0)
-        ay = np.where(iy.ravel() > 0, 1.0, 0.0)
-        az = np.where(iz.ravel() > 0, 1.0, 0.0) if p.is_3d else np.zeros(n)
+        centre = 6.0 if p.is_3d else 4.0
+        diag = np.full(n, centre)
+        one = np.ones(n)
+        ax = ay = az = one
     else:
         diag, ax, ay, az = p.diag, p.ax, p.ay, p.az
-    offs = [(1, ax, ix.ravel() > 0), (nx, ay, iy.ravel() > 0)]
+    nxny = nx * ny
+    # candidate entries of every row, in ascending column order
+    cand, vals, ok = [], [], []
     if p.is_3d:
-        offs.append((nx * ny, az, iz.ravel() > 0))
-    r = idx.ravel()
-    rows.append(r)
-    cols.append(r)
-    vals.append(diag)
-    for off, coef, has_lower in offs:
-        m = has_lower
-        rr = r[m]
-        # lower neighbour entry in row c, and the symmetric upper entry in row c - off
-        rows += [rr, rr - off]
-        cols += [rr - off, rr]
-        vals += [-coef[m], -coef[m]]
-    rows = np.concatenate(rows)
-    cols = np.concatenate(cols)
-    vals = np.concatenate(vals)
-    order = np.lexsort((cols, rows))
-    rows, cols, vals = rows[order], cols[order], vals[order]
+        cand.append(c - nxny); ok.append(k > 0); vals.append(-az)
+    cand.append(c - nx); ok.append(j > 0); vals.append(-ay)
+    cand.append(c - 1); ok.append(i > 0); vals.append(-ax)
+    cand.append(c); ok.append(np.ones(n, dtype=bool)); vals.append(diag)
+    up = lambda a, off: np.concatenate([a[off:], np.zeros(off)])  # noqa: E731  coefficient of the upper face
+    cand.append(c + 1); ok.append(i < nx - 1); vals.append(-up(ax, 1))
+    cand.append(c + nx); ok.append(j < ny - 1); vals.append(-up(ay, nx))
+    if p.is_3d:
+        cand.append(c + nxny); ok.append(k < nz - 1); vals.append(-up(az, nxny))
+    mask = np.stack(ok, axis=1)
+    col = np.stack(cand, axis=1)[mask]
+    val = np.stack(vals, axis=1)[mask]
     row_ptr = np.zeros(n + 1, dtype=np.int64)
-    np.add.at(row_ptr, rows + 1, 1)
-    row_ptr = np.cumsum(row_ptr)
+    np.cumsum(mask.sum(axis=1), out=row_ptr[1:])
     assert row_ptr[-1] < 2 ** 31
-    return Problem(CSR32, row_ptr=row_ptr.astype(np.int32), col=cols.astype(np.int32),
-                   val=vals.astype(np.float64), n_csr=n, name=p.name + "_csr",
+    return Problem(CSR32, row_ptr=row_ptr.astype(np.int32), col=col.astype(np.int32),
+                   val=np.ascontiguousarray(val, dtype=np.float64), n_csr=n, name=p.name + "_csr",
                    meta={"from": p.name, "nx": nx, "ny": ny, "nz": nz})
 
 
