@@ -3,6 +3,11 @@
 
 #include "pcg_kernels.cuh"
 
+// Largest number of unknowns per thread for stencil operators (2 = 128-bit accesses).
+#ifndef PCG_STENCIL_MAX_VEC
+#define PCG_STENCIL_MAX_VEC 2
+#endif
+
 namespace pcgk {
 namespace {
 
@@ -57,7 +62,7 @@ using K = Kernels<std::decay_t<Op>>;
 }  // namespace
 
 int op_vec(const OpDesc& d) {
-  if (d.layout == 2) return 1;
+  if (d.layout == 2 || PCG_STENCIL_MAX_VEC < 2) return 1;
   if (d.nx % 2 != 0) return 1;
   if (d.diag != nullptr) {
     const uintptr_t m = (uintptr_t)d.diag | (uintptr_t)d.ax | (uintptr_t)d.ay | (d.layout == 1 ? (uintptr_t)d.az : 0);

@@ -7,8 +7,8 @@
 //
 // How: every term is an integer significand times a power of two (C*w_c is exact: 6*m
 // = 3*m * 2 and 4*m = m * 4).  All terms are aligned to the largest exponent E with
-// kFxGuard guard bits below its unit in the last place and summed exactly in a signed
-// 64-bit integer (the magnitudes bound the sum below 2^63).  A term more than kFxGuard
+// kFxGuard guard bits below its unit in the last place and summed exactly in 64-bit
+// integers (positive and negative terms apart; each sum stays below 2^62).  A term more than kFxGuard
 // binades below E loses the bits shifted out (truncation, < 2^-kFxGuard ulp(2^E) per
 // term).  The integer sum is then rounded to nearest-even binary64.
 // Error: |result - exact| <= 0.5 ulp(result) + 6 * 2^-kFxGuard * ulp_E, where ulp_E is the
@@ -25,23 +25,25 @@ namespace pcgk {
 constexpr int kFxGuard = 6;
 
 struct FxRaw {
-  unsigned long long m;   // significand (with the implicit bit for normal numbers)
+  unsigned long long mg;  // significand (implicit bit included for normal numbers) << kFxGuard
   int e;                  // biased exponent, 1 for zero and subnormals
   int neg;                // sign bit
   int special;            // Inf or NaN
 };
 
 struct FxTerm {
-  unsigned long long m;
+  unsigned long long mg;  // aligned significand before the exponent shift
   int e;
   int neg;
 };
 
+// Unpacks a binary64 value with integer operations only (an FP64 compare would
+// use the FP64 pipe).
 __device__ __forceinline__ FxRaw fx_raw(double v) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(v);
   const int eb = (int)(u >> 52) & 0x7FF;
   FxRaw r;
-  r.m = (u & 0x000FFFFFFFFFFFFFull) | ((unsigned long long)(eb != 0) << 52);
+  r.mg = ((u & 0x000FFFFFFFFFFFFFull) | ((unsigned long long)(eb != 0) << 52)) << kFxGuard;
   r.e = eb > 1 ? eb : 1;
   r.neg = (int)(u >> 63);
   r.special = eb == 0x7FF;
@@ -52,7 +54,7 @@ __device__ __forceinline__ FxRaw fx_raw(double v) {
 template <int DIM>
 __device__ __forceinline__ FxTerm fx_centre(const FxRaw& r) {
   FxTerm t;
-  t.m = DIM == 3 ? 3ull * r.m : r.m;
+  t.mg = DIM == 3 ? 3ull * r.mg : r.mg;
   t.e = r.e + (DIM == 3 ? 1 : 2);
   t.neg = r.neg;
   return t;
@@ -61,33 +63,34 @@ __device__ __forceinline__ FxTerm fx_centre(const FxRaw& r) {
 // -v as a term.
 __device__ __forceinline__ FxTerm fx_minus(const FxRaw& r) {
   FxTerm t;
-  t.m = r.m;
+  t.mg = r.mg;
   t.e = r.e;
   t.neg = r.neg ^ 1;
   return t;
 }
 
+// Sum of the terms, rounded once.  Positive and negative terms go to separate
+// accumulators (each below 2^62) and are aligned with one right shift each:
+// (m << kFxGuard) >> d is m << (kFxGuard - d) exactly when d <= kFxGuard and
+// truncates the bits below the accumulator's unit otherwise.
 template <int NT>
 __device__ __forceinline__ double fx_sum(const FxTerm (&t)[NT], bool& ok) {
   int E = t[0].e;
 #pragma unroll
   for (int k = 1; k < NT; ++k) E = max(E, t[k].e);
-  long long S = 0;
+  unsigned long long sp = 0ull, sn = 0ull;
 #pragma unroll
   for (int k = 0; k < NT; ++k) {
-    const int d = E - t[k].e;
-    unsigned long long a;
-    if (d <= kFxGuard) {
-      a = t[k].m << (kFxGuard - d);
+    const unsigned long long a = t[k].mg >> min(E - t[k].e, 63);
+    if (t[k].neg) {
+      sn += a;
     } else {
-      const int sh = d - kFxGuard;
-      a = sh < 64 ? (t[k].m >> sh) : 0ull;
+      sp += a;
     }
-    S += t[k].neg ? -(long long)a : (long long)a;
   }
-  if (S == 0) return 0.0;
-  const unsigned long long sgn = S < 0 ? (1ull << 63) : 0ull;
-  const unsigned long long A = S < 0 ? (unsigned long long)(-S) : (unsigned long long)S;
+  if (sp == sn) return 0.0;
+  const bool negative = sn > sp;
+  const unsigned long long A = negative ? sn - sp : sp - sn;
   const int p = 63 - __clzll((long long)A);        // position of the leading one
   int er = p + E - kFxGuard - 52;                  // biased exponent of the result
   unsigned long long mant;
@@ -107,6 +110,7 @@ __device__ __forceinline__ double fx_sum(const FxTerm (&t)[NT], bool& ok) {
     }
   }
   ok = ok && er > 0 && er < 0x7FF;
+  const unsigned long long sgn = negative ? (1ull << 63) : 0ull;
   return __longlong_as_double((long long)(sgn | ((unsigned long long)(er & 0x7FF) << 52) |
                                           (mant & 0x000FFFFFFFFFFFFFull)));
 }

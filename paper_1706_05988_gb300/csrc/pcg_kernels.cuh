@@ -20,6 +20,11 @@
 namespace pcgk {
 
 constexpr int kBlock = kBlockThreads;
+
+// Resident blocks per SM the fused iteration kernel is compiled for (register cap).
+#ifndef PCG_ITER_MIN_BLOCKS
+#define PCG_ITER_MIN_BLOCKS 4
+#endif
 constexpr int kWarps = kBlock / 32;
 
 // ---------------------------------------------------------------- operators
@@ -40,14 +45,48 @@ struct StencilOp {
   __host__ __device__ int units() const { return n / VEC; }
 
 #ifdef PCG_KERNELS_IMPL
+  // Position of a unit: first unknown c0 and its grid coordinates.  The
+  // grid-stride loops advance it by a fixed step with carries instead of
+  // dividing by nx and ny for every unit.
+  struct Cursor {
+    unsigned c0, i0, j, k;
+  };
+  struct Step {
+    unsigned dc, di, dj, dk;
+  };
+  __device__ __forceinline__ Cursor cursor(int u) const {
+    Cursor q;
+    q.c0 = (unsigned)u * VEC;
+    q.i0 = q.c0 % (unsigned)nx;
+    const unsigned t = q.c0 / (unsigned)nx;
+    q.j = t % (unsigned)ny;
+    q.k = t / (unsigned)ny;
+    return q;
+  }
+  __device__ __forceinline__ Step step(unsigned stride_units) const {
+    Step s;
+    s.dc = stride_units * VEC;
+    s.di = s.dc % (unsigned)nx;
+    const unsigned rows = s.dc / (unsigned)nx;
+    s.dj = rows % (unsigned)ny;
+    s.dk = rows / (unsigned)ny;
+    return s;
+  }
+  __device__ __forceinline__ void advance(Cursor& q, const Step& s) const {
+    q.c0 += s.dc;
+    q.i0 += s.di;
+    const unsigned cx = q.i0 >= (unsigned)nx;
+    q.i0 -= cx ? (unsigned)nx : 0u;
+    q.j += s.dj + cx;
+    const unsigned cy = q.j >= (unsigned)ny;
+    q.j -= cy ? (unsigned)ny : 0u;
+    q.k += s.dk + cy;
+  }
+
   // wc[e] = w at the unit's own unknowns, aw[e] = (A w) there.
-  __device__ __forceinline__ void apply(const double* __restrict__ w, int u, double (&wc)[VEC],
+  __device__ __forceinline__ void apply(const double* __restrict__ w, const Cursor& q, double (&wc)[VEC],
                                         double (&aw)[VEC]) const {
-    const unsigned c0 = (unsigned)u * VEC;
-    const unsigned i0 = c0 % (unsigned)nx;
-    const unsigned t = c0 / (unsigned)nx;
-    const unsigned j = t % (unsigned)ny;
-    const unsigned k = t / (unsigned)ny;
+    const unsigned c0 = q.c0, i0 = q.i0, j = q.j, k = q.k;
     const bool has_ym = j > 0, has_yp = j + 1 < (unsigned)ny;
     const bool has_zm = DIM == 3 && k > 0, has_zp = DIM == 3 && k + 1 < (unsigned)nz;
     double c[VEC], ym[VEC], yp[VEC], zm[VEC], zp[VEC];
@@ -177,7 +216,19 @@ struct CsrOp {
   __host__ __device__ int units() const { return n; }
 
 #ifdef PCG_KERNELS_IMPL
-  __device__ __forceinline__ void apply(const double* __restrict__ w, int u, double (&wc)[1], double (&aw)[1]) const {
+  struct Cursor {
+    unsigned c0;
+  };
+  struct Step {
+    unsigned dc;
+  };
+  __device__ __forceinline__ Cursor cursor(int u) const { return Cursor{(unsigned)u}; }
+  __device__ __forceinline__ Step step(unsigned stride_units) const { return Step{stride_units}; }
+  __device__ __forceinline__ void advance(Cursor& q, const Step& s) const { q.c0 += s.dc; }
+
+  __device__ __forceinline__ void apply(const double* __restrict__ w, const Cursor& q, double (&wc)[1],
+                                        double (&aw)[1]) const {
+    const int u = (int)q.c0;
     const int beg = __ldg(row_ptr + u), end = __ldg(row_ptr + u + 1);
     double a = 0.0;
     for (int k = beg; k < end; ++k) a = fma(__ldg(val + k), __ldg(w + __ldg(col + k)), a);
@@ -373,14 +424,15 @@ __global__ void __launch_bounds__(kBlock) k_residual(Op op, const double* __rest
                                                      double* partials) {
   constexpr int VEC = Op::VEC;
   double bb = 0.0;
-  const int nu = op.units();
-  for (int u = blockIdx.x * kBlock + threadIdx.x; u < nu; u += gridDim.x * kBlock) {
-    const int c0 = u * VEC;
+  const unsigned nc = (unsigned)op.units() * VEC;
+  const auto stp = op.step(gridDim.x * kBlock);
+  for (auto q = op.cursor(blockIdx.x * kBlock + threadIdx.x); q.c0 < nc; op.advance(q, stp)) {
+    const int c0 = (int)q.c0;
     double bv[VEC], rv[VEC];
     ld_stream<VEC>(b + c0, bv);
     if (has_x0) {
       double xc[VEC], ax[VEC];
-      op.apply(x, u, xc, ax);
+      op.apply(x, q, xc, ax);
 #pragma unroll
       for (int e = 0; e < VEC; ++e) rv[e] = bv[e] - ax[e];
     } else {
@@ -413,11 +465,12 @@ __global__ void __launch_bounds__(kBlock) k_spcg_w0(Op op, Vecs v, State* st, Hi
   if (st->status != ST_RUNNING) return;
   const double sigma = st->sigma;
   double g = 0.0, o = 0.0;
-  const int nu = op.units();
-  for (int u = blockIdx.x * kBlock + threadIdx.x; u < nu; u += gridDim.x * kBlock) {
-    const int c0 = u * VEC;
+  const unsigned nc = (unsigned)op.units() * VEC;
+  const auto stp = op.step(gridDim.x * kBlock);
+  for (auto q = op.cursor(blockIdx.x * kBlock + threadIdx.x); q.c0 < nc; op.advance(q, stp)) {
+    const int c0 = (int)q.c0;
     double rc[VEC], ar[VEC], w[VEC], zero[VEC];
-    op.apply(v.r, u, rc, ar);
+    op.apply(v.r, q, rc, ar);
 #pragma unroll
     for (int e = 0; e < VEC; ++e) {
       w[e] = fma(-sigma, rc[e], ar[e]);
@@ -444,7 +497,7 @@ __global__ void __launch_bounds__(kBlock) k_spcg_w0(Op op, Vecs v, State* st, Hi
 // (w_{i+1}, r_{i+1}); the last block turns them into alpha_{i+1}, beta_{i+1}.
 // w is double-buffered (neighbours read w_i while w_{i+1} is written).
 template <class Op>
-__global__ void __launch_bounds__(kBlock) k_spcg_iter(Op op, Vecs v, State* st, Hist h, double* partials) {
+__global__ void __launch_bounds__(kBlock, PCG_ITER_MIN_BLOCKS) k_spcg_iter(Op op, Vecs v, State* st, Hist h, double* partials) {
   constexpr int VEC = Op::VEC;
   if (st->status != ST_RUNNING) return;
   const int it = st->iter;
@@ -453,11 +506,12 @@ __global__ void __launch_bounds__(kBlock) k_spcg_iter(Op op, Vecs v, State* st, 
   const double* __restrict__ w = (it & 1) ? v.w1 : v.w0;
   double* __restrict__ wn = (it & 1) ? v.w0 : v.w1;
   double g = 0.0, o = 0.0;
-  const int nu = op.units();
-  for (int u = blockIdx.x * kBlock + threadIdx.x; u < nu; u += gridDim.x * kBlock) {
-    const int c0 = u * VEC;
+  const unsigned nc = (unsigned)op.units() * VEC;
+  const auto stp = op.step(gridDim.x * kBlock);
+  for (auto q = op.cursor(blockIdx.x * kBlock + threadIdx.x); q.c0 < nc; op.advance(q, stp)) {
+    const int c0 = (int)q.c0;
     double wc[VEC], nv[VEC], z[VEC], s[VEC], p[VEC], x[VEC], r[VEC], w1[VEC];
-    op.apply(w, u, wc, nv);
+    op.apply(w, q, wc, nv);
     ld_stream<VEC>(v.z + c0, z);
     ld_stream<VEC>(v.s + c0, s);
     ld_stream<VEC>(v.p + c0, p);
@@ -494,11 +548,12 @@ template <class Op>
 __global__ void __launch_bounds__(kBlock) k_true_res(Op op, Vecs v, State* st, Hist h, double* partials) {
   constexpr int VEC = Op::VEC;
   double t2 = 0.0, f2 = 0.0;
-  const int nu = op.units();
-  for (int u = blockIdx.x * kBlock + threadIdx.x; u < nu; u += gridDim.x * kBlock) {
-    const int c0 = u * VEC;
+  const unsigned nc = (unsigned)op.units() * VEC;
+  const auto stp = op.step(gridDim.x * kBlock);
+  for (auto q = op.cursor(blockIdx.x * kBlock + threadIdx.x); q.c0 < nc; op.advance(q, stp)) {
+    const int c0 = (int)q.c0;
     double xc[VEC], ax[VEC], bv[VEC], rv[VEC];
-    op.apply(v.x, u, xc, ax);
+    op.apply(v.x, q, xc, ax);
     ld_stream<VEC>(v.b + c0, bv);
     ld_stream<VEC>(v.r + c0, rv);
 #pragma unroll
@@ -544,11 +599,12 @@ __global__ void __launch_bounds__(kBlock) k_cg_spmv(Op op, Vecs v, State* st, Hi
   constexpr int VEC = Op::VEC;
   if (st->status != ST_RUNNING) return;
   double sp = 0.0;
-  const int nu = op.units();
-  for (int u = blockIdx.x * kBlock + threadIdx.x; u < nu; u += gridDim.x * kBlock) {
-    const int c0 = u * VEC;
+  const unsigned nc = (unsigned)op.units() * VEC;
+  const auto stp = op.step(gridDim.x * kBlock);
+  for (auto q = op.cursor(blockIdx.x * kBlock + threadIdx.x); q.c0 < nc; op.advance(q, stp)) {
+    const int c0 = (int)q.c0;
     double pc[VEC], s[VEC];
-    op.apply(v.p, u, pc, s);
+    op.apply(v.p, q, pc, s);
     st_plain<VEC>(v.s + c0, s);
 #pragma unroll
     for (int e = 0; e < VEC; ++e) sp = fma(s[e], pc[e], sp);
@@ -615,11 +671,12 @@ __global__ void __launch_bounds__(kBlock) k_cg_p(int n, Vecs v, State* st, Hist 
 template <class Op>
 __global__ void __launch_bounds__(kBlock) k_apply(Op op, const double* __restrict__ x, double* __restrict__ y) {
   constexpr int VEC = Op::VEC;
-  const int nu = op.units();
-  for (int u = blockIdx.x * kBlock + threadIdx.x; u < nu; u += gridDim.x * kBlock) {
+  const unsigned nc = (unsigned)op.units() * VEC;
+  const auto stp = op.step(gridDim.x * kBlock);
+  for (auto q = op.cursor(blockIdx.x * kBlock + threadIdx.x); q.c0 < nc; op.advance(q, stp)) {
     double xc[VEC], ax[VEC];
-    op.apply(x, u, xc, ax);
-    st_plain<VEC>(y + u * VEC, ax);
+    op.apply(x, q, xc, ax);
+    st_plain<VEC>(y + q.c0, ax);
   }
 }
 
