@@ -162,6 +162,33 @@ pcg_status pcg_select_sigma(pcg_ctx *ctx, const double *b, int32_t iters, const 
 pcg_status pcg_psi(pcg_ctx *ctx, const double *alpha, const double *beta, int32_t i, const double *grid,
                    int32_t ngrid, double *psi_out);
 
+/* Largest n accepted by pcg_true_residual_noalloc. */
+#define PCG_NOALLOC_MAX_N 16777216
+
+/* ||b - A x||_2 and ||(b - A x) - r||_2 without allocating anything.
+ * The paper has no counterpart: this entry point exists for callers that must not
+ * allocate device memory -- an application whose device memory is owned by another
+ * allocator (a framework's caching pool that holds the whole GPU), a latency-bound
+ * loop that cannot afford cudaMalloc's implicit device synchronisation, or a
+ * program that fixes its memory footprint at start-up.  It needs no context: A
+ * describes the operator as for pcg_create with PCG_DEVICE_PTRS (every array a
+ * device pointer); b, x and r (r may be NULL) are device arrays of n doubles,
+ * 16-byte aligned; norms is a device array of 2 doubles that receives
+ * ||b - A x||_2 and ||(b - A x) - r||_2 (NaN when r is NULL).  A is evaluated as
+ * inside the solver (fixed-point rows for constant-coefficient stencils).
+ * The work is queued on `stream` (NULL = the default stream) and the call returns
+ * without waiting; norms is valid once the stream reaches that point.
+ * Scratch: one file-scope device array of 64 KiB (per-block partial sums and a
+ * ticket), held by every GPU that loads this library until the process exits.  The
+ * first call on a device looks up that array's address and caches it; make that
+ * first call before any stream capture.  Every call shares the array: calls whose
+ * work overlaps on a GPU (other streams, other host threads) race and give wrong
+ * norms; serialise them.  No cudaMalloc, cudaFree or other allocating call is made.
+ * Errors: PCG_EINVAL for NULL pointers, an invalid description, misaligned vectors
+ * or n > PCG_NOALLOC_MAX_N (16,777,216 unknowns); PCG_ECUDA if a CUDA call fails. */
+pcg_status pcg_true_residual_noalloc(const pcg_matrix *A, const double *b, const double *x, const double *r,
+                                     double *norms, void *stream);
+
 /* Kernel accounting of the context since creation (or the last reset):
  * total launches of every kernel of this library, and -- with PCG_PROFILE --
  * the launches and summed CUDA-event time (ms) of the fused iteration kernel. */

@@ -76,12 +76,13 @@ def lib() -> ctypes.CDLL:
         L.pcg_select_sigma.argtypes = [vp, vp, i32, vp, i32, ctypes.POINTER(f64), vp]
         L.pcg_psi.argtypes = [vp, vp, vp, i32, vp, i32, vp]
         L.pcg_apply.argtypes = [vp, vp, vp]
+        L.pcg_true_residual_noalloc.argtypes = [ctypes.POINTER(pcg_matrix), vp, vp, vp, vp, vp]
         L.pcg_kernel_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(f64)]
         L.pcg_kernel_stats_reset.argtypes = [vp]
         L.pcg_version.argtypes = []
         L.pcg_version.restype = ctypes.c_char_p
         for f in ("pcg_create", "pcg_set_stream", "pcg_solve", "pcg_solve_device", "pcg_select_sigma", "pcg_psi",
-                  "pcg_apply",
+                  "pcg_apply", "pcg_true_residual_noalloc",
                   "pcg_kernel_stats", "pcg_kernel_stats_reset"):
             getattr(L, f).restype = st
         _lib = L
@@ -140,6 +141,12 @@ def pcg_solve_device(ctx, b, x0, method, sigma, tol, maxit, precision, x_out, re
 def pcg_apply(ctx, x, y) -> int:
     """y = A x on the device (x, y: CUDA tensors or device addresses)."""
     return lib().pcg_apply(ctx, _p(x), _p(y))
+
+
+def pcg_true_residual_noalloc(A: pcg_matrix, b, x, r, norms, stream=None) -> int:
+    """||b - A x|| and ||(b - A x) - r|| into the device array norms[2] without allocating;
+    A's arrays, b, x, r (or None) and norms are device memory (tensors or addresses)."""
+    return lib().pcg_true_residual_noalloc(ctypes.byref(A), _p(b), _p(x), _p(r), _p(norms), stream)
 
 
 def pcg_psi(ctx, alpha: np.ndarray, beta: np.ndarray, i: int, grid: np.ndarray) -> np.ndarray:
