@@ -39,7 +39,7 @@ NCU_TRAFFIC = {}
 
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
-    for f in ("pcg_kernels.cuh", "pcg_kernels_3d.cu"):
+    for f in ("pcg_kernels.cuh", "pcg_fixedsum.cuh", "pcg_kernels_3d.cu"):
         with open(os.path.join(ROOT, "paper_1706_05988_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
