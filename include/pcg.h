@@ -128,10 +128,19 @@ pcg_status pcg_set_stream(pcg_ctx *ctx, void *stream);
 
 /* Solve A x = b.  b, x0 (NULL = zero) and x_out are host arrays of length n.
  * method: pcg_method; sigma: the shift of Algorithm 3 (must be >= 0; ignored
- * by PCG_CG and forced to 0 by PCG_PCG).  tol: stop once the recursive
- * residual satisfies ||r_i|| <= tol ||b|| (the scaled criterion of the
- * paper's Section 5.2); tol = 0 runs exactly maxit iterations.  maxit >= 0.
- * precision must be PCG_FP64 (PCG_MIXED_IR is not implemented: PCG_ENOTIMPL).
+ * by PCG_CG and forced to 0 by PCG_PCG).  maxit >= 0.
+ * precision PCG_FP64: every vector and operation in binary64.  tol: stop once the
+ *   recursive residual satisfies ||r_i|| <= tol ||b|| (the scaled criterion of
+ *   the paper's Section 5.2); tol = 0 runs exactly maxit iterations.
+ * precision PCG_MIXED_IR (Algorithm 3 only, not PCG_CG): w, z, s, p stored and
+ *   updated in binary32; x, r, the dot products (exact binary64 products, binary64
+ *   sums), alpha, beta and sigma in binary64.  When the recursive residual reaches
+ *   eta (PCG_PARAM_MIXED_ETA, default 2^-10) times the true residual of the last
+ *   restart, the true residual b - A x is recomputed in binary64 and Algorithm 3
+ *   restarts from the current x (iterative refinement).  tol applies to the true
+ *   residual ||b - A x|| <= tol ||b||; the solve also ends at maxit iterations or
+ *   when a restart does not lower the true residual (PCG_ENOTCONV).  true_hist
+ *   holds the true residual at every restart and at exit.
  * Returns PCG_OK on convergence, PCG_ENOTCONV at maxit (always when tol = 0),
  * PCG_EBREAKDOWN; res may be NULL.  x_out is written in every non-error case. */
 pcg_status pcg_solve(pcg_ctx *ctx, const double *b, const double *x0, int32_t method, double sigma, double tol,
@@ -188,6 +197,14 @@ pcg_status pcg_psi(pcg_ctx *ctx, const double *alpha, const double *beta, int32_
  * or n > PCG_NOALLOC_MAX_N (16,777,216 unknowns); PCG_ECUDA if a CUDA call fails. */
 pcg_status pcg_true_residual_noalloc(const pcg_matrix *A, const double *b, const double *x, const double *r,
                                      double *norms, void *stream);
+
+/* Solver parameters (not part of the paper's method statement).
+ *   PCG_PARAM_MIXED_ETA      inner tolerance of PCG_MIXED_IR, in (0, 1); default 2^-10
+ *   PCG_PARAM_MAX_RESTARTS   most restarts of one PCG_MIXED_IR solve, >= 1; default 200
+ * Errors: PCG_EINVAL for an unknown parameter or a value out of range. */
+#define PCG_PARAM_MIXED_ETA 1
+#define PCG_PARAM_MAX_RESTARTS 2
+pcg_status pcg_set_param(pcg_ctx *ctx, int32_t param, double value);
 
 /* Kernel accounting of the context since creation (or the last reset):
  * total launches of every kernel of this library, and -- with PCG_PROFILE --

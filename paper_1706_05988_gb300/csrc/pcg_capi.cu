@@ -37,6 +37,11 @@ struct pcg_ctx {
   double* d_small = nullptr;            // psi workspace
   int small_cap = 0;
   int grid[K_NKINDS] = {0};
+  // mixed precision: binary32 copies of the operator's coefficients, grids, parameters
+  bool mixed_ready = false;
+  int grid_mx[KM_NKINDS] = {0};
+  double mx_eta = 0.0009765625;        // 2^-10
+  int mx_max_restarts = 200;
   int64_t launches = 0, iter_launches = 0;
   double iter_ms = 0.0;
   std::vector<cudaEvent_t> ev;          // PCG_PROFILE: pairs around iteration launches
@@ -264,6 +269,22 @@ pcg_status pcg_set_stream(pcg_ctx* c, void* stream) {
   return PCG_OK;
 }
 
+pcg_status pcg_set_param(pcg_ctx* c, int32_t param, double value) {
+  if (!c) return PCG_EINVAL;
+  switch (param) {
+    case PCG_PARAM_MIXED_ETA:
+      if (!(value > 0.0 && value < 1.0)) return fail(c, PCG_EINVAL, "eta must lie in (0, 1)");
+      c->mx_eta = value;
+      return PCG_OK;
+    case PCG_PARAM_MAX_RESTARTS:
+      if (!(value >= 1.0 && value <= 1e6)) return fail(c, PCG_EINVAL, "max restarts must lie in [1, 1e6]");
+      c->mx_max_restarts = (int)value;
+      return PCG_OK;
+    default:
+      return fail(c, PCG_EINVAL, "unknown parameter");
+  }
+}
+
 pcg_status pcg_kernel_stats(pcg_ctx* c, int64_t* launches_total, int64_t* iter_launches, double* iter_ms) {
   if (!c) return PCG_EINVAL;
   if (launches_total) *launches_total = c->launches;
@@ -365,6 +386,100 @@ pcg_status run_solve(pcg_ctx* c, bool has_x0, int method, double sigma, double t
   return PCG_OK;
 }
 
+pcg_status ensure_mixed(pcg_ctx* c) {
+  if (c->mixed_ready) return PCG_OK;
+  auto copy32 = [&](const double* src, const float** dst) -> pcg_status {
+    void* p;
+    const long long count = src == c->op.val ? c->nnz : c->n;
+    pcg_status s = dev_alloc(c, &p, (size_t)(count > 0 ? count : 1) * sizeof(float));
+    if (s != PCG_OK) return s;
+    CUDA_TRY(c, launch_to_f32(src, (float*)p, count, c->stream));
+    *dst = (const float*)p;
+    return PCG_OK;
+  };
+  pcg_status s;
+  if (c->op.layout == PCG_CSR32) {
+    if ((s = copy32(c->op.val, &c->op.val32)) != PCG_OK) return s;
+  } else if (c->op.diag) {
+    if ((s = copy32(c->op.diag, &c->op.diag32)) != PCG_OK) return s;
+    if ((s = copy32(c->op.ax, &c->op.ax32)) != PCG_OK) return s;
+    if ((s = copy32(c->op.ay, &c->op.ay32)) != PCG_OK) return s;
+    if (c->op.layout == PCG_STENCIL7_3D && (s = copy32(c->op.az, &c->op.az32)) != PCG_OK) return s;
+  }
+  for (int k = 0; k < KM_NKINDS; ++k) {
+    c->grid_mx[k] = grid_for_mixed(c->op, k, kBlockThreads);
+    if (c->grid_mx[k] <= 0) {
+      cudaGetLastError();
+      return fail(c, PCG_ECUDA, "could not size the mixed-precision grids");
+    }
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->mixed_ready = true;
+  return PCG_OK;
+}
+
+// Mixed precision with restarts: the restart pair (binary64 true residual, w_0)
+// is queued after every kRestartEvery iteration launches and does nothing unless
+// the inner iteration asked for it, so the refinement loop runs on the device;
+// the host only polls between chunks to stop queueing once the solve has ended.
+pcg_status run_solve_mixed(pcg_ctx* c, bool has_x0, int method, double sigma, double tol, int maxit,
+                           int true_every, int* iters_out, int* status_out) {
+  constexpr int kRestartEvery = 4;
+  State st{};
+  st.iter = 0;
+  st.status = ST_RESTART;
+  st.maxit = maxit;
+  st.sigma = method == PCG_SPCG ? sigma : 0.0;
+  st.tol_abs = 0.0;
+  st.tol_rel = tol;
+  st.eta = c->mx_eta;
+  st.rprev = INFINITY;
+  st.restarts = 0;
+  st.max_restarts = c->mx_max_restarts;
+  *c->h_state = st;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_state, c->h_state, sizeof(State), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_hist, 0xff, 7 * (size_t)c->hist_cap * sizeof(double), c->stream));  // NaN
+  if (!has_x0) CUDA_TRY(c, cudaMemsetAsync(c->v.x, 0, (size_t)c->n * sizeof(double), c->stream));
+  const Launch Lr{c->grid_mx[KM_RESTART], kBlockThreads, c->stream};
+  const Launch Lw{c->grid_mx[KM_W0], kBlockThreads, c->stream};
+  const Launch Li{c->grid_mx[KM_ITER], kBlockThreads, c->stream};
+  auto restart_pair = [&]() -> pcg_status {
+    CUDA_TRY(c, launch_mx_restart(c->op, Lr, c->v, c->d_state, c->h, c->d_partials));
+    CUDA_TRY(c, launch_mx_w0(c->op, Lw, c->v, c->d_state, c->h, c->d_partials));
+    c->launches += 2;
+    return PCG_OK;
+  };
+  pcg_status s = restart_pair();
+  if (s != PCG_OK) return s;
+  (void)true_every;   // the true residual is logged at every restart and at exit
+  const long long max_launches = (long long)maxit + (long long)kRestartEvery * (c->mx_max_restarts + 2) + 64;
+  long long launched = 0;
+  int chunk = 32;
+  for (;;) {
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(State), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    const int stt = c->h_state->status;
+    if (stt != ST_RUNNING && stt != ST_RESTART) break;
+    if (launched >= max_launches) break;
+    for (int k = 0; k < chunk; ++k) {
+      CUDA_TRY(c, launch_mx_iter(c->op, Li, c->v, c->d_state, c->h, c->d_partials));
+      ++c->launches;
+      ++launched;
+      if (launched % kRestartEvery == 0) {
+        if ((s = restart_pair()) != PCG_OK) return s;
+      }
+    }
+    chunk = std::min(chunk * 2, 512);
+  }
+  CUDA_TRY(c, launch_true_res(c->op, launch_of(c, K_TRUE_RES), c->v, c->d_state, c->h, c->d_partials));
+  ++c->launches;
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(State), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  *iters_out = c->h_state->iter;
+  *status_out = c->h_state->status;
+  return PCG_OK;
+}
+
 pcg_status solve_common(pcg_ctx* c, const double* b, const double* x0, int32_t method, double sigma, double tol,
                         int32_t maxit, int32_t precision, double* x_out, pcg_result* res, bool host) {
   if (!c) return PCG_EINVAL;
@@ -374,11 +489,13 @@ pcg_status solve_common(pcg_ctx* c, const double* b, const double* x0, int32_t m
   if (!(sigma >= 0.0) || !isfinite(sigma)) return fail(c, PCG_EINVAL, "sigma must be finite and >= 0");
   if (!(tol >= 0.0) || !isfinite(tol)) return fail(c, PCG_EINVAL, "tol must be finite and >= 0");
   if (maxit < 0 || maxit > (1 << 28)) return fail(c, PCG_EINVAL, "maxit out of range");
-  if (precision == PCG_MIXED_IR) return fail(c, PCG_ENOTIMPL, "PCG_MIXED_IR is not implemented");
-  if (precision != PCG_FP64) return fail(c, PCG_EINVAL, "unknown precision");
+  if (precision != PCG_FP64 && precision != PCG_MIXED_IR) return fail(c, PCG_EINVAL, "unknown precision");
+  if (precision == PCG_MIXED_IR && method == PCG_CG)
+    return fail(c, PCG_ENOTIMPL, "PCG_MIXED_IR runs Algorithm 3 (PCG_PCG or PCG_SPCG), not classic CG");
   CUDA_TRY(c, cudaSetDevice(c->device));
   pcg_status s;
   if ((s = ensure_vectors(c)) != PCG_OK) return s;
+  if (precision == PCG_MIXED_IR && (s = ensure_mixed(c)) != PCG_OK) return s;
   if ((s = ensure_hist(c, maxit + 1)) != PCG_OK) return s;
   const size_t bytes = (size_t)c->n * sizeof(double);
   const cudaMemcpyKind in = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
@@ -392,11 +509,13 @@ pcg_status solve_common(pcg_ctx* c, const double* b, const double* x0, int32_t m
   if (x0) CUDA_TRY(c, cudaMemcpyAsync(c->v.x, x0, bytes, in, c->stream));
   const int true_every = res ? res->true_every : 0;
   int iters = 0, st = ST_RUNNING;
-  s = run_solve(c, x0 != nullptr, method, sigma, tol, maxit, true_every, &iters, &st);
+  s = precision == PCG_MIXED_IR ? run_solve_mixed(c, x0 != nullptr, method, sigma, tol, maxit, true_every, &iters, &st)
+                                 : run_solve(c, x0 != nullptr, method, sigma, tol, maxit, true_every, &iters, &st);
   c->v.b = c->d_b;
   if (s != PCG_OK) return s;
   CUDA_TRY(c, cudaMemcpyAsync(x_out, c->v.x, bytes, outk, c->stream));
   pcg_status ret = st == ST_CONVERGED ? PCG_OK : st == ST_BREAKDOWN ? PCG_EBREAKDOWN : PCG_ENOTCONV;
+  if (st == ST_STALLED) c->err = "iterative refinement stalled: a restart did not lower the true residual";
   if (res) {
     const size_t k = (size_t)iters + 1;
     auto get = [&](double* dst, const double* src) -> cudaError_t {

@@ -7,7 +7,10 @@
 namespace pcgk {
 
 // Run state of one solve (device memory).
-enum : int { ST_RUNNING = 0, ST_CONVERGED = 1, ST_BREAKDOWN = 2, ST_MAXIT = 3 };
+// ST_RESTART (mixed precision only): the inner iteration reached its tolerance;
+// the restart kernels recompute the true residual in FP64 and restart Algorithm 3.
+// ST_STALLED (mixed precision only): a restart did not lower the true residual.
+enum : int { ST_RUNNING = 0, ST_CONVERGED = 1, ST_BREAKDOWN = 2, ST_MAXIT = 3, ST_RESTART = 4, ST_STALLED = 5 };
 
 struct State {
   int iter;              // index i of the next iteration to execute (or of the last iterate once stopped)
@@ -19,6 +22,12 @@ struct State {
   double bnorm;          // ||b||_2
   unsigned int ticket;   // last-block ticket of the running reduction (reset to 0 by its finisher)
   unsigned int pad1;
+  // mixed precision with restarts (iterative refinement)
+  double tol_rel;        // outer tolerance on ||b - A x|| / ||b||
+  double eta;            // inner tolerance, relative to the true residual at the restart
+  double rprev;          // true residual at the previous restart
+  int restarts;          // restarts performed
+  int max_restarts;
 };
 
 // Per-iteration histories (device arrays of maxit + 1 entries).
@@ -35,6 +44,8 @@ struct OpDesc {
   const double *diag, *ax, *ay, *az;   // variable coefficients; diag == nullptr: Laplacian
   const int *row_ptr, *col;
   const double *val;
+  // binary32 copies used by the mixed-precision inner iteration
+  const float *diag32, *ax32, *ay32, *az32, *val32;
 };
 
 // Solver vectors (device, n entries each, 256-byte aligned).
@@ -67,6 +78,15 @@ cudaError_t launch_cg_spmv(const OpDesc& op, const Launch& L, Vecs v, State* st,
 cudaError_t launch_cg_update(const OpDesc& op, const Launch& L, Vecs v, State* st, Hist h, double* partials);
 cudaError_t launch_cg_p(const OpDesc& op, const Launch& L, Vecs v, State* st, Hist h);
 cudaError_t launch_apply(const OpDesc& op, const Launch& L, const double* x, double* y);
+
+// Mixed precision (pcg_mixed.cuh): FP32 w, z, s, p stored in the FP64 buffers of Vecs.
+enum { KM_RESTART = 0, KM_W0, KM_ITER, KM_NKINDS };
+int mixed_vec(const OpDesc& op);
+int grid_for_mixed(const OpDesc& op, int kind, int block);
+cudaError_t launch_mx_restart(const OpDesc& op, const Launch& L, Vecs v, State* st, Hist h, double* partials);
+cudaError_t launch_mx_w0(const OpDesc& op, const Launch& L, Vecs v, State* st, Hist h, double* partials);
+cudaError_t launch_mx_iter(const OpDesc& op, const Launch& L, Vecs v, State* st, Hist h, double* partials);
+cudaError_t launch_to_f32(const double* src, float* dst, long long n, cudaStream_t stream);
 
 // psi_i(sigma) for every shift of sig[ngrid]; alpha/beta device arrays (>= i+1 entries).
 cudaError_t launch_psi(const double* alpha, const double* beta, int i, const double* sig, int ngrid, double* psi,

@@ -28,6 +28,8 @@ PCG_FP64, PCG_MIXED_IR = 0, 1
 PCG_DEVICE_PTRS = 0x1
 PCG_PROFILE = 0x2
 PCG_STENCIL_FP64_SUM = 0x4
+# pcg_set_param parameters
+PCG_PARAM_MIXED_ETA, PCG_PARAM_MAX_RESTARTS = 1, 2
 
 METHODS = {"cg": PCG_CG, "pcg": PCG_PCG, "spcg": PCG_SPCG}
 
@@ -76,13 +78,14 @@ def lib() -> ctypes.CDLL:
         L.pcg_select_sigma.argtypes = [vp, vp, i32, vp, i32, ctypes.POINTER(f64), vp]
         L.pcg_psi.argtypes = [vp, vp, vp, i32, vp, i32, vp]
         L.pcg_apply.argtypes = [vp, vp, vp]
+        L.pcg_set_param.argtypes = [vp, i32, f64]
         L.pcg_true_residual_noalloc.argtypes = [ctypes.POINTER(pcg_matrix), vp, vp, vp, vp, vp]
         L.pcg_kernel_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(f64)]
         L.pcg_kernel_stats_reset.argtypes = [vp]
         L.pcg_version.argtypes = []
         L.pcg_version.restype = ctypes.c_char_p
         for f in ("pcg_create", "pcg_set_stream", "pcg_solve", "pcg_solve_device", "pcg_select_sigma", "pcg_psi",
-                  "pcg_apply", "pcg_true_residual_noalloc",
+                  "pcg_apply", "pcg_true_residual_noalloc", "pcg_set_param",
                   "pcg_kernel_stats", "pcg_kernel_stats_reset"):
             getattr(L, f).restype = st
         _lib = L
@@ -136,6 +139,10 @@ def pcg_solve(ctx, b, x0, method, sigma, tol, maxit, precision, x_out, res) -> i
 def pcg_solve_device(ctx, b, x0, method, sigma, tol, maxit, precision, x_out, res) -> int:
     return lib().pcg_solve_device(ctx, _p(b), _p(x0), method, sigma, tol, maxit, precision, _p(x_out),
                                   ctypes.byref(res) if res is not None else None)
+
+
+def pcg_set_param(ctx, param: int, value: float) -> int:
+    return lib().pcg_set_param(ctx, param, value)
 
 
 def pcg_apply(ctx, x, y) -> int:
@@ -257,7 +264,7 @@ class Solver:
         self.close()
 
     def solve(self, b, x0=None, method="spcg", sigma=0.0, tol=0.0, maxit=100, true_every=0, device=False,
-              x_out=None, raise_on_error=True) -> SolveResult:
+              x_out=None, raise_on_error=True, precision=PCG_FP64) -> SolveResult:
         """b/x0/x_out: numpy arrays (host) or, with device=True, CUDA tensors."""
         m = METHODS[method] if isinstance(method, str) else method
         k = maxit + 1
@@ -270,13 +277,13 @@ class Solver:
             if x_out is None:
                 import torch
                 x_out = torch.empty(self.n, dtype=torch.float64, device=b.device)
-            s = pcg_solve_device(self.ctx, b, x0, m, sigma, tol, maxit, PCG_FP64, x_out, res)
+            s = pcg_solve_device(self.ctx, b, x0, m, sigma, tol, maxit, precision, x_out, res)
         else:
             b = np.ascontiguousarray(b, dtype=np.float64)
             x0 = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
             if x_out is None:
                 x_out = np.empty(self.n)
-            s = pcg_solve(self.ctx, b, x0, m, sigma, tol, maxit, PCG_FP64, x_out, res)
+            s = pcg_solve(self.ctx, b, x0, m, sigma, tol, maxit, precision, x_out, res)
         if s not in (PCG_OK, PCG_ENOTCONV, PCG_EBREAKDOWN) and raise_on_error:
             raise PcgError(s, pcg_last_error(self.ctx))
         it = res.iters

@@ -277,7 +277,8 @@ def test_invalid_arguments(B):
         assert C.pcg_solve(s.ctx, b, None, 9, 0.0, 0.0, 5, 0, x, None) == C.PCG_EINVAL
         assert C.pcg_solve(s.ctx, b, None, 2, 0.0, -1.0, 5, 0, x, None) == C.PCG_EINVAL
         assert C.pcg_solve(s.ctx, b, None, 2, 0.0, 0.0, -1, 0, x, None) == C.PCG_EINVAL
-        assert C.pcg_solve(s.ctx, b, None, 2, 0.0, 0.0, 5, 1, x, None) == C.PCG_ENOTIMPL
+        assert C.pcg_solve(s.ctx, b, None, 2, 0.0, 0.0, 5, 7, x, None) == C.PCG_EINVAL        # precision
+        assert C.pcg_solve(s.ctx, b, None, 0, 0.0, 0.0, 5, 1, x, None) == C.PCG_ENOTIMPL      # mixed CG
         # the context stays usable after rejected calls
         r = s.solve(b, method="spcg", sigma=4.0, maxit=5)
         assert r.iters == 5
