@@ -265,6 +265,30 @@ def run_ours(args):
 
     solver.close()
 
+    # the same step with the persistent cooperative kernel (one launch for all iterations)
+    persistent = None
+    if not args.no_persistent:
+        with pkg.Solver(P, flags=C.PCG_PROFILE | C.PCG_PERSISTENT) as sp:
+            C.pcg_set_stream(sp.ctx, stream.cuda_stream)
+            for _ in range(2):
+                s = C.pcg_solve_device(sp.ctx, b_dev, None, C.PCG_SPCG, SIGMA, 0.0, ITERS_PER_STEP, C.PCG_FP64,
+                                       x_dev, None)
+                assert s == C.PCG_ENOTCONV, C.pcg_last_error(sp.ctx)
+            C.pcg_kernel_stats_reset(sp.ctx)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(args.steps):
+                s = C.pcg_solve_device(sp.ctx, b_dev, None, C.PCG_SPCG, SIGMA, 0.0, ITERS_PER_STEP, C.PCG_FP64,
+                                       x_dev, None)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            assert s == C.PCG_ENOTCONV
+            _, il, ims = C.pcg_kernel_stats(sp.ctx)
+            k_s = ims / il / 1e3                   # per iteration inside the launch
+            persistent = {"value": args.steps * ITERS_PER_STEP / (ev0.elapsed_time(ev1) / 1e3), "unit": UNIT,
+                          "ms_per_iteration": k_s * 1e3, "achieved_gbs": alg_bytes / k_s / 1e9,
+                          "frac": alg_bytes / k_s / 1e9 / peak}
+
     # the same workload as CSR (int32 indices): config's second form, one timed step
     csr = None
     if not args.no_csr:
@@ -303,7 +327,7 @@ def run_ours(args):
                                       "per SM x 152 SMs x 2.07 GHz (ncu sm__sass_thread_inst_executed_op_dfma "
                                       "peak_sustained)"},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
-                "csr_int32": csr}
+                "csr_int32": csr, "persistent": persistent}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -320,6 +344,7 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=10, help="oracle iterations per sample")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timing")
     ap.add_argument("--no-csr", action="store_true", help="skip the CSR form of the workload")
+    ap.add_argument("--no-persistent", action="store_true", help="skip the persistent-kernel measurement")
     ap.add_argument("--size", type=int, default=N_SIDE, help="grid side (default: the 256^3 workload)")
     args = ap.parse_args()
     globals()["N_SIDE"] = args.size

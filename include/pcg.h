@@ -57,6 +57,11 @@ typedef enum { PCG_FP64 = 0, PCG_MIXED_IR = 1 } pcg_precision;
 #define PCG_DEVICE_PTRS 0x1u   /* every array in pcg_matrix is a device pointer          */
 #define PCG_PROFILE 0x2u       /* time every launch of the fused iteration kernel with
                                   CUDA events (read back with pcg_kernel_stats)          */
+#define PCG_PERSISTENT 0x8u    /* PCG_PCG / PCG_SPCG in FP64 with true_every <= 0: run every
+                                  iteration inside one cooperative launch; a grid barrier
+                                  replaces the kernel boundary and each block overlaps the
+                                  global reduction of (r,r), (w,r) with the SpMV of its next
+                                  unit (the paper's communication hiding, Section 1) */
 #define PCG_STENCIL_FP64_SUM 0x4u  /* constant-coefficient stencils: sum each row with FP64
                                   additions instead of the default fixed-point row sum.
                                   Default: the row C*w_c - sum(neighbours) is summed exactly
@@ -201,9 +206,15 @@ pcg_status pcg_true_residual_noalloc(const pcg_matrix *A, const double *b, const
 /* Solver parameters (not part of the paper's method statement).
  *   PCG_PARAM_MIXED_ETA      inner tolerance of PCG_MIXED_IR, in (0, 1); default 2^-10
  *   PCG_PARAM_MAX_RESTARTS   most restarts of one PCG_MIXED_IR solve, >= 1; default 200
+ *   PCG_PARAM_BARRIER_TIMEOUT_MS, PCG_PARAM_TEST_BARRIER_PHANTOMS: see below
  * Errors: PCG_EINVAL for an unknown parameter or a value out of range. */
 #define PCG_PARAM_MIXED_ETA 1
 #define PCG_PARAM_MAX_RESTARTS 2
+#define PCG_PARAM_BARRIER_TIMEOUT_MS 3   /* PCG_PERSISTENT: longest grid-barrier wait before
+                                            the solve ends with PCG_ETIMEOUT; default 2000 */
+#define PCG_PARAM_TEST_BARRIER_PHANTOMS 4 /* PCG_PERSISTENT, for tests of the time limit: the
+                                            barrier waits for this many arrivals that never
+                                            come (0 = off, the default) */
 pcg_status pcg_set_param(pcg_ctx *ctx, int32_t param, double value);
 
 /* Kernel accounting of the context since creation (or the last reset):

@@ -42,6 +42,10 @@ struct pcg_ctx {
   int grid_mx[KM_NKINDS] = {0};
   double mx_eta = 0.0009765625;        // 2^-10
   int mx_max_restarts = 200;
+  // persistent kernel
+  int grid_persistent = 0;
+  double barrier_timeout_ms = 2000.0;
+  unsigned barrier_phantoms = 0;
   int64_t launches = 0, iter_launches = 0;
   double iter_ms = 0.0;
   std::vector<cudaEvent_t> ev;          // PCG_PROFILE: pairs around iteration launches
@@ -163,7 +167,7 @@ pcg_status pcg_create(const pcg_matrix* A, uint32_t flags, pcg_ctx** out) {
   if (!out) return PCG_EINVAL;
   *out = nullptr;
   if (!A) return PCG_EINVAL;
-  if (flags & ~(PCG_DEVICE_PTRS | PCG_PROFILE | PCG_STENCIL_FP64_SUM)) return PCG_EINVAL;
+  if (flags & ~(PCG_DEVICE_PTRS | PCG_PROFILE | PCG_STENCIL_FP64_SUM | PCG_PERSISTENT)) return PCG_EINVAL;
   OpDesc op{};
   op.layout = A->layout;
   op.fixed_sum = (flags & PCG_STENCIL_FP64_SUM) ? 0 : 1;
@@ -237,6 +241,13 @@ pcg_status pcg_create(const pcg_matrix* A, uint32_t flags, pcg_ctx** out) {
     return bail(PCG_ENOMEM);
   }
   c->h_state = (State*)p;
+  if (flags & PCG_PERSISTENT) {
+    c->grid_persistent = grid_for_persistent(c->op);
+    if (c->grid_persistent <= 0) {
+      cudaGetLastError();
+      return bail(fail(c, PCG_ECUDA, "could not size the persistent grid"));
+    }
+  }
   for (int k = 0; k < K_NKINDS; ++k) {
     c->grid[k] = grid_for(c->op, k, kBlockThreads);
     if (c->grid[k] <= 0) {
@@ -275,6 +286,14 @@ pcg_status pcg_set_param(pcg_ctx* c, int32_t param, double value) {
     case PCG_PARAM_MIXED_ETA:
       if (!(value > 0.0 && value < 1.0)) return fail(c, PCG_EINVAL, "eta must lie in (0, 1)");
       c->mx_eta = value;
+      return PCG_OK;
+    case PCG_PARAM_BARRIER_TIMEOUT_MS:
+      if (!(value >= 1.0 && value <= 600000.0)) return fail(c, PCG_EINVAL, "timeout must lie in [1, 600000] ms");
+      c->barrier_timeout_ms = value;
+      return PCG_OK;
+    case PCG_PARAM_TEST_BARRIER_PHANTOMS:
+      if (!(value >= 0.0 && value <= 1024.0)) return fail(c, PCG_EINVAL, "phantoms must lie in [0, 1024]");
+      c->barrier_phantoms = (unsigned)value;
       return PCG_OK;
     case PCG_PARAM_MAX_RESTARTS:
       if (!(value >= 1.0 && value <= 1e6)) return fail(c, PCG_EINVAL, "max restarts must lie in [1, 1e6]");
@@ -336,6 +355,27 @@ pcg_status run_solve(pcg_ctx* c, bool has_x0, int method, double sigma, double t
   if (true_every > 0) {
     CUDA_TRY(c, launch_true_res(c->op, L(K_TRUE_RES), c->v, c->d_state, c->h, c->d_partials));
     ++c->launches;
+  }
+  if (!cg && (c->flags & PCG_PERSISTENT) && true_every <= 0 && maxit > 0) {
+    // every iteration inside one cooperative launch
+    if (profile) CUDA_TRY(c, cudaEventRecord(c->ev[0], c->stream));
+    CUDA_TRY(c, launch_spcg_persistent(c->op, c->grid_persistent, c->stream, c->v, c->d_state, c->h, c->d_partials,
+                                       (unsigned long long)(c->barrier_timeout_ms * 1e6), c->barrier_phantoms));
+    if (profile) CUDA_TRY(c, cudaEventRecord(c->ev[1], c->stream));
+    ++c->launches;
+    CUDA_TRY(c, launch_true_res(c->op, L(K_TRUE_RES), c->v, c->d_state, c->h, c->d_partials));
+    ++c->launches;
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(State), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (profile) {
+      float ms = 0.f;
+      CUDA_TRY(c, cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+      c->iter_ms += ms;
+      c->iter_launches += c->h_state->iter;   // iterations run inside the launch
+    }
+    *iters_out = c->h_state->iter;
+    *status_out = c->h_state->status;
+    return PCG_OK;
   }
   int done = 0;            // iteration launches issued
   int prof_pairs = 0;
@@ -514,7 +554,9 @@ pcg_status solve_common(pcg_ctx* c, const double* b, const double* x0, int32_t m
   c->v.b = c->d_b;
   if (s != PCG_OK) return s;
   CUDA_TRY(c, cudaMemcpyAsync(x_out, c->v.x, bytes, outk, c->stream));
-  pcg_status ret = st == ST_CONVERGED ? PCG_OK : st == ST_BREAKDOWN ? PCG_EBREAKDOWN : PCG_ENOTCONV;
+  pcg_status ret = st == ST_CONVERGED ? PCG_OK : st == ST_BREAKDOWN ? PCG_EBREAKDOWN
+                   : st == ST_TIMEOUT ? PCG_ETIMEOUT : PCG_ENOTCONV;
+  if (st == ST_TIMEOUT) c->err = "a grid-barrier wait of the persistent kernel exceeded its time limit";
   if (st == ST_STALLED) c->err = "iterative refinement stalled: a restart did not lower the true residual";
   if (res) {
     const size_t k = (size_t)iters + 1;

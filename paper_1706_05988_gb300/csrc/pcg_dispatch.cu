@@ -2,6 +2,7 @@
 #include <utility>
 
 #include "pcg_kernels.cuh"
+#include "pcg_persistent.cuh"
 
 // Largest number of unknowns per thread for stencil operators (2 = 128-bit accesses).
 #ifndef PCG_STENCIL_MAX_VEC
@@ -114,6 +115,31 @@ cudaError_t launch_cg_update(const OpDesc& d, const Launch& L, Vecs v, State* st
 }
 cudaError_t launch_cg_p(const OpDesc& d, const Launch& L, Vecs v, State* st, Hist h) {
   return with_op(d, [&](auto op) { return K<decltype(op)>::cg_p(op, L, v, st, h); });
+}
+int grid_for_persistent(const OpDesc& d) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  int per_sm = 0;
+  with_op(d, [&](auto op) {
+    per_sm = PersistentKernels<std::decay_t<decltype(op)>>::blocks_per_sm();
+    return cudaSuccess;
+  });
+  if (per_sm <= 0) return 0;
+  const long long units = d.n / op_vec(d);
+  long long g = (long long)sms * per_sm;       // every block resident: a cooperative launch
+  const long long need = (units + kBlock - 1) / kBlock;
+  if (need < g) g = need;
+  if (g < 1) g = 1;
+  if (g > kMaxPartialBlocks / 2) g = kMaxPartialBlocks / 2;   // two partial slots per block
+  return (int)g;
+}
+cudaError_t launch_spcg_persistent(const OpDesc& d, int grid, cudaStream_t stream, Vecs v, State* st, Hist h,
+                                   double* partials, unsigned long long timeout_ns, unsigned phantoms) {
+  return with_op(d, [&](auto op) {
+    return PersistentKernels<std::decay_t<decltype(op)>>::spcg(op, grid, stream, v, st, h, partials, timeout_ns,
+                                                                phantoms);
+  });
 }
 cudaError_t launch_apply(const OpDesc& d, const Launch& L, const double* x, double* y) {
   return with_op(d, [&](auto op) { return K<decltype(op)>::apply(op, L, x, y); });

@@ -10,7 +10,9 @@ namespace pcgk {
 // ST_RESTART (mixed precision only): the inner iteration reached its tolerance;
 // the restart kernels recompute the true residual in FP64 and restart Algorithm 3.
 // ST_STALLED (mixed precision only): a restart did not lower the true residual.
-enum : int { ST_RUNNING = 0, ST_CONVERGED = 1, ST_BREAKDOWN = 2, ST_MAXIT = 3, ST_RESTART = 4, ST_STALLED = 5 };
+// ST_TIMEOUT (persistent kernel only): a grid-barrier wait exceeded its time limit.
+enum : int { ST_RUNNING = 0, ST_CONVERGED = 1, ST_BREAKDOWN = 2, ST_MAXIT = 3, ST_RESTART = 4, ST_STALLED = 5,
+             ST_TIMEOUT = 6 };
 
 struct State {
   int iter;              // index i of the next iteration to execute (or of the last iterate once stopped)
@@ -28,6 +30,9 @@ struct State {
   double rprev;          // true residual at the previous restart
   int restarts;          // restarts performed
   int max_restarts;
+  // grid barrier of the persistent kernel
+  unsigned int bar_count;
+  unsigned int bar_gen;
 };
 
 // Per-iteration histories (device arrays of maxit + 1 entries).
@@ -78,6 +83,11 @@ cudaError_t launch_cg_spmv(const OpDesc& op, const Launch& L, Vecs v, State* st,
 cudaError_t launch_cg_update(const OpDesc& op, const Launch& L, Vecs v, State* st, Hist h, double* partials);
 cudaError_t launch_cg_p(const OpDesc& op, const Launch& L, Vecs v, State* st, Hist h);
 cudaError_t launch_apply(const OpDesc& op, const Launch& L, const double* x, double* y);
+
+// Persistent cooperative form of the iteration (pcg_persistent.cuh).
+int grid_for_persistent(const OpDesc& op);
+cudaError_t launch_spcg_persistent(const OpDesc& op, int grid, cudaStream_t stream, Vecs v, State* st, Hist h,
+                                   double* partials, unsigned long long timeout_ns, unsigned phantoms);
 
 // Mixed precision (pcg_mixed.cuh): FP32 w, z, s, p stored in the FP64 buffers of Vecs.
 enum { KM_RESTART = 0, KM_W0, KM_ITER, KM_NKINDS };

@@ -2,6 +2,7 @@
 // variable-coefficient rows; one or two unknowns per thread).
 #define PCG_KERNELS_IMPL
 #include "pcg_kernels.cuh"
+#include "pcg_persistent.cuh"
 
 namespace pcgk {
 template struct Kernels<StencilOp<2, ST_LAP_FP64, 1>>;
@@ -10,4 +11,10 @@ template struct Kernels<StencilOp<2, ST_LAP_FIXED, 1>>;
 template struct Kernels<StencilOp<2, ST_LAP_FIXED, 2>>;
 template struct Kernels<StencilOp<2, ST_VAR, 1>>;
 template struct Kernels<StencilOp<2, ST_VAR, 2>>;
+template struct PersistentKernels<StencilOp<2, ST_LAP_FP64, 1>>;
+template struct PersistentKernels<StencilOp<2, ST_LAP_FP64, 2>>;
+template struct PersistentKernels<StencilOp<2, ST_LAP_FIXED, 1>>;
+template struct PersistentKernels<StencilOp<2, ST_LAP_FIXED, 2>>;
+template struct PersistentKernels<StencilOp<2, ST_VAR, 1>>;
+template struct PersistentKernels<StencilOp<2, ST_VAR, 2>>;
 }  // namespace pcgk

@@ -29,7 +29,8 @@ PCG_DEVICE_PTRS = 0x1
 PCG_PROFILE = 0x2
 PCG_STENCIL_FP64_SUM = 0x4
 # pcg_set_param parameters
-PCG_PARAM_MIXED_ETA, PCG_PARAM_MAX_RESTARTS = 1, 2
+PCG_PARAM_MIXED_ETA, PCG_PARAM_MAX_RESTARTS, PCG_PARAM_BARRIER_TIMEOUT_MS, PCG_PARAM_TEST_BARRIER_PHANTOMS = 1, 2, 3, 4
+PCG_PERSISTENT = 0x8
 
 METHODS = {"cg": PCG_CG, "pcg": PCG_PCG, "spcg": PCG_SPCG}
 
