@@ -147,6 +147,46 @@ def cpu_oracle_rate(P, b, iters: int) -> tuple[float, float]:
     return iters / dt, dt
 
 
+def batch_measure(pkg, S, nsys: int, seed: int = 0) -> dict:
+    """Solves/s of nsys 2D FV systems (sides U{32..128}, kappa = 10^U[-2,2] per cell, b ~ N(0,1),
+    tol 1e-8, FP64 shifted p-CG with sigma = half the median diagonal): one batched launch against
+    the single-system entry point (sampled), both through host buffers."""
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(seed)
+    sides = rng.integers(32, 129, size=nsys)
+    probs = [S.varcoef_2d(int(L), int(L), seed=seed + i) for i, L in enumerate(sides)]
+    bs = [S.normal(1000 + i, P.n) for i, P in enumerate(probs)]
+    sig = [0.5 * float(np.median(P.diag)) for P in probs]
+    with pkg.Batch(probs) as bt:
+        c, _ = bt.autotune(bs, sig, probe_iters=100)
+        bt.solve(bs, sig, tol=1e-8, maxit=100000)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, it, st, tr = bt.solve(bs, sig, tol=1e-8, maxit=100000)
+        torch.cuda.synchronize()
+        tb = time.perf_counter() - t0
+        kms = bt.last_kernel_ms()
+    k = min(nsys, 16)
+    idx = np.linspace(0, nsys - 1, k).astype(int)
+    t1 = 0.0
+    for i in idx:
+        with pkg.Solver(probs[i]) as one:
+            one.solve(bs[i], method="spcg", sigma=sig[i], tol=1e-8, maxit=100000)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            one.solve(bs[i], method="spcg", sigma=sig[i], tol=1e-8, maxit=100000)
+            torch.cuda.synchronize()
+            t1 += time.perf_counter() - t0
+    one_rate = k / t1
+    return {"workload": f"{nsys} 2D variable-coefficient 5-point systems, sides U{{32..128}}, kappa 10^U[-2,2] "
+                        "per cell, b ~ N(0,1), tol 1e-8, FP64",
+            "solves_per_s": nsys / tb, "kernel_ms": kms, "cluster_size": c, "converged": int(np.sum(st == 0)),
+            "max_true_relres": float(np.max(tr)), "mean_iters": float(np.mean(it)),
+            "one_at_a_time_solves_per_s": one_rate, "one_at_a_time_sample": int(k),
+            "speedup": (nsys / tb) / one_rate}
+
+
 def run_reference(args):
     """The oracle, as it stands, on the host: bounded samples of the same workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -289,6 +329,11 @@ def run_ours(args):
                           "ms_per_iteration": k_s * 1e3, "achieved_gbs": alg_bytes / k_s / 1e9,
                           "frac": alg_bytes / k_s / 1e9 / peak}
 
+    # batch of independent 2D variable-coefficient systems in one persistent launch vs one at a time
+    batch = None
+    if not args.no_batch:
+        batch = batch_measure(pkg, S, args.batch_systems)
+
     # the same workload as CSR (int32 indices): config's second form, one timed step
     csr = None
     if not args.no_csr:
@@ -327,7 +372,7 @@ def run_ours(args):
                                       "per SM x 152 SMs x 2.07 GHz (ncu sm__sass_thread_inst_executed_op_dfma "
                                       "peak_sustained)"},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
-                "csr_int32": csr, "persistent": persistent}
+                "csr_int32": csr, "persistent": persistent, "batch": batch}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -345,6 +390,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timing")
     ap.add_argument("--no-csr", action="store_true", help="skip the CSR form of the workload")
     ap.add_argument("--no-persistent", action="store_true", help="skip the persistent-kernel measurement")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve measurement")
+    ap.add_argument("--batch-systems", type=int, default=128, help="systems in the batched-solve measurement")
     ap.add_argument("--size", type=int, default=N_SIDE, help="grid side (default: the 256^3 workload)")
     args = ap.parse_args()
     globals()["N_SIDE"] = args.size

@@ -176,6 +176,43 @@ pcg_status pcg_select_sigma(pcg_ctx *ctx, const double *b, int32_t iters, const 
 pcg_status pcg_psi(pcg_ctx *ctx, const double *alpha, const double *beta, int32_t i, const double *grid,
                    int32_t ngrid, double *psi_out);
 
+/* ---- Batches of independent systems (one persistent launch) ------------------
+ * Many systems A_k x_k = b_k, each solved by Algorithm 3 (M = I, binary64) with its
+ * own shift, advance in one launch: every thread-block cluster takes systems from a
+ * device queue (largest first) and runs all iterations of one system, its blocks
+ * sharing the unknowns; the dot products reduce through distributed shared memory
+ * and one cluster barrier per iteration replaces the paper's global reduction.
+ * All systems of a batch share one operator family (2D or 3D stencil, constant or
+ * variable coefficients, or CSR) but not their sizes. */
+typedef struct pcg_batch pcg_batch;
+
+/* Copy nsys operators (host arrays, pcg_matrix as for pcg_create) to the device.
+ * flags must be 0.  Errors: PCG_EINVAL (mixed families, invalid description),
+ * PCG_ENOMEM, PCG_ECUDA. */
+pcg_status pcg_batch_create(const pcg_matrix *systems, int32_t nsys, uint32_t flags, pcg_batch **out);
+
+/* Solve every system: b[k] and x_out[k] are host arrays of n_k doubles; method
+ * PCG_PCG or PCG_SPCG with sigma[k] >= 0 (sigma may be NULL for PCG_PCG); x_0 = 0;
+ * stop at ||r_i|| <= tol ||b_k|| or after maxit iterations.  iters[k], status[k]
+ * (a pcg_status per system) and true_relres[k] = ||b_k - A_k x_k|| / ||b_k|| may be
+ * NULL.  Returns PCG_OK when every system converged, else PCG_ENOTCONV. */
+pcg_status pcg_batch_solve(pcg_batch *batch, const double *const *b, double *const *x_out, int32_t method,
+                           const double *sigma, double tol, int32_t maxit, int32_t *iters, int32_t *status,
+                           double *true_relres);
+
+/* Autotuner: times probe_iters iterations of every system for each cluster size in
+ * {1, 2, 4, 8, 16} and keeps the fastest for later solves; cluster_out (may be NULL)
+ * receives it, ms_out[5] (may be NULL) the kernel time of each candidate (NaN where a
+ * size cannot be launched).  pcg_batch_set_cluster sets the size directly. */
+pcg_status pcg_batch_autotune(pcg_batch *batch, const double *const *b, const double *sigma, int32_t probe_iters,
+                              int32_t *cluster_out, double *ms_out);
+pcg_status pcg_batch_set_cluster(pcg_batch *batch, int32_t cluster_size);
+
+/* CUDA-event time (ms) of the last batch kernel. */
+pcg_status pcg_batch_last_kernel_ms(const pcg_batch *batch, double *ms);
+
+void pcg_batch_destroy(pcg_batch *batch);
+
 /* Largest n accepted by pcg_true_residual_noalloc. */
 #define PCG_NOALLOC_MAX_N 16777216
 

@@ -1,0 +1,633 @@
+// Batched shifted pipelined CG: many independent systems in one persistent launch.
+//
+// Each thread-block cluster takes systems from a device work queue (largest first)
+// and runs every iteration of Algorithm 3 (M = I, binary64) for that system itself:
+// the blocks of the cluster split the system's unknowns, the dot products reduce
+// warp -> block -> cluster through distributed shared memory, and one cluster
+// barrier per iteration stands in for the global reduction.  Every block sums
+// the cluster's partials in rank order, so all blocks hold identical scalars and
+// take the same stop decision.  Blocks of different clusters never wait on each
+// other; the only barrier is the hardware cluster barrier.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+#include <new>
+#include <numeric>
+#include <string>
+#include <type_traits>
+#include <utility>
+#include <vector>
+
+#define PCG_KERNELS_IMPL
+#include "../../include/pcg.h"
+#include "pcg_kernels.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace pcgk {
+namespace {
+
+// One system of the batch (device table).
+struct BatchSys {
+  int layout, n, nx, ny, nz, pad;
+  const double *diag, *ax, *ay, *az;   // variable coefficients (stencils)
+  const int *row_ptr, *col;            // CSR
+  const double* val;
+  long long off;                       // offset of the system's unknowns in every batch vector
+  double sigma;
+};
+
+// Per-system results written by the kernel.
+struct BatchOut {
+  int iters, status;
+  double bnorm, true_res;
+};
+
+struct BatchVecs {
+  const double* b;
+  double *x, *r, *w0, *w1, *z, *s, *p;
+};
+
+
+template <int F>
+struct FamilyOp;
+template <>
+struct FamilyOp<0> {
+  using T = StencilOp<2, ST_LAP_FIXED, 1>;
+};
+template <>
+struct FamilyOp<1> {
+  using T = StencilOp<2, ST_VAR, 1>;
+};
+template <>
+struct FamilyOp<2> {
+  using T = StencilOp<3, ST_LAP_FIXED, 1>;
+};
+template <>
+struct FamilyOp<3> {
+  using T = StencilOp<3, ST_VAR, 1>;
+};
+template <>
+struct FamilyOp<4> {
+  using T = CsrOp;
+};
+
+template <int F>
+__device__ __forceinline__ typename FamilyOp<F>::T make_op(const BatchSys& d) {
+  typename FamilyOp<F>::T o;
+  if constexpr (F == 4) {
+    o.n = d.n;
+    o.row_ptr = d.row_ptr;
+    o.col = d.col;
+    o.val = d.val;
+  } else {
+    o.n = d.n;
+    o.nx = d.nx;
+    o.ny = d.ny;
+    o.nz = d.nz;
+    o.nxny = d.nx * d.ny;
+    o.diag = d.diag;
+    o.ax = d.ax;
+    o.ay = d.ay;
+    o.az = d.az;
+  }
+  return o;
+}
+
+// Sum of NV values over the cluster: warp shuffles, block (shared memory), then the
+// cluster's blocks read each other's block sums through DSMEM in rank order.
+// `slot` alternates between calls so that one cluster barrier per call suffices.
+template <int NV>
+__device__ __forceinline__ void cluster_sum(cg::cluster_group& cl, double (&v)[NV], double (*part)[4], int slot,
+                                            double (&tot)[NV]) {
+  __shared__ double sh[kWarps][4];
+  __shared__ double bc[4];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sh[wid][q] = v[q];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double a = 0.0;
+      for (int k = 0; k < kWarps; ++k) a += sh[k][q];
+      part[slot][q] = a;
+    }
+  }
+  cl.sync();   // release/acquire at cluster scope: the partials and every global write are visible
+  if (threadIdx.x == 0) {
+    const unsigned C = cl.num_blocks();
+    double a[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) a[q] = 0.0;
+    for (unsigned rk = 0; rk < C; ++rk) {
+      const double* rp = cl.map_shared_rank(&part[slot][0], rk);
+#pragma unroll
+      for (int q = 0; q < NV; ++q) a[q] += rp[q];
+    }
+#pragma unroll
+    for (int q = 0; q < NV; ++q) bc[q] = a[q];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NV; ++q) tot[q] = bc[q];
+  __syncthreads();
+}
+
+template <int F>
+__global__ void __launch_bounds__(kBlock) k_batch(const BatchSys* __restrict__ sys, const int* __restrict__ order,
+                                                  int nsys, int* next, BatchVecs V, BatchOut* out, double tol,
+                                                  int maxit) {
+  using Op = typename FamilyOp<F>::T;
+  cg::cluster_group cl = cg::this_cluster();
+  const unsigned rank = cl.block_rank(), C = cl.num_blocks();
+  __shared__ double part[2][4];
+  __shared__ int s_task;
+  int slot = 0;
+  for (;;) {
+    if (rank == 0 && threadIdx.x == 0) s_task = atomicAdd(next, 1);
+    cl.sync();
+    const int task = *cl.map_shared_rank(&s_task, 0);
+    cl.sync();                       // every block has read the task before rank 0 overwrites it
+    if (task >= nsys) return;
+    const int k = order[task];
+    const BatchSys d = sys[k];
+    const Op op = make_op<F>(d);
+    const double sigma = d.sigma;
+    const long long off = d.off;
+    const double* b = V.b + off;
+    double *x = V.x + off, *r = V.r + off, *w0 = V.w0 + off, *w1 = V.w1 + off, *z = V.z + off, *s = V.s + off,
+           *p = V.p + off;
+    const unsigned nc = (unsigned)d.n;
+    const auto stp = op.step(C * kBlock);
+    const int first = (int)(rank * kBlock + threadIdx.x);
+
+    // r_0 = b (x_0 = 0), ||b||
+    double bb = 0.0;
+    for (unsigned i = first; i < nc; i += C * kBlock) {
+      const double bv = b[i];
+      r[i] = bv;
+      x[i] = 0.0;
+      bb = fma(bv, bv, bb);
+    }
+    double t1[1] = {bb}, o1[1];
+    cluster_sum<1>(cl, t1, part, slot, o1);
+    slot ^= 1;
+    const double bnorm = sqrt(o1[0]);
+    const double tol_abs = tol * bnorm;
+
+    // w_0 = A r_0 - sigma r_0; z = s = p = 0; gamma_0, (w_0, r_0)
+    double g = 0.0, o = 0.0;
+    for (auto q = op.cursor(first); q.c0 < nc; op.advance(q, stp)) {
+      double rc[1], ar[1];
+      op.apply(r, q, rc, ar);
+      const double wv = fma(-sigma, rc[0], ar[0]);
+      w0[q.c0] = wv;
+      z[q.c0] = 0.0;
+      s[q.c0] = 0.0;
+      p[q.c0] = 0.0;
+      g = fma(rc[0], rc[0], g);
+      o = fma(wv, rc[0], o);
+    }
+    double t2[2] = {g, o}, o2[2];
+    cluster_sum<2>(cl, t2, part, slot, o2);
+    slot ^= 1;
+    double gamma = o2[0], delta = o2[1] + sigma * o2[0];
+    int status = ST_RUNNING, it = 0;
+    double alpha = 0.0, beta = 0.0;
+    if (tol_abs > 0.0 && sqrt(gamma) <= tol_abs) {
+      status = ST_CONVERGED;
+    } else if (maxit <= 0) {
+      status = ST_MAXIT;
+    } else if (gamma == 0.0) {
+      status = ST_CONVERGED;
+    } else if (!(delta > 0.0) || !isfinite(delta)) {
+      status = ST_BREAKDOWN;
+    } else {
+      alpha = gamma / delta;
+    }
+    while (status == ST_RUNNING) {
+      const double asg = alpha * sigma;
+      const double* __restrict__ w = (it & 1) ? w1 : w0;
+      double* __restrict__ wn = (it & 1) ? w0 : w1;
+      g = 0.0;
+      o = 0.0;
+      for (auto q = op.cursor(first); q.c0 < nc; op.advance(q, stp)) {
+        const unsigned c = q.c0;
+        double wc[1], nv[1];
+        op.apply(w, q, wc, nv);
+        const double zz = fma(beta, z[c], nv[0]);
+        const double ss = fma(beta, s[c], wc[0]);
+        const double rr = r[c];
+        const double pp = fma(beta, p[c], rr);
+        x[c] = fma(alpha, pp, x[c]);
+        const double rn = fma(-alpha, ss, fma(-asg, pp, rr));
+        const double wv = fma(-alpha, zz, wc[0]);
+        z[c] = zz;
+        s[c] = ss;
+        p[c] = pp;
+        r[c] = rn;
+        wn[c] = wv;
+        g = fma(rn, rn, g);
+        o = fma(wv, rn, o);
+      }
+      double t[2] = {g, o}, tt[2];
+      cluster_sum<2>(cl, t, part, slot, tt);
+      slot ^= 1;
+      ++it;
+      const double gn = tt[0], dn = tt[1] + sigma * tt[0];
+      if (tol_abs > 0.0 && sqrt(gn) <= tol_abs) {
+        status = ST_CONVERGED;
+      } else if (it >= maxit) {
+        status = ST_MAXIT;
+      } else if (gn == 0.0) {
+        status = ST_CONVERGED;
+      } else {
+        const double bt = gn / gamma;
+        const double den = dn / gn - bt / alpha;
+        if (!(den > 0.0) || !isfinite(den)) {
+          status = ST_BREAKDOWN;
+        } else {
+          alpha = 1.0 / den;
+          beta = bt;
+        }
+      }
+      gamma = gn;
+    }
+
+    // true residual ||b - A x||
+    double tr = 0.0;
+    for (auto q = op.cursor(first); q.c0 < nc; op.advance(q, stp)) {
+      double xc[1], ax[1];
+      op.apply(x, q, xc, ax);
+      const double e = b[q.c0] - ax[0];
+      tr = fma(e, e, tr);
+    }
+    double t3[1] = {tr}, o3[1];
+    cluster_sum<1>(cl, t3, part, slot, o3);
+    slot ^= 1;
+    if (rank == 0 && threadIdx.x == 0) {
+      out[k].iters = it;
+      out[k].status = status;
+      out[k].bnorm = bnorm;
+      out[k].true_res = sqrt(o3[0]);
+    }
+  }
+}
+
+template <int F>
+cudaError_t launch_batch(int clusters, int csize, cudaStream_t stream, const BatchSys* sys, const int* order,
+                         int nsys, int* next, BatchVecs V, BatchOut* out, double tol, int maxit) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(clusters * csize);
+  cfg.blockDim = dim3(kBlock);
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_batch<F>, sys, order, nsys, next, V, out, tol, maxit);
+}
+
+template <int F>
+int max_clusters(int csize) {
+  if (csize > 8) {
+    if (cudaFuncSetAttribute(k_batch<F>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) return 0;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(csize);
+  cfg.blockDim = dim3(kBlock);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  return cudaOccupancyMaxActiveClusters(&n, k_batch<F>, &cfg) == cudaSuccess ? n : 0;
+}
+
+template <class Fn>
+cudaError_t with_family(int fam, Fn&& fn) {
+  switch (fam) {
+    case 0: return fn(std::integral_constant<int, 0>{});
+    case 1: return fn(std::integral_constant<int, 1>{});
+    case 2: return fn(std::integral_constant<int, 2>{});
+    case 3: return fn(std::integral_constant<int, 3>{});
+    case 4: return fn(std::integral_constant<int, 4>{});
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+}  // namespace pcgk
+
+using namespace pcgk;
+
+struct pcg_batch {
+  int device = 0;
+  int family = -1;
+  int nsys = 0;
+  std::vector<int> n;             // unknowns per system
+  std::vector<long long> off;     // offsets in the batch vectors
+  long long total = 0;            // padded length of every batch vector
+  std::vector<void*> owned;
+  std::vector<BatchSys> host_sys;
+  BatchSys* d_sys = nullptr;
+  int* d_order = nullptr;
+  int* d_next = nullptr;
+  BatchOut* d_out = nullptr;
+  double* d_vec = nullptr;        // b, x, r, w0, w1, z, s, p
+  double* h_stage = nullptr;      // pinned staging of b / x (total doubles)
+  cudaStream_t stream = nullptr;
+  int csize = 8;
+  int tuned = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  double last_kernel_ms = 0.0;
+};
+
+namespace {
+
+pcg_status balloc(pcg_batch* B, void** p, size_t bytes) {
+  if (cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) {
+    cudaGetLastError();
+    return PCG_ENOMEM;
+  }
+  B->owned.push_back(*p);
+  return PCG_OK;
+}
+
+int family_of(const pcg_matrix& A) {
+  if (A.layout == PCG_CSR32) return 4;
+  if (A.layout == PCG_STENCIL5_2D) return A.diag ? 1 : 0;
+  if (A.layout == PCG_STENCIL7_3D) return A.diag ? 3 : 2;
+  return -1;
+}
+
+BatchVecs vecs_of(pcg_batch* B) {
+  const long long t = B->total;
+  double* base = B->d_vec;
+  BatchVecs V;
+  V.b = base;
+  V.x = base + t;
+  V.r = base + 2 * t;
+  V.w0 = base + 3 * t;
+  V.w1 = base + 4 * t;
+  V.z = base + 5 * t;
+  V.s = base + 6 * t;
+  V.p = base + 7 * t;
+  return V;
+}
+
+int max_clusters_of(int fam, int csize) {
+  switch (fam) {
+    case 0: return max_clusters<0>(csize);
+    case 1: return max_clusters<1>(csize);
+    case 2: return max_clusters<2>(csize);
+    case 3: return max_clusters<3>(csize);
+    case 4: return max_clusters<4>(csize);
+    default: return 0;
+  }
+}
+
+pcg_status run_batch(pcg_batch* B, int csize, double tol, int maxit) {
+  const int maxc = max_clusters_of(B->family, csize);
+  if (maxc <= 0) {
+    cudaGetLastError();
+    return PCG_ECUDA;
+  }
+  const int clusters = std::min(maxc, B->nsys);
+  if (cudaMemsetAsync(B->d_next, 0, sizeof(int), B->stream) != cudaSuccess) return PCG_ECUDA;
+  const BatchVecs V = vecs_of(B);
+  if (cudaEventRecord(B->e0, B->stream) != cudaSuccess) return PCG_ECUDA;
+  const cudaError_t e = with_family(B->family, [&](auto F) {
+    return launch_batch<decltype(F)::value>(clusters, csize, B->stream, B->d_sys, B->d_order, B->nsys, B->d_next, V,
+                                            B->d_out, tol, maxit);
+  });
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return PCG_ECUDA;
+  }
+  if (cudaEventRecord(B->e1, B->stream) != cudaSuccess) return PCG_ECUDA;
+  if (cudaStreamSynchronize(B->stream) != cudaSuccess) return PCG_ECUDA;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, B->e0, B->e1);
+  B->last_kernel_ms = ms;
+  return PCG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pcg_status pcg_batch_create(const pcg_matrix* systems, int32_t nsys, uint32_t flags, pcg_batch** out) {
+  if (!out) return PCG_EINVAL;
+  *out = nullptr;
+  if (!systems || nsys < 1 || flags != 0) return PCG_EINVAL;
+  const int fam = family_of(systems[0]);
+  if (fam < 0) return PCG_EINVAL;
+  pcg_batch* B = new (std::nothrow) pcg_batch();
+  if (!B) return PCG_ENOMEM;
+  auto bail = [&](pcg_status s) {
+    pcg_batch_destroy(B);
+    return s;
+  };
+  B->family = fam;
+  B->nsys = nsys;
+  if (cudaGetDevice(&B->device) != cudaSuccess) return bail(PCG_ECUDA);
+  long long total = 0;
+  for (int k = 0; k < nsys; ++k) {
+    const pcg_matrix& A = systems[k];
+    if (family_of(A) != fam) return bail(PCG_EINVAL);   // one operator family per batch
+    long long n;
+    if (fam == 4) {
+      if (A.n < 1 || A.n > INT32_MAX || A.nnz < 0 || A.nnz > INT32_MAX || !A.row_ptr || !A.col || !A.val)
+        return bail(PCG_EINVAL);
+      if (A.row_ptr[0] != 0 || A.row_ptr[A.n] != A.nnz) return bail(PCG_EINVAL);
+      for (long long i = 0; i < A.nnz; ++i)
+        if (A.col[i] < 0 || A.col[i] >= A.n) return bail(PCG_EINVAL);
+      n = A.n;
+    } else {
+      const long long nz = A.layout == PCG_STENCIL7_3D ? A.nz : 1;
+      if (A.nx < 1 || A.ny < 1 || nz < 1) return bail(PCG_EINVAL);
+      n = A.nx * A.ny * nz;
+      if ((fam == 1 || fam == 3) && (!A.ax || !A.ay || (fam == 3 && !A.az))) return bail(PCG_EINVAL);
+    }
+    if (n > INT32_MAX - 64) return bail(PCG_EINVAL);
+    B->n.push_back((int)n);
+    B->off.push_back(total);
+    total += (n + 31) & ~31LL;
+  }
+  B->total = total;
+  // device copies of every operator's arrays
+  B->host_sys.resize(nsys);
+  for (int k = 0; k < nsys; ++k) {
+    const pcg_matrix& A = systems[k];
+    BatchSys d{};
+    d.layout = A.layout;
+    d.n = B->n[k];
+    d.off = B->off[k];
+    auto put = [&](const void* src, size_t bytes, const void** dst) -> pcg_status {
+      void* p;
+      pcg_status s = balloc(B, &p, bytes);
+      if (s != PCG_OK) return s;
+      if (cudaMemcpy(p, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return PCG_ECUDA;
+      *dst = p;
+      return PCG_OK;
+    };
+    pcg_status s = PCG_OK;
+    if (fam == 4) {
+      s = put(A.row_ptr, (A.n + 1) * sizeof(int), (const void**)&d.row_ptr);
+      if (s == PCG_OK) s = put(A.col, A.nnz * sizeof(int), (const void**)&d.col);
+      if (s == PCG_OK) s = put(A.val, A.nnz * sizeof(double), (const void**)&d.val);
+    } else {
+      d.nx = (int)A.nx;
+      d.ny = (int)A.ny;
+      d.nz = A.layout == PCG_STENCIL7_3D ? (int)A.nz : 1;
+      if (fam == 1 || fam == 3) {
+        s = put(A.diag, d.n * sizeof(double), (const void**)&d.diag);
+        if (s == PCG_OK) s = put(A.ax, d.n * sizeof(double), (const void**)&d.ax);
+        if (s == PCG_OK) s = put(A.ay, d.n * sizeof(double), (const void**)&d.ay);
+        if (s == PCG_OK && fam == 3) s = put(A.az, d.n * sizeof(double), (const void**)&d.az);
+      }
+    }
+    if (s != PCG_OK) return bail(s);
+    B->host_sys[k] = d;
+  }
+  void* p;
+  if (balloc(B, &p, nsys * sizeof(BatchSys)) != PCG_OK) return bail(PCG_ENOMEM);
+  B->d_sys = (BatchSys*)p;
+  if (balloc(B, &p, nsys * sizeof(int)) != PCG_OK) return bail(PCG_ENOMEM);
+  B->d_order = (int*)p;
+  if (balloc(B, &p, sizeof(int)) != PCG_OK) return bail(PCG_ENOMEM);
+  B->d_next = (int*)p;
+  if (balloc(B, &p, nsys * sizeof(BatchOut)) != PCG_OK) return bail(PCG_ENOMEM);
+  B->d_out = (BatchOut*)p;
+  if (balloc(B, &p, 8 * (size_t)total * sizeof(double)) != PCG_OK) return bail(PCG_ENOMEM);
+  B->d_vec = (double*)p;
+  if (cudaMallocHost(&p, (size_t)total * sizeof(double)) != cudaSuccess) return bail(PCG_ENOMEM);
+  B->h_stage = (double*)p;
+  // largest systems first: the queue then balances the clusters' work
+  std::vector<int> order(nsys);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return B->n[a] > B->n[b]; });
+  if (cudaMemcpy(B->d_order, order.data(), nsys * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+    return bail(PCG_ECUDA);
+  if (cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(PCG_ECUDA);
+  if (cudaEventCreate(&B->e0) != cudaSuccess || cudaEventCreate(&B->e1) != cudaSuccess) return bail(PCG_ECUDA);
+  *out = B;
+  return PCG_OK;
+}
+
+void pcg_batch_destroy(pcg_batch* B) {
+  if (!B) return;
+  if (B->stream) cudaStreamSynchronize(B->stream);
+  for (void* p : B->owned) cudaFree(p);
+  if (B->h_stage) cudaFreeHost(B->h_stage);
+  if (B->e0) cudaEventDestroy(B->e0);
+  if (B->e1) cudaEventDestroy(B->e1);
+  if (B->stream) cudaStreamDestroy(B->stream);
+  cudaGetLastError();
+  delete B;
+}
+
+pcg_status pcg_batch_solve(pcg_batch* B, const double* const* b, double* const* x_out, int32_t method,
+                           const double* sigma, double tol, int32_t maxit, int32_t* iters, int32_t* status,
+                           double* true_relres) {
+  if (!B || !b || !x_out) return PCG_EINVAL;
+  if (method != PCG_PCG && method != PCG_SPCG) return PCG_EINVAL;
+  if (!(tol >= 0.0) || !isfinite(tol) || maxit < 0) return PCG_EINVAL;
+  if (method == PCG_SPCG && !sigma) return PCG_EINVAL;
+  for (int k = 0; k < B->nsys; ++k) {
+    if (!b[k] || !x_out[k]) return PCG_EINVAL;
+    const double sg = method == PCG_SPCG ? sigma[k] : 0.0;
+    if (!(sg >= 0.0) || !isfinite(sg)) return PCG_EINVAL;
+    B->host_sys[k].sigma = sg;
+  }
+  if (cudaSetDevice(B->device) != cudaSuccess) return PCG_ECUDA;
+  if (cudaMemcpyAsync(B->d_sys, B->host_sys.data(), B->nsys * sizeof(BatchSys), cudaMemcpyHostToDevice, B->stream) !=
+      cudaSuccess)
+    return PCG_ECUDA;
+  for (int k = 0; k < B->nsys; ++k) std::copy(b[k], b[k] + B->n[k], B->h_stage + B->off[k]);
+  const BatchVecs V = vecs_of(B);
+  if (cudaMemcpyAsync((double*)V.b, B->h_stage, (size_t)B->total * sizeof(double), cudaMemcpyHostToDevice,
+                      B->stream) != cudaSuccess)
+    return PCG_ECUDA;
+  pcg_status s = run_batch(B, B->csize, tol, maxit);
+  if (s != PCG_OK) return s;
+  if (cudaMemcpyAsync(B->h_stage, V.x, (size_t)B->total * sizeof(double), cudaMemcpyDeviceToHost, B->stream) !=
+      cudaSuccess)
+    return PCG_ECUDA;
+  std::vector<BatchOut> o(B->nsys);
+  if (cudaMemcpyAsync(o.data(), B->d_out, B->nsys * sizeof(BatchOut), cudaMemcpyDeviceToHost, B->stream) !=
+      cudaSuccess)
+    return PCG_ECUDA;
+  if (cudaStreamSynchronize(B->stream) != cudaSuccess) return PCG_ECUDA;
+  bool all_ok = true;
+  for (int k = 0; k < B->nsys; ++k) {
+    std::copy(B->h_stage + B->off[k], B->h_stage + B->off[k] + B->n[k], x_out[k]);
+    const int st = o[k].status;
+    const int code = st == ST_CONVERGED ? PCG_OK : st == ST_BREAKDOWN ? PCG_EBREAKDOWN : PCG_ENOTCONV;
+    if (iters) iters[k] = o[k].iters;
+    if (status) status[k] = code;
+    if (true_relres) true_relres[k] = o[k].bnorm > 0 ? o[k].true_res / o[k].bnorm : o[k].true_res;
+    all_ok = all_ok && code == PCG_OK;
+  }
+  return all_ok ? PCG_OK : PCG_ENOTCONV;
+}
+
+pcg_status pcg_batch_autotune(pcg_batch* B, const double* const* b, const double* sigma, int32_t probe_iters,
+                              int32_t* cluster_out, double* ms_out) {
+  if (!B || !b || !sigma || probe_iters < 1) return PCG_EINVAL;
+  std::vector<double*> xs(B->nsys);
+  std::vector<std::vector<double>> store(B->nsys);
+  for (int k = 0; k < B->nsys; ++k) {
+    store[k].resize(B->n[k]);
+    xs[k] = store[k].data();
+  }
+  const int cand[] = {1, 2, 4, 8, 16};
+  double best = INFINITY;
+  int best_c = B->csize;
+  for (int ci = 0; ci < 5; ++ci) {
+    const int c = cand[ci];
+    B->csize = c;
+    if (ms_out) ms_out[ci] = NAN;
+    pcg_status s = pcg_batch_solve(B, b, xs.data(), PCG_SPCG, sigma, 0.0, probe_iters, nullptr, nullptr, nullptr);
+    if (s != PCG_OK && s != PCG_ENOTCONV) continue;   // a shape this GPU cannot launch is skipped
+    if (ms_out) ms_out[ci] = B->last_kernel_ms;
+    if (B->last_kernel_ms < best) {
+      best = B->last_kernel_ms;
+      best_c = c;
+    }
+  }
+  B->csize = best_c;
+  B->tuned = 1;
+  if (cluster_out) *cluster_out = best_c;
+  return PCG_OK;
+}
+
+pcg_status pcg_batch_set_cluster(pcg_batch* B, int32_t cluster_size) {
+  if (!B) return PCG_EINVAL;
+  if (cluster_size != 1 && cluster_size != 2 && cluster_size != 4 && cluster_size != 8 && cluster_size != 16)
+    return PCG_EINVAL;
+  B->csize = cluster_size;
+  return PCG_OK;
+}
+
+pcg_status pcg_batch_last_kernel_ms(const pcg_batch* B, double* ms) {
+  if (!B || !ms) return PCG_EINVAL;
+  *ms = B->last_kernel_ms;
+  return PCG_OK;
+}
+
+}  // extern "C"

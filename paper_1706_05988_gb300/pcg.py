@@ -80,13 +80,21 @@ def lib() -> ctypes.CDLL:
         L.pcg_psi.argtypes = [vp, vp, vp, i32, vp, i32, vp]
         L.pcg_apply.argtypes = [vp, vp, vp]
         L.pcg_set_param.argtypes = [vp, i32, f64]
+        L.pcg_batch_create.argtypes = [vp, i32, ctypes.c_uint32, ctypes.POINTER(vp)]
+        L.pcg_batch_solve.argtypes = [vp, vp, vp, i32, vp, f64, i32, vp, vp, vp]
+        L.pcg_batch_autotune.argtypes = [vp, vp, vp, i32, vp, vp]
+        L.pcg_batch_set_cluster.argtypes = [vp, i32]
+        L.pcg_batch_last_kernel_ms.argtypes = [vp, ctypes.POINTER(f64)]
+        L.pcg_batch_destroy.argtypes = [vp]
+        L.pcg_batch_destroy.restype = None
         L.pcg_true_residual_noalloc.argtypes = [ctypes.POINTER(pcg_matrix), vp, vp, vp, vp, vp]
         L.pcg_kernel_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(f64)]
         L.pcg_kernel_stats_reset.argtypes = [vp]
         L.pcg_version.argtypes = []
         L.pcg_version.restype = ctypes.c_char_p
         for f in ("pcg_create", "pcg_set_stream", "pcg_solve", "pcg_solve_device", "pcg_select_sigma", "pcg_psi",
-                  "pcg_apply", "pcg_true_residual_noalloc", "pcg_set_param",
+                  "pcg_apply", "pcg_true_residual_noalloc", "pcg_set_param", "pcg_batch_create", "pcg_batch_solve",
+                  "pcg_batch_autotune", "pcg_batch_set_cluster", "pcg_batch_last_kernel_ms",
                   "pcg_kernel_stats", "pcg_kernel_stats_reset"):
             getattr(L, f).restype = st
         _lib = L
@@ -290,3 +298,70 @@ class Solver:
         it = res.iters
         return SolveResult(x_out, it, s, res.final_true_relres, res.final_rec_relres, hist["rec"][:it + 1],
                            hist["true"][:it + 1], hist["gap"][:it + 1], hist["alpha"][:it], hist["beta"][:it])
+
+
+class Batch:
+    """pcg_batch over a list of problems of one operator family (host arrays)."""
+
+    def __init__(self, problems):
+        self.mats = [Matrix(P) for P in problems]
+        self.n = [P.n for P in problems]
+        arr = (pcg_matrix * len(problems))(*[m.m for m in self.mats])
+        self._arr = arr
+        out = ctypes.c_void_p()
+        s = lib().pcg_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(problems), 0, ctypes.byref(out))
+        if s != PCG_OK:
+            raise PcgError(s, "pcg_batch_create")
+        self.h = out.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pcg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @staticmethod
+    def _ptrs(arrays):
+        return (ctypes.c_void_p * len(arrays))(*[a.ctypes.data for a in arrays])
+
+    def solve(self, bs, sigma, tol=0.0, maxit=1000, method=PCG_SPCG):
+        bs = [np.ascontiguousarray(b, dtype=np.float64) for b in bs]
+        xs = [np.empty(n) for n in self.n]
+        sg = np.ascontiguousarray(sigma, dtype=np.float64)
+        k = len(bs)
+        it = np.zeros(k, dtype=np.int32)
+        st = np.zeros(k, dtype=np.int32)
+        tr = np.zeros(k)
+        s = lib().pcg_batch_solve(self.h, ctypes.cast(self._ptrs(bs), ctypes.c_void_p),
+                                  ctypes.cast(self._ptrs(xs), ctypes.c_void_p), method, sg.ctypes.data, tol, maxit,
+                                  it.ctypes.data, st.ctypes.data, tr.ctypes.data)
+        if s not in (PCG_OK, PCG_ENOTCONV):
+            raise PcgError(s, "pcg_batch_solve")
+        return xs, it, st, tr
+
+    def autotune(self, bs, sigma, probe_iters=50):
+        bs = [np.ascontiguousarray(b, dtype=np.float64) for b in bs]
+        sg = np.ascontiguousarray(sigma, dtype=np.float64)
+        c = ctypes.c_int32()
+        ms = np.zeros(5)
+        s = lib().pcg_batch_autotune(self.h, ctypes.cast(self._ptrs(bs), ctypes.c_void_p), sg.ctypes.data,
+                                     probe_iters, ctypes.byref(c), ms.ctypes.data)
+        if s != PCG_OK:
+            raise PcgError(s, "pcg_batch_autotune")
+        return c.value, ms
+
+    def set_cluster(self, c):
+        return lib().pcg_batch_set_cluster(self.h, c)
+
+    def last_kernel_ms(self):
+        v = ctypes.c_double()
+        lib().pcg_batch_last_kernel_ms(self.h, ctypes.byref(v))
+        return v.value

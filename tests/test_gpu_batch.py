@@ -1,0 +1,82 @@
+"""Batched persistent launch (pcg_batch_*), GB300 only: every system of a batch gets
+the same result as the single-system solver, for every cluster shape."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1706_05988_gb300 import build
+    build.build()
+    import paper_1706_05988_gb300 as pkg
+    return pkg
+
+
+def shift(P):
+    c = S.to_csr(P)
+    rows = np.repeat(np.arange(c.n), np.diff(c.row_ptr))
+    return 0.5 * float(np.median(c.val[c.col == rows]))
+
+
+def var2d_batch(k=10, seed=0):
+    rng = np.random.default_rng(seed)
+    sides = rng.integers(8, 80, size=(k, 2))
+    probs = [S.varcoef_2d(int(a), int(b), seed=seed + i) for i, (a, b) in enumerate(sides)]
+    bs = [S.normal(100 + i, P.n) for i, P in enumerate(probs)]
+    return probs, bs
+
+
+@pytest.mark.parametrize("cluster", [1, 2, 4, 8, 16])
+def test_batch_matches_single_solver(B, cluster):
+    probs, bs = var2d_batch()
+    sig = [shift(P) for P in probs]
+    with B.Batch(probs) as bt:
+        assert bt.set_cluster(cluster) == B.PCG_OK
+        xs, it, st, tr = bt.solve(bs, sig, tol=1e-9, maxit=5000)
+    for P, b, s, x, i, code, t in zip(probs, bs, sig, xs, it, st, tr):
+        with B.Solver(P) as one:
+            r = one.solve(b, method="spcg", sigma=s, tol=1e-9, maxit=5000)
+        assert code == B.PCG_OK and r.status == B.PCG_OK
+        # the reduction order differs (per-block partials of a cluster vs of the whole grid), and
+        # these high-contrast systems take ~10^3 iterations: the stop may move by a few iterations
+        assert abs(int(i) - r.iters) <= 0.02 * r.iters + 2
+        tt = np.linalg.norm(b - oracle.apply(P, x)) / np.linalg.norm(b)
+        assert tt <= 3e-9 and abs(t - tt) <= 1e-6 * tt + 1e-15
+        # both iterates solve the system to the tolerance: their difference is bounded by it
+        assert np.linalg.norm(x - r.x) <= 1e-4 * np.linalg.norm(r.x)
+
+
+def test_batch_first_iterations_vs_oracle(B):
+    probs = [S.laplacian_3d(12, 10, 9), S.laplacian_3d(17, 5, 20), S.laplacian_3d(4, 4, 4)]
+    bs = [S.normal(7 + i, P.n) for i, P in enumerate(probs)]
+    with B.Batch(probs) as bt:
+        xs, it, st, tr = bt.solve(bs, [6.0] * 3, tol=0.0, maxit=15)
+    for P, b, x, i in zip(probs, bs, xs, it):
+        o = oracle.pcg_sh(P, b, sigma=6.0, maxit=15, log_every=0)
+        assert i == o.iters == 15 or (o.status == 1 and i == o.iters)
+        assert np.linalg.norm(x - o.x) <= 1e-9 * np.linalg.norm(o.x)
+
+
+def test_batch_csr_and_autotune(B):
+    probs = [S.to_csr(S.laplacian_3d(n)) for n in (6, 9, 14, 20, 11)]
+    bs = [S.normal(i, P.n) for i, P in enumerate(probs)]
+    with B.Batch(probs) as bt:
+        c, ms = bt.autotune(bs, [6.0] * 5, probe_iters=20)
+        assert c in (1, 2, 4, 8, 16) and np.isfinite(ms).any()
+        xs, it, st, tr = bt.solve(bs, [6.0] * 5, tol=1e-10, maxit=3000)
+    assert np.all(st == B.PCG_OK) and np.all(tr <= 2e-10)
+    for P, b, x in zip(probs, bs, xs):
+        assert np.linalg.norm(b - oracle.apply(P, x)) <= 2e-10 * np.linalg.norm(b)
+
+
+def test_batch_rejects_mixed_families(B):
+    from paper_1706_05988_gb300 import pcg as C
+    with pytest.raises(C.PcgError):
+        B.Batch([S.laplacian_2d(8), S.laplacian_3d(4)])
