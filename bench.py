@@ -187,6 +187,78 @@ def batch_measure(pkg, S, nsys: int, seed: int = 0) -> dict:
             "speedup": (nsys / tb) / one_rate}
 
 
+def serving_trace(nreq: int, rate: float, seed: int = 0):
+    """Seeded request stream: Poisson arrivals at `rate` per second; n log-uniform in
+    [1e3, 1e5]; half stencils (2D/3D unscaled Laplacians), half random SDD CSR (7-27 entries
+    per row, off-diagonals U[-1,0]); tolerance log-uniform in [1e-10, 1e-6]; b ~ N(0,1)."""
+    import numpy as np
+    import synthetic as S
+    u = S.uniform01(seed, 4 * nreq).reshape(nreq, 4)
+    gaps = -np.log(1.0 - u[:, 0]) / rate
+    arrive = np.cumsum(gaps)
+    reqs = []
+    for i in range(nreq):
+        n = int(10 ** (3 + 2 * u[i, 1]))
+        if u[i, 2] < 0.25:
+            side = max(int(round(n ** 0.5)), 4)
+            P = S.laplacian_2d(side)
+        elif u[i, 2] < 0.5:
+            side = max(int(round(n ** (1 / 3))), 4)
+            P = S.laplacian_3d(side)
+        else:
+            P = S.random_sdd_csr(n, seed=seed + 100 + i)
+        tol = 10 ** (-10 + 4 * u[i, 3])
+        reqs.append((arrive[i], P, S.normal(seed + 10000 + i, P.n), tol))
+    return reqs
+
+
+def serving_measure(pkg, nreq: int, rate: float) -> dict:
+    """p50/p99 latency and solves/s of the request stream through the continuous-batching
+    server, against the same stream served one request at a time by the single-system
+    solver (FP64, same shift rule and tolerances)."""
+    import numpy as np
+    reqs = serving_trace(nreq, rate)
+    lat = np.zeros(nreq)
+    with pkg.Server(8 << 30, 512) as srv:
+        pending = {}
+        t0 = time.perf_counter()
+        i = 0
+        done = 0
+        while done < nreq:
+            now = time.perf_counter() - t0
+            while i < nreq and reqs[i][0] <= now:
+                pending[srv.submit(reqs[i][1], reqs[i][2], tol=reqs[i][3])] = i
+                i += 1
+            for t in list(pending):
+                r = srv.poll(t)
+                if r is not None:
+                    k = pending.pop(t)
+                    lat[k] = time.perf_counter() - t0 - reqs[k][0]
+                    done += 1
+            if not pending and i < nreq:
+                time.sleep(max(0.0, min(0.001, reqs[i][0] - (time.perf_counter() - t0))))
+        span = time.perf_counter() - t0
+    # one at a time: each request starts when it has arrived and the previous one is done
+    lat1 = np.zeros(nreq)
+    t0 = time.perf_counter()
+    for k, (arr, P, b, tol) in enumerate(reqs):
+        now = time.perf_counter() - t0
+        if now < arr:
+            time.sleep(arr - now)
+        with pkg.Solver(P) as one:
+            diag = 4.0 if P.layout == 0 else 6.0 if P.layout == 1 else float(np.mean(P.val[P.col == np.repeat(
+                np.arange(P.n), np.diff(P.row_ptr))]))
+            one.solve(b, method="spcg", sigma=diag, tol=tol, maxit=100000)
+        lat1[k] = time.perf_counter() - t0 - arr
+    span1 = time.perf_counter() - t0
+    return {"workload": f"{nreq} requests, Poisson arrivals {rate:g}/s, n log-uniform [1e3, 1e5], half 2D/3D "
+                        "Laplacian stencils, half random SDD CSR (7-27 nnz/row), tol log-uniform [1e-10, 1e-6], FP64",
+            "solves_per_s": nreq / span, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+            "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "one_at_a_time": {"solves_per_s": nreq / span1, "p50_ms": 1e3 * float(np.percentile(lat1, 50)),
+                              "p99_ms": 1e3 * float(np.percentile(lat1, 99))}}
+
+
 def run_reference(args):
     """The oracle, as it stands, on the host: bounded samples of the same workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -334,6 +406,10 @@ def run_ours(args):
     if not args.no_batch:
         batch = batch_measure(pkg, S, args.batch_systems)
 
+    serving = None
+    if not args.no_serving:
+        serving = serving_measure(pkg, args.serving_requests, args.serving_rate)
+
     # the same workload as CSR (int32 indices): config's second form, one timed step
     csr = None
     if not args.no_csr:
@@ -372,7 +448,7 @@ def run_ours(args):
                                       "per SM x 152 SMs x 2.07 GHz (ncu sm__sass_thread_inst_executed_op_dfma "
                                       "peak_sustained)"},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
-                "csr_int32": csr, "persistent": persistent, "batch": batch}
+                "csr_int32": csr, "persistent": persistent, "batch": batch, "serving": serving}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -392,6 +468,9 @@ def main():
     ap.add_argument("--no-persistent", action="store_true", help="skip the persistent-kernel measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve measurement")
     ap.add_argument("--batch-systems", type=int, default=128, help="systems in the batched-solve measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serving-requests", type=int, default=400)
+    ap.add_argument("--serving-rate", type=float, default=2000.0, help="Poisson arrival rate, requests/s")
     ap.add_argument("--size", type=int, default=N_SIDE, help="grid side (default: the 256^3 workload)")
     args = ap.parse_args()
     globals()["N_SIDE"] = args.size

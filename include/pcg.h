@@ -213,6 +213,42 @@ pcg_status pcg_batch_last_kernel_ms(const pcg_batch *batch, double *ms);
 
 void pcg_batch_destroy(pcg_batch *batch);
 
+/* ---- Serving: continuous batching of solve requests ----------------------------
+ * A server owns a device arena of hbm_budget_bytes.  pcg_submit admits a request when
+ * its operator and vectors fit in the arena and a slot is free (first come, first
+ * served); otherwise the request waits on the host until earlier requests are polled.
+ * Admitted requests go to a persistent kernel whose thread-block clusters take them as
+ * they come free, so requests that arrive while others run overlap on the device;
+ * each request is solved by one cluster exactly as in pcg_batch (binary64, x_0 = 0),
+ * so its result does not depend on what else runs.  With no work for 20 ms the kernel
+ * exits and is relaunched by the next submit or poll.  The server is internally
+ * synchronised (calls may come from several host threads). */
+typedef struct pcg_server pcg_server;
+
+/* max_slots >= 1 requests in flight at once; hbm_budget_bytes >= 1 MiB.
+ * Errors: PCG_EINVAL, PCG_ENOMEM (the arena cannot be allocated), PCG_ECUDA. */
+pcg_status pcg_server_create(size_t hbm_budget_bytes, int32_t max_slots, pcg_server **out);
+
+/* Queue a solve of A x = b (host arrays, copied): method PCG_PCG or PCG_SPCG, stop at
+ * ||r_i|| <= tol ||b|| or maxit.  sigma < 0 selects the mean diagonal entry of A (for
+ * the unscaled Laplacians half the top of the spectrum, as Table 1's lapl200 shift).
+ * *ticket identifies the request.  Errors: PCG_EINVAL; PCG_ENOMEM when the request can
+ * never fit in the arena. */
+pcg_status pcg_submit(pcg_server *server, const pcg_matrix *A, const double *b, double tol, int32_t method,
+                      double sigma, int32_t maxit, uint64_t *ticket);
+
+/* PCG_PENDING until the request is done; then x_out (host, n doubles, may be NULL) and
+ * res (iters, status, final_true_relres; may be NULL) are filled, the request's memory
+ * is released and its status is returned (PCG_OK, PCG_ENOTCONV, PCG_EBREAKDOWN); the
+ * ticket is then no longer valid (PCG_EINVAL). */
+pcg_status pcg_poll(pcg_server *server, uint64_t ticket, double *x_out, pcg_result *res);
+
+/* Requests waiting for admission, requests admitted and not yet polled, free arena bytes. */
+pcg_status pcg_server_stats(pcg_server *server, int64_t *waiting, int64_t *inflight, size_t *free_bytes);
+
+/* Stops the kernel and releases everything (pending requests are dropped). */
+void pcg_server_destroy(pcg_server *server);
+
 /* Largest n accepted by pcg_true_residual_noalloc. */
 #define PCG_NOALLOC_MAX_N 16777216
 

@@ -4,7 +4,7 @@ The solver lives in libpcg.so (hand-written CUDA for sm_103a behind the C ABI
 of include/pcg.h); `pcg` is its thin ctypes binding and `build` compiles it.
 """
 from . import build  # noqa: F401
-from .pcg import (METHODS, Batch, PCG_CG, PCG_CSR32, PCG_DEVICE_PTRS, PCG_EBREAKDOWN, PCG_EINVAL, PCG_ENOTCONV,  # noqa: F401
+from .pcg import (METHODS, Batch, Server, PCG_CG, PCG_CSR32, PCG_DEVICE_PTRS, PCG_EBREAKDOWN, PCG_EINVAL, PCG_ENOTCONV,  # noqa: F401
                   PCG_FP64, PCG_MIXED_IR, PCG_OK, PCG_PCG, PCG_PERSISTENT, PCG_PROFILE, PCG_SPCG, PCG_STENCIL5_2D, PCG_STENCIL7_3D,
                   PCG_STENCIL_FP64_SUM, Matrix, pcg_apply,
                   PcgError, Solver, SolveResult, lib, pcg_create, pcg_destroy, pcg_kernel_stats,

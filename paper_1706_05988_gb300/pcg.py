@@ -87,6 +87,12 @@ def lib() -> ctypes.CDLL:
         L.pcg_batch_last_kernel_ms.argtypes = [vp, ctypes.POINTER(f64)]
         L.pcg_batch_destroy.argtypes = [vp]
         L.pcg_batch_destroy.restype = None
+        L.pcg_server_create.argtypes = [ctypes.c_size_t, i32, ctypes.POINTER(vp)]
+        L.pcg_submit.argtypes = [vp, ctypes.POINTER(pcg_matrix), vp, f64, i32, f64, i32, ctypes.POINTER(ctypes.c_uint64)]
+        L.pcg_poll.argtypes = [vp, ctypes.c_uint64, vp, ctypes.POINTER(pcg_result)]
+        L.pcg_server_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_size_t)]
+        L.pcg_server_destroy.argtypes = [vp]
+        L.pcg_server_destroy.restype = None
         L.pcg_true_residual_noalloc.argtypes = [ctypes.POINTER(pcg_matrix), vp, vp, vp, vp, vp]
         L.pcg_kernel_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(f64)]
         L.pcg_kernel_stats_reset.argtypes = [vp]
@@ -94,7 +100,8 @@ def lib() -> ctypes.CDLL:
         L.pcg_version.restype = ctypes.c_char_p
         for f in ("pcg_create", "pcg_set_stream", "pcg_solve", "pcg_solve_device", "pcg_select_sigma", "pcg_psi",
                   "pcg_apply", "pcg_true_residual_noalloc", "pcg_set_param", "pcg_batch_create", "pcg_batch_solve",
-                  "pcg_batch_autotune", "pcg_batch_set_cluster", "pcg_batch_last_kernel_ms",
+                  "pcg_batch_autotune", "pcg_batch_set_cluster", "pcg_batch_last_kernel_ms", "pcg_server_create",
+                  "pcg_submit", "pcg_poll", "pcg_server_stats",
                   "pcg_kernel_stats", "pcg_kernel_stats_reset"):
             getattr(L, f).restype = st
         _lib = L
@@ -365,3 +372,56 @@ class Batch:
         v = ctypes.c_double()
         lib().pcg_batch_last_kernel_ms(self.h, ctypes.byref(v))
         return v.value
+
+
+class Server:
+    """pcg_server: continuous batching of solve requests (host arrays in and out)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int):
+        out = ctypes.c_void_p()
+        s = lib().pcg_server_create(hbm_budget_bytes, max_slots, ctypes.byref(out))
+        if s != PCG_OK:
+            raise PcgError(s, "pcg_server_create")
+        self.h = out.value
+        self.n = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pcg_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, P, b, tol=1e-8, method=PCG_SPCG, sigma=-1.0, maxit=100000) -> int:
+        m = Matrix(P)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        t = ctypes.c_uint64()
+        s = lib().pcg_submit(self.h, ctypes.byref(m.m), b.ctypes.data, tol, method, sigma, maxit, ctypes.byref(t))
+        if s != PCG_OK:
+            raise PcgError(s, "pcg_submit")
+        self.n[t.value] = P.n
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while pending, else (status, x, iters, true_relres)."""
+        x = np.empty(self.n[ticket])
+        res = pcg_result()
+        s = lib().pcg_poll(self.h, ticket, x.ctypes.data, ctypes.byref(res))
+        if s == PCG_PENDING:
+            return None
+        if s not in (PCG_OK, PCG_ENOTCONV, PCG_EBREAKDOWN):
+            raise PcgError(s, "pcg_poll")
+        del self.n[ticket]
+        return s, x, res.iters, res.final_true_relres
+
+    def stats(self):
+        w, i, f = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_size_t()
+        lib().pcg_server_stats(self.h, ctypes.byref(w), ctypes.byref(i), ctypes.byref(f))
+        return w.value, i.value, f.value

@@ -244,6 +244,31 @@ def to_csr(p: Problem) -> Problem:
                    meta={"from": p.name, "nx": nx, "ny": ny, "nz": nz})
 
 
+def random_sdd_csr(n: int, seed: int = 0, nnz_lo: int = 7, nnz_hi: int = 27, margin: float = 1e-2) -> Problem:
+    """Random symmetric strictly diagonally dominant CSR matrix (SPD).
+
+    Each row draws a target count d ~ U{nnz_lo..nnz_hi} of entries; (d - 1) // 2 partner
+    columns are drawn uniformly among the other rows and the pattern is mirrored, so rows
+    hold about nnz_lo..nnz_hi entries.  Off-diagonals ~ U[-1, 0]; the diagonal is
+    (1 + margin) * sum |off-diagonals| of its row (strict dominance makes A SPD)."""
+    import scipy.sparse as sp
+    d = nnz_lo + (splitmix64(seed, n) % np.uint64(nnz_hi - nnz_lo + 1)).astype(np.int64)
+    k = (d - 1) // 2
+    rows = np.repeat(np.arange(n, dtype=np.int64), k)
+    cols = (splitmix64(seed + 1, rows.size) % np.uint64(max(n - 1, 1))).astype(np.int64)
+    cols = cols + (cols >= rows)                     # never the diagonal
+    vals = -uniform01(seed + 2, rows.size)
+    U = sp.coo_matrix((vals, (rows, cols)), shape=(n, n)).tocsr()
+    A = (U + U.T).tocsr()
+    A.sum_duplicates()
+    diag = (1.0 + margin) * np.asarray(np.abs(A).sum(axis=1)).ravel()
+    diag[diag == 0] = 1.0
+    A = (A + sp.diags(diag)).tocsr()
+    A.sort_indices()
+    return Problem(CSR32, row_ptr=A.indptr.astype(np.int32), col=A.indices.astype(np.int32),
+                   val=A.data.astype(np.float64), n_csr=n, name=f"sdd_{n}")
+
+
 def laplacian_rhs(p: Problem, xstar: np.ndarray) -> np.ndarray:
     """b = A x* for a constant-coefficient Laplacian and dyadic x* (see module doc).
 

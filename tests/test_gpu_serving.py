@@ -1,0 +1,138 @@
+"""Continuous-batching server (pcg_server_create / pcg_submit / pcg_poll), GB300 only.
+
+A request's result is the same bit for bit whether it runs alone or among other
+requests (each request is solved by one cluster with a fixed reduction order), every
+result reaches its tolerance by the oracle's true residual, requests wait for arena
+memory and still complete, and an idle server restarts its kernel for new work."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1706_05988_gb300 import build
+    build.build()
+    import paper_1706_05988_gb300 as pkg
+    return pkg
+
+
+def random_sdd(n, seed):
+    import scipy.sparse as sp
+    rng = np.random.default_rng(seed)
+    deg = rng.integers(3, 13, size=n)
+    rows = np.repeat(np.arange(n), deg)
+    cols = rng.integers(0, n, size=rows.size)
+    keep = rows != cols
+    U = sp.coo_matrix((-rng.random(keep.sum()), (rows[keep], cols[keep])), shape=(n, n)).tocsr()
+    A = (U + U.T).tocsr()
+    A.sum_duplicates()
+    d = np.asarray(np.abs(A).sum(axis=1)).ravel() * 1.01 + 1e-3
+    A = (A + sp.diags(d)).tocsr()
+    A.sort_indices()
+    return S.Problem(S.CSR32, row_ptr=A.indptr.astype(np.int32), col=A.indices.astype(np.int32),
+                     val=A.data.astype(np.float64), n_csr=n)
+
+
+def request_mix():
+    probs = [S.laplacian_2d(40, 33), S.laplacian_3d(18, 15, 12), S.varcoef_2d(30, 30, seed=4),
+             random_sdd(3000, 1), S.laplacian_2d(7, 5), S.varcoef_3d(16, block=4, lo_exp=-1.0, hi_exp=1.0, seed=2), random_sdd(500, 2),
+             S.laplacian_3d(25)]
+    bs = [S.normal(50 + i, P.n) for i, P in enumerate(probs)]
+    return probs, bs
+
+
+def wait(srv, t, timeout=60.0):
+    t0 = time.time()
+    while True:
+        r = srv.poll(t)
+        if r is not None:
+            return r
+        assert time.time() - t0 < timeout, "request did not finish"
+        time.sleep(0.0005)
+
+
+def test_same_result_alone_and_in_the_mix(B):
+    probs, bs = request_mix()
+    alone = []
+    for P, b in zip(probs, bs):
+        with B.Server(256 << 20, 4) as srv:
+            alone.append(wait(srv, srv.submit(P, b, tol=1e-10)))
+    with B.Server(256 << 20, 16) as srv:
+        tickets = [srv.submit(P, b, tol=1e-10) for P, b in zip(probs, bs)]
+        mixed = [wait(srv, t) for t in reversed(tickets)][::-1]
+    for P, b, a, m in zip(probs, bs, alone, mixed):
+        assert a[0] == m[0] and a[2] == m[2] and np.array_equal(a[1], m[1])
+        assert m[0] == B.PCG_OK
+        tr = np.linalg.norm(b - oracle.apply(P, m[1])) / np.linalg.norm(b)
+        assert tr <= 2e-10 and abs(tr - m[3]) <= 1e-6 * tr + 1e-16
+
+
+def test_matches_single_system_solver(B):
+    P = S.varcoef_2d(45, 31, seed=9)
+    b = S.normal(9, P.n)
+    sigma = float(np.mean(P.diag))
+    with B.Server(64 << 20, 2) as srv:
+        st, x, it, tr = wait(srv, srv.submit(P, b, tol=1e-9, sigma=sigma))
+    with B.Solver(P) as one:
+        r = one.solve(b, method="spcg", sigma=sigma, tol=1e-9, maxit=100000)
+    assert st == r.status == B.PCG_OK and abs(it - r.iters) <= 0.02 * r.iters + 2
+    assert np.linalg.norm(x - r.x) <= 1e-4 * np.linalg.norm(r.x)
+
+
+def test_admission_waits_for_memory(B):
+    probs = [S.laplacian_3d(40) for _ in range(6)]          # ~4.1 MB of vectors each
+    bs = [S.normal(i, P.n) for i, P in enumerate(probs)]
+    with B.Server(10 << 20, 8) as srv:                        # room for two at a time
+        tickets = [srv.submit(P, b, tol=1e-8) for P, b in zip(probs, bs)]
+        waiting, inflight, free = srv.stats()
+        assert waiting >= 3 and inflight <= 2
+        res = [wait(srv, t) for t in tickets]
+        assert srv.stats()[:2] == (0, 0)
+    for P, b, r in zip(probs, bs, res):
+        assert r[0] == B.PCG_OK
+        assert np.linalg.norm(b - oracle.apply(P, r[1])) <= 2e-8 * np.linalg.norm(b)
+
+
+def test_idle_kernel_restarts(B):
+    P, b, _ = S.poisson2d_manufactured(50)
+    with B.Server(32 << 20, 2) as srv:
+        first = wait(srv, srv.submit(P, b, tol=1e-10))
+        time.sleep(0.2)                                       # the kernel exits after 20 ms idle
+        second = wait(srv, srv.submit(P, b, tol=1e-10))
+    assert first[0] == second[0] == B.PCG_OK and np.array_equal(first[1], second[1])
+
+
+def test_submissions_from_two_threads(B):
+    probs, bs = request_mix()
+    out = {}
+    with B.Server(256 << 20, 8) as srv:
+        def worker(idx):
+            for i in idx:
+                out[i] = wait(srv, srv.submit(probs[i], bs[i], tol=1e-9))
+        th = [threading.Thread(target=worker, args=(list(range(k, len(probs), 2)),)) for k in (0, 1)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+    assert sorted(out) == list(range(len(probs))) and all(v[0] == B.PCG_OK for v in out.values())
+
+
+def test_server_rejects_bad_requests(B):
+    from paper_1706_05988_gb300 import pcg as C
+    with B.Server(1 << 20, 1) as srv:
+        with pytest.raises(C.PcgError):
+            srv.submit(S.laplacian_3d(64), np.ones(64 ** 3))     # can never fit in 1 MiB
+        with pytest.raises(C.PcgError):
+            srv.submit(S.laplacian_2d(8), np.ones(64), method=C.PCG_CG)
+    with pytest.raises(C.PcgError):
+        B.Server(100, 1)
