@@ -11,6 +11,7 @@ Contents
   apply(P, x)      y = A x                         (operator of the model problem)
   cg(...)          Algorithm 1, classic CG
   pcg(...)         Algorithm 2, pipelined CG (written out without shift terms)
+  pcg_varsh(...)   Algorithm 4, pipelined CG with a variable shift
   pcg_sh(...)      Algorithm 3, shifted pipelined CG
   psi / select_sigma   Section 3.2, Eq. (functionpsi)        -> oracle.psi
   exact rational CG / p-CG-sh for tiny systems               -> oracle.exact
@@ -69,7 +70,8 @@ def _load():
         _lib.oracle_cg.argtypes = [vp, vp, vp, vp, i32, f64, f64, i32, vp, vp, vp, vp, vp, vp]
         _lib.oracle_pcg_sh.argtypes = [vp, vp, vp, vp, f64, i32, f64, f64, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         _lib.oracle_pcg.argtypes = [vp, vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp]
-        for f in (_lib.oracle_cg, _lib.oracle_pcg_sh, _lib.oracle_pcg):
+        _lib.oracle_pcg_varsh.argtypes = [vp, vp, vp, vp, vp, i32, f64, i32, vp, vp, vp, vp, vp, vp]
+        for f in (_lib.oracle_cg, _lib.oracle_pcg_sh, _lib.oracle_pcg, _lib.oracle_pcg_varsh):
             f.restype = ctypes.c_int
     return _lib
 
@@ -201,5 +203,26 @@ def pcg(P, b, x0=None, maxit=100, log_every=1, minv=None) -> Run:
                         be.ctypes.data, rec.ctypes.data, tru.ctypes.data, gap.ctypes.data, ctypes.byref(info))
     if rc != 0:
         raise MemoryError("oracle_pcg allocation failed")
+    k = info.iters
+    return Run(x, k, info.status, al[:k], be[:k], rec[:k + 1], tru[:k + 1], gap[:k + 1])
+
+
+def pcg_varsh(P, b, shifts, x0=None, maxit=100, rtol=0.0, log_every=1, minv=None) -> Run:
+    """Algorithm 4: shifts[0] = sigma_{-1}, shifts[k + 1] = sigma_k (at least maxit + 1 values)."""
+    lib = _load()
+    h = _OpHolder(P)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    sh = np.ascontiguousarray(shifts, dtype=np.float64)
+    if sh.size < maxit + 1:
+        raise ValueError("need maxit + 1 shifts")
+    x = np.zeros(P.n) if x0 is None else np.array(x0, dtype=np.float64)
+    al, be, rec, tru, gap = _hist(maxit)
+    info = _Info()
+    mv = _minv(minv)
+    rc = lib.oracle_pcg_varsh(h.ref, _ptr(mv), b.ctypes.data, x.ctypes.data, sh.ctypes.data, maxit, rtol, log_every,
+                              al.ctypes.data, be.ctypes.data, rec.ctypes.data, tru.ctypes.data, gap.ctypes.data,
+                              ctypes.byref(info))
+    if rc != 0:
+        raise MemoryError("oracle_pcg_varsh allocation failed")
     k = info.iters
     return Run(x, k, info.status, al[:k], be[:k], rec[:k + 1], tru[:k + 1], gap[:k + 1])

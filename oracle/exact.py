@@ -94,3 +94,47 @@ def pcg_sh(A, b, x0=None, sigma=F(0), iters: int = 10, minv: Optional[Sequence[F
         gamma_prev, alpha_prev = gamma, a
         xs.append(list(x))
     return alphas, betas, x, xs
+
+
+def pcg_varsh(A, b, shifts, x0=None, iters: int = 10, minv: Optional[Sequence[F]] = None):
+    """Algorithm 4 (variable shift): shifts[0] = sigma_{-1}, shifts[k + 1] = sigma_k."""
+    n = len(b)
+    sg = [F(v) for v in shifts]
+    x = [F(0)] * n if x0 is None else [F(v) for v in x0]
+    Ax = _mv(A, x)
+    r = [F(bi) - ai for bi, ai in zip(b, Ax)]
+    u = _minv(minv, r)
+    Au = _mv(A, u)
+    w = [au - sg[0] * ri for au, ri in zip(Au, r)]
+    z = q = s = t = p = [F(0)] * n
+    alphas, betas, xs = [], [], [list(x)]
+    gamma_prev = alpha_prev = None
+    for i in range(iters):
+        sp, sc = sg[i], sg[i + 1]
+        ds = sc - sp
+        gamma = _dot(r, u)
+        if gamma == 0:
+            break
+        delta = _dot([wi + sp * ri for wi, ri in zip(w, r)], u)
+        m = _minv(minv, w)
+        nn = _mv(A, m)
+        if i > 0:
+            bt = gamma / gamma_prev
+            a = 1 / (delta / gamma - bt / alpha_prev)
+        else:
+            bt = F(0)
+            a = gamma / delta
+        alphas.append(a)
+        betas.append(bt)
+        t = [ri + bt * ti for ri, ti in zip(r, t)]
+        p = [ui + bt * pi for ui, pi in zip(u, p)]
+        s = [wi + bt * si - ds * ti for wi, si, ti in zip(w, s, t)]
+        q = [mi + bt * qi - ds * pi for mi, qi, pi in zip(m, q, p)]
+        z = [ni + bt * zi - ds * (si + sc * ti) for ni, zi, si, ti in zip(nn, z, s, t)]
+        x = [xi + a * pi for xi, pi in zip(x, p)]
+        w = [wi - a * zi - ds * ri for wi, zi, ri in zip(w, z, r)]
+        r = [ri - (a * si + a * sc * ti) for ri, si, ti in zip(r, s, t)]
+        u = [ui - (a * qi + a * sc * pi) for ui, qi, pi in zip(u, q, p)]
+        gamma_prev, alpha_prev = gamma, a
+        xs.append(list(x))
+    return alphas, betas, x, xs

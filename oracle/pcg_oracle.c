@@ -13,6 +13,7 @@
  *   oracle_pcg     Algorithm 2 (pipelined CG), Section 2.1.
  *   oracle_pcg_sh  Algorithm 3 (shifted pipelined CG), Section 2.2, with the
  *                  auxiliary definitions of Eq. (pipe_cg_shift_aux).
+ *   oracle_pcg_varsh  Algorithm 4 (variable shift), Section 4.1.
  *   oracle_apply   the operator A (CSR or a matrix-free 5/7-point stencil).
  *
  * Readings of the paper taken here:
@@ -327,6 +328,78 @@ int oracle_pcg(const oracle_op *A, const double *minv, const double *b, double *
     alpha_prev = a;
   }
   if (log_every > 0 && !want_log(i, log_every))   /* the final iterate is always logged */
+    log_true(A, b, x, r, work, tru ? &tru[i] : NULL, gap ? &gap[i] : NULL);
+  if (info) { info->iters = i; info->status = status; }
+  free(r); free(u); free(w); free(m); free(nn); free(z); free(q); free(s); free(t); free(p); free(work);
+  return 0;
+}
+
+/* ---- Algorithm 4: pipelined CG with a variable shift -------------------- */
+
+/* shifts[0] = sigma_{-1}, shifts[k + 1] = sigma_k (maxit + 1 entries).  The
+   correction terms follow the algorithm statement of Section 4.1 (z_i uses
+   s_i + sigma_i t_i; the garbled sign in the error analysis of Section 4.2 does
+   not concern the algorithm).  Same logging and stop rules as oracle_pcg_sh. */
+int oracle_pcg_varsh(const oracle_op *A, const double *minv, const double *b, double *x, const double *shifts,
+                     int32_t maxit, double rtol, int32_t log_every, double *alpha, double *beta, double *rec,
+                     double *tru, double *gap, oracle_info *info) {
+  const int64_t n = A->n;
+  double *r = zeros(n), *u = zeros(n), *w = zeros(n), *m = zeros(n), *nn = zeros(n), *z = zeros(n), *q = zeros(n),
+         *s = zeros(n), *t = zeros(n), *p = zeros(n), *work = zeros(n);
+  if (!r || !u || !w || !m || !nn || !z || !q || !s || !t || !p || !work) return -1;
+  fill_nan(alpha, maxit + 1); fill_nan(beta, maxit + 1); fill_nan(rec, maxit + 1);
+  fill_nan(tru, maxit + 1); fill_nan(gap, maxit + 1);
+  const double bnorm = oracle_nrm2(n, b);
+
+  /* r_0 := b - A x_0; u_0 := M^{-1} r_0; w_0 := A u_0 - sigma_{-1} r_0 */
+  oracle_apply(A, x, work);
+  for (int64_t j = 0; j < n; ++j) r[j] = b[j] - work[j];
+  apply_minv(n, minv, r, u);
+  oracle_apply(A, u, work);
+  for (int64_t j = 0; j < n; ++j) w[j] = work[j] - shifts[0] * r[j];
+
+  double gamma_prev = 0.0, alpha_prev = 0.0;
+  int32_t i = 0, status = 0;
+  for (;; ++i) {
+    if (rec) rec[i] = oracle_nrm2(n, r);
+    if (want_log(i, log_every)) log_true(A, b, x, r, work, tru ? &tru[i] : NULL, gap ? &gap[i] : NULL);
+    if (rtol > 0 && oracle_nrm2(n, r) <= rtol * bnorm) { status = 1; break; }
+    if (i >= maxit) break;
+    const double sprev = shifts[i], scur = shifts[i + 1];   /* sigma_{i-1}, sigma_i */
+    const double ds = scur - sprev;
+    const double gamma = oracle_dot(n, r, u);        /* gamma_i := (r_i, u_i) */
+    double delta = 0.0;                              /* delta := (w_i + sigma_{i-1} r_i, u_i) */
+    for (int64_t j = 0; j < n; ++j) delta += (w[j] + sprev * r[j]) * u[j];
+    if (gamma == 0.0) { status = 1; break; }
+    apply_minv(n, minv, w, m);                       /* m_i := M^{-1} w_i */
+    oracle_apply(A, m, nn);                          /* n_i := A m_i */
+    double a, bt;
+    if (i > 0) {
+      bt = gamma / gamma_prev;
+      const double den = delta / gamma - bt / alpha_prev;
+      if (!(den > 0.0) || !isfinite(den)) { status = 2; break; }
+      a = 1.0 / den;
+    } else {
+      if (!(delta > 0.0) || !isfinite(delta)) { status = 2; break; }
+      bt = 0.0;
+      a = gamma / delta;
+    }
+    if (alpha) alpha[i] = a;
+    if (beta) beta[i] = bt;
+    const double as = a * scur;
+    for (int64_t j = 0; j < n; ++j) t[j] = r[j] + bt * t[j];                    /* t_i */
+    for (int64_t j = 0; j < n; ++j) p[j] = u[j] + bt * p[j];                    /* p_i */
+    for (int64_t j = 0; j < n; ++j) s[j] = (w[j] + bt * s[j]) - ds * t[j];      /* s_i */
+    for (int64_t j = 0; j < n; ++j) q[j] = (m[j] + bt * q[j]) - ds * p[j];      /* q_i */
+    for (int64_t j = 0; j < n; ++j) z[j] = (nn[j] + bt * z[j]) - ds * (s[j] + scur * t[j]);   /* z_i */
+    for (int64_t j = 0; j < n; ++j) x[j] = x[j] + a * p[j];                     /* x_{i+1} */
+    for (int64_t j = 0; j < n; ++j) w[j] = (w[j] - a * z[j]) - ds * r[j];       /* w_{i+1} (before r) */
+    for (int64_t j = 0; j < n; ++j) r[j] = r[j] - (a * s[j] + as * t[j]);       /* r_{i+1} */
+    for (int64_t j = 0; j < n; ++j) u[j] = u[j] - (a * q[j] + as * p[j]);       /* u_{i+1} */
+    gamma_prev = gamma;
+    alpha_prev = a;
+  }
+  if (log_every > 0 && !want_log(i, log_every))
     log_true(A, b, x, r, work, tru ? &tru[i] : NULL, gap ? &gap[i] : NULL);
   if (info) { info->iters = i; info->status = status; }
   free(r); free(u); free(w); free(m); free(nn); free(z); free(q); free(s); free(t); free(p); free(work);

@@ -317,3 +317,60 @@ def test_select_sigma_lapl200(lapl200_runs):
     assert vals[0] > 5 * vals.min()
     # beyond the top of the spectrum (lambda_max < 8) psi explodes: the cliff the rule avoids
     assert PS.psi(sh.alpha, sh.beta, 499, 9.0) > 1e6 * vals.min()
+
+
+# ---------------------------------------------------------------- Algorithm 4 (variable shift)
+
+@pytest.mark.parametrize("precond", [False, True])
+def test_exact_varsh_equals_cg(precond):
+    """Algorithm 4 coincides with Algorithm 1 in exact arithmetic for any shift sequence (Section 4.1)."""
+    n = 7
+    A = spd_int(n, 5)
+    Af = [[F(int(v)) for v in row] for row in A]
+    b = [F(int(v)) for v in np.random.default_rng(9).integers(-5, 6, n)]
+    minv = [F(1, int(A[i, i])) for i in range(n)] if precond else None
+    shifts = [F(3), F(1, 2), F(4), F(0), F(7, 3), F(5), F(2), F(1), F(6)]
+    a1, b1, _, xs1 = EX.cg(Af, b, iters=n, minv=minv)
+    a4, b4, _, xs4 = EX.pcg_varsh(Af, b, shifts, iters=n, minv=minv)
+    assert a1 == a4 and b1 == b4 and xs1 == xs4
+
+
+def test_exact_varsh_constant_and_switching_shift():
+    """Exact arithmetic: Algorithm 4 with a constant shift equals Algorithm 3 and CG, and a
+    shift that switches mid-run (the correction terms then act) still equals CG."""
+    n = 6
+    A = spd_int(n, 3)
+    Af = [[F(int(v)) for v in row] for row in A]
+    b = [F(int(v)) for v in np.random.default_rng(2).integers(-5, 6, n)]
+    a1, _, _, _ = EX.cg(Af, b, iters=n)
+    a3, _, _, _ = EX.pcg_sh(Af, b, sigma=F(2), iters=n)
+    a4, _, _, _ = EX.pcg_varsh(Af, b, [F(2)] * (n + 1), iters=n)
+    assert a1 == a3 == a4
+    a4v, _, _, _ = EX.pcg_varsh(Af, b, [F(2), F(2), F(5)] + [F(5)] * n, iters=n)
+    assert a4v == a1
+
+
+@pytest.mark.parametrize("precond", [False, True])
+def test_fp64_varsh_matches_exact(precond):
+    n = 10
+    A = spd_int(n, 17)
+    bi = np.random.default_rng(4).integers(-9, 10, n)
+    Af = [[F(int(v)) for v in row] for row in A]
+    minv_f = [F(1, int(A[i, i])) for i in range(n)] if precond else None
+    minv = np.array([1.0 / A[i, i] for i in range(n)]) if precond else None
+    shifts = [0.5, 1.0, 2.0, 1.5, 3.0, 0.25, 1.0, 2.0, 4.0, 1.0, 0.5, 2.0]
+    a_ex, b_ex, _, xs_ex = EX.pcg_varsh(Af, [F(int(v)) for v in bi], [F(v) for v in shifts], iters=n, minv=minv_f)
+    k = min(len(a_ex) - 1, 6)
+    r = oracle.pcg_varsh(dense_csr(A), bi.astype(float), shifts, maxit=k, minv=minv)
+    np.testing.assert_allclose(r.alpha, [float(v) for v in a_ex[:k]], rtol=1e-10)
+    np.testing.assert_allclose(r.beta[1:], [float(v) for v in b_ex[1:k]], rtol=1e-10)
+    np.testing.assert_allclose(r.x, [float(v) for v in xs_ex[k]], rtol=1e-9, atol=1e-12)
+
+
+def test_varsh_constant_shift_is_algorithm3_bitwise():
+    """With sigma_i constant every correction term is an exact zero: Algorithm 4 reproduces
+    Algorithm 3 bit for bit."""
+    P, b, _ = S.poisson2d_manufactured(30)
+    r3 = oracle.pcg_sh(P, b, sigma=4.0, maxit=80)
+    r4 = oracle.pcg_varsh(P, b, [4.0] * 81, maxit=80)
+    assert np.array_equal(r3.alpha, r4.alpha) and np.array_equal(r3.x, r4.x)
