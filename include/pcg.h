@@ -62,6 +62,9 @@ typedef enum { PCG_FP64 = 0, PCG_MIXED_IR = 1 } pcg_precision;
                                   replaces the kernel boundary and each block overlaps the
                                   global reduction of (r,r), (w,r) with the SpMV of its next
                                   unit (the paper's communication hiding, Section 1) */
+#define PCG_JACOBI 0x10u      /* preconditioner M^{-1} = diag(A)^{-1} (the paper's JAC, Table 1):
+                                  Algorithm 3 with its separate preconditioned recurrences for
+                                  u, q, p (PCG_PCG / PCG_SPCG, FP64; host arrays only) */
 #define PCG_STENCIL_FP64_SUM 0x4u  /* constant-coefficient stencils: sum each row with FP64
                                   additions instead of the default fixed-point row sum.
                                   Default: the row C*w_c - sum(neighbours) is summed exactly
@@ -275,6 +278,14 @@ void pcg_server_destroy(pcg_server *server);
  * or n > PCG_NOALLOC_MAX_N (16,777,216 unknowns); PCG_ECUDA if a CUDA call fails. */
 pcg_status pcg_true_residual_noalloc(const pcg_matrix *A, const double *b, const double *x, const double *r,
                                      double *norms, void *stream);
+
+/* Variable shift, Algorithm 4 (Section 4.1): later PCG_SPCG solves on this context use
+ * shifts[0] = sigma_{-1} (the shift of w_0) and shifts[k + 1] = sigma_k for iteration k,
+ * with the correction terms of Algorithm 4 in s, q, z and w; the sigma argument of the
+ * solve is then ignored.  count must be at least maxit + 1 at solve time (else the solve
+ * fails with PCG_EINVAL).  shifts = NULL or count <= 0 returns to a constant shift.
+ * Errors: PCG_EINVAL for a negative or non-finite shift. */
+pcg_status pcg_set_shifts(pcg_ctx *ctx, const double *shifts, int32_t count);
 
 /* Solver parameters (not part of the paper's method statement).
  *   PCG_PARAM_MIXED_ETA      inner tolerance of PCG_MIXED_IR, in (0, 1); default 2^-10

@@ -13,6 +13,7 @@
 
 #include "../../include/pcg.h"
 #include "pcg_internal.h"
+#include "pcg_general.cuh"
 
 using namespace pcgk;
 
@@ -42,6 +43,13 @@ struct pcg_ctx {
   int grid_mx[KM_NKINDS] = {0};
   double mx_eta = 0.0009765625;        // 2^-10
   int mx_max_restarts = 200;
+  // general iteration (Jacobi M^-1 and/or variable shift)
+  double* gen_base = nullptr;           // u, q, p, m (two buffers); t is v.p
+  double* d_dinv = nullptr;
+  double* d_shifts = nullptr;
+  int shifts_cap = 0;
+  std::vector<double> var_shifts;       // pcg_set_shifts (empty: constant shift)
+  int grid_gen[4] = {0, 0, 0, 0};       // by variant: 2 * jac + var
   // persistent kernel
   int grid_persistent = 0;
   double barrier_timeout_ms = 2000.0;
@@ -167,7 +175,8 @@ pcg_status pcg_create(const pcg_matrix* A, uint32_t flags, pcg_ctx** out) {
   if (!out) return PCG_EINVAL;
   *out = nullptr;
   if (!A) return PCG_EINVAL;
-  if (flags & ~(PCG_DEVICE_PTRS | PCG_PROFILE | PCG_STENCIL_FP64_SUM | PCG_PERSISTENT)) return PCG_EINVAL;
+  if (flags & ~(PCG_DEVICE_PTRS | PCG_PROFILE | PCG_STENCIL_FP64_SUM | PCG_PERSISTENT | PCG_JACOBI)) return PCG_EINVAL;
+  if ((flags & PCG_JACOBI) && (flags & PCG_DEVICE_PTRS)) return PCG_EINVAL;   // the diagonal is read on the host
   OpDesc op{};
   op.layout = A->layout;
   op.fixed_sum = (flags & PCG_STENCIL_FP64_SUM) ? 0 : 1;
@@ -241,6 +250,32 @@ pcg_status pcg_create(const pcg_matrix* A, uint32_t flags, pcg_ctx** out) {
     return bail(PCG_ENOMEM);
   }
   c->h_state = (State*)p;
+  if (flags & PCG_JACOBI) {
+    // M^{-1} = diag(A)^{-1}, formed on the host from the operator's description
+    std::vector<double> dinv(n);
+    bool ok = true;
+    if (A->layout == PCG_CSR32) {
+      for (int64_t i = 0; i < n; ++i) {
+        double d = 0.0;
+        for (int32_t k = A->row_ptr[i]; k < A->row_ptr[i + 1]; ++k)
+          if (A->col[k] == i) d += A->val[k];
+        ok = ok && d > 0.0;
+        dinv[i] = 1.0 / d;
+      }
+    } else if (A->diag) {
+      for (int64_t i = 0; i < n; ++i) {
+        ok = ok && A->diag[i] > 0.0;
+        dinv[i] = 1.0 / A->diag[i];
+      }
+    } else {
+      std::fill(dinv.begin(), dinv.end(), A->layout == PCG_STENCIL7_3D ? 1.0 / 6.0 : 1.0 / 4.0);
+    }
+    if (!ok) return bail(fail(c, PCG_EINVAL, "PCG_JACOBI needs a positive diagonal"));
+    const double* dd = nullptr;
+    c->flags &= ~PCG_DEVICE_PTRS;
+    if ((s = place<double>(c, dinv.data(), n, &dd)) != PCG_OK) return bail(s);
+    c->d_dinv = (double*)dd;
+  }
   if (flags & PCG_PERSISTENT) {
     c->grid_persistent = grid_for_persistent(c->op);
     if (c->grid_persistent <= 0) {
@@ -277,6 +312,18 @@ void pcg_destroy(pcg_ctx* c) {
 pcg_status pcg_set_stream(pcg_ctx* c, void* stream) {
   if (!c) return PCG_EINVAL;
   c->stream = stream ? (cudaStream_t)stream : c->own_stream;
+  return PCG_OK;
+}
+
+pcg_status pcg_set_shifts(pcg_ctx* c, const double* shifts, int32_t count) {
+  if (!c) return PCG_EINVAL;
+  if (!shifts || count <= 0) {
+    c->var_shifts.clear();
+    return PCG_OK;
+  }
+  for (int32_t k = 0; k < count; ++k)
+    if (!(shifts[k] >= 0.0) || !isfinite(shifts[k])) return fail(c, PCG_EINVAL, "shifts must be finite and >= 0");
+  c->var_shifts.assign(shifts, shifts + count);
   return PCG_OK;
 }
 
@@ -520,6 +567,115 @@ pcg_status run_solve_mixed(pcg_ctx* c, bool has_x0, int method, double sigma, do
   return PCG_OK;
 }
 
+pcg_status ensure_general(pcg_ctx* c, int maxit, bool jac, bool var) {
+  if (jac && !c->gen_base) {
+    void* p;
+    pcg_status s = dev_alloc(c, &p, 5 * c->vec_stride * sizeof(double));
+    if (s != PCG_OK) return s;
+    c->gen_base = (double*)p;
+  }
+  int& grid = c->grid_gen[2 * jac + var];
+  if (grid <= 0) {
+    grid = grid_for_general(c->op, jac, var);
+    if (grid <= 0) {
+      cudaGetLastError();
+      return fail(c, PCG_ECUDA, "could not size the general grid");
+    }
+  }
+  if (c->shifts_cap < maxit + 1) {
+    if (c->d_shifts) {
+      cudaFree(c->d_shifts);
+      c->owned.erase(std::find(c->owned.begin(), c->owned.end(), (void*)c->d_shifts));
+      c->d_shifts = nullptr;
+    }
+    void* p;
+    const int cap = std::max(maxit + 1, 1024);
+    pcg_status s = dev_alloc(c, &p, cap * sizeof(double));
+    if (s != PCG_OK) return s;
+    c->d_shifts = (double*)p;
+    c->shifts_cap = cap;
+  }
+  return PCG_OK;
+}
+
+// Jacobi M^{-1} and/or a variable shift: Algorithm 4 (Algorithm 3 for a constant shift).
+// sh: maxit + 1 shifts (sh[0] = sigma_{-1}).
+pcg_status run_solve_general(pcg_ctx* c, bool has_x0, const std::vector<double>& sh, bool var, double tol,
+                             int maxit, int true_every, int* iters_out, int* status_out) {
+  const bool jac = c->d_dinv != nullptr;
+  pcg_status s = ensure_general(c, maxit, jac, var);
+  if (s != PCG_OK) return s;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_shifts, sh.data(), (maxit + 1) * sizeof(double), cudaMemcpyHostToDevice,
+                              c->stream));
+  GenVecs g{};
+  g.b = c->v.b;
+  g.x = c->v.x;
+  g.r = c->v.r;
+  g.w0 = c->v.w0;
+  g.w1 = c->v.w1;
+  g.z = c->v.z;
+  g.s = c->v.s;
+  g.t = c->v.p;
+  if (jac) {
+    g.u = c->gen_base;
+    g.q = c->gen_base + c->vec_stride;
+    g.p = c->gen_base + 2 * c->vec_stride;
+    g.m0 = c->gen_base + 3 * c->vec_stride;
+    g.m1 = c->gen_base + 4 * c->vec_stride;
+    g.dinv = c->d_dinv;
+  }
+  g.shifts = c->d_shifts;
+  State st{};
+  st.status = ST_RUNNING;
+  st.maxit = maxit;
+  st.sigma = sh[0];
+  st.tol_abs = tol;   // relative until the residual kernel scales it by ||b||
+  *c->h_state = st;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_state, c->h_state, sizeof(State), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_hist, 0xff, 7 * (size_t)c->hist_cap * sizeof(double), c->stream));  // NaN
+  auto L = [&](int kind) { return launch_of(c, kind); };
+  const Launch Lg{c->grid_gen[2 * jac + var], kBlockThreads, c->stream};
+  CUDA_TRY(c, launch_residual(c->op, L(K_RESIDUAL), c->v.b, has_x0 ? c->v.x : nullptr, c->v.x, c->v.r, c->d_state,
+                              c->d_partials));
+  ++c->launches;
+  if (jac) {
+    CUDA_TRY(c, launch_diag_scale(c->d_dinv, c->v.r, g.u, (int)c->n, c->d_state, c->stream));   // u_0
+    ++c->launches;
+  }
+  CUDA_TRY(c, launch_gen_w0(c->op, Lg, g, c->d_state, c->h, c->d_partials, jac, var));
+  ++c->launches;
+  if (true_every > 0) {
+    CUDA_TRY(c, launch_true_res(c->op, L(K_TRUE_RES), c->v, c->d_state, c->h, c->d_partials));
+    ++c->launches;
+  }
+  int done = 0, chunk = 16;
+  while (done < maxit) {
+    const int todo = tol > 0.0 ? std::min(chunk, maxit - done) : maxit - done;
+    for (int k = 0; k < todo; ++k) {
+      CUDA_TRY(c, launch_gen_iter(c->op, Lg, g, c->d_state, c->h, c->d_partials, jac, var));
+      ++c->launches;
+      ++done;
+      if (true_every > 0 && done % true_every == 0) {
+        CUDA_TRY(c, launch_true_res(c->op, L(K_TRUE_RES), c->v, c->d_state, c->h, c->d_partials));
+        ++c->launches;
+      }
+    }
+    if (tol > 0.0 && done < maxit) {
+      CUDA_TRY(c, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(State), cudaMemcpyDeviceToHost, c->stream));
+      CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+      if (c->h_state->status != ST_RUNNING) break;
+      chunk = std::min(chunk * 2, 256);
+    }
+  }
+  CUDA_TRY(c, launch_true_res(c->op, L(K_TRUE_RES), c->v, c->d_state, c->h, c->d_partials));
+  ++c->launches;
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(State), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  *iters_out = c->h_state->iter;
+  *status_out = c->h_state->status;
+  return PCG_OK;
+}
+
 pcg_status solve_common(pcg_ctx* c, const double* b, const double* x0, int32_t method, double sigma, double tol,
                         int32_t maxit, int32_t precision, double* x_out, pcg_result* res, bool host) {
   if (!c) return PCG_EINVAL;
@@ -532,6 +688,21 @@ pcg_status solve_common(pcg_ctx* c, const double* b, const double* x0, int32_t m
   if (precision != PCG_FP64 && precision != PCG_MIXED_IR) return fail(c, PCG_EINVAL, "unknown precision");
   if (precision == PCG_MIXED_IR && method == PCG_CG)
     return fail(c, PCG_ENOTIMPL, "PCG_MIXED_IR runs Algorithm 3 (PCG_PCG or PCG_SPCG), not classic CG");
+  // the shift schedule: pcg_set_shifts (PCG_SPCG only), else the constant sigma (0 for PCG_PCG)
+  const bool scheduled = method == PCG_SPCG && !c->var_shifts.empty();
+  if (scheduled && (int)c->var_shifts.size() < maxit + 1)
+    return fail(c, PCG_EINVAL, "pcg_set_shifts gave fewer than maxit + 1 shifts");
+  std::vector<double> sh(maxit + 1, method == PCG_SPCG ? sigma : 0.0);
+  bool var = false;
+  if (scheduled) {
+    std::copy(c->var_shifts.begin(), c->var_shifts.begin() + maxit + 1, sh.begin());
+    for (int k = 1; k <= maxit; ++k) var = var || sh[k] != sh[0];
+    sigma = sh[0];
+  }
+  const bool general = c->d_dinv != nullptr || var;
+  if (general && method == PCG_CG) return fail(c, PCG_ENOTIMPL, "PCG_JACOBI is implemented for Algorithms 2 and 3");
+  if (general && precision == PCG_MIXED_IR)
+    return fail(c, PCG_ENOTIMPL, "PCG_MIXED_IR with PCG_JACOBI or variable shifts is not implemented");
   CUDA_TRY(c, cudaSetDevice(c->device));
   pcg_status s;
   if ((s = ensure_vectors(c)) != PCG_OK) return s;
@@ -550,6 +721,7 @@ pcg_status solve_common(pcg_ctx* c, const double* b, const double* x0, int32_t m
   const int true_every = res ? res->true_every : 0;
   int iters = 0, st = ST_RUNNING;
   s = precision == PCG_MIXED_IR ? run_solve_mixed(c, x0 != nullptr, method, sigma, tol, maxit, true_every, &iters, &st)
+      : general                  ? run_solve_general(c, x0 != nullptr, sh, var, tol, maxit, true_every, &iters, &st)
                                  : run_solve(c, x0 != nullptr, method, sigma, tol, maxit, true_every, &iters, &st);
   c->v.b = c->d_b;
   if (s != PCG_OK) return s;

@@ -3,6 +3,7 @@
 
 #include "pcg_kernels.cuh"
 #include "pcg_persistent.cuh"
+#include "pcg_general.cuh"
 
 // Largest number of unknowns per thread for stencil operators (2 = 128-bit accesses).
 #ifndef PCG_STENCIL_MAX_VEC
@@ -116,6 +117,51 @@ cudaError_t launch_cg_update(const OpDesc& d, const Launch& L, Vecs v, State* st
 cudaError_t launch_cg_p(const OpDesc& d, const Launch& L, Vecs v, State* st, Hist h) {
   return with_op(d, [&](auto op) { return K<decltype(op)>::cg_p(op, L, v, st, h); });
 }
+// (jac, var) -> the instantiated variant; M = I with a constant shift has no general variant
+template <class Op, class F>
+cudaError_t with_general(bool jac, bool var, F&& f) {
+  if (jac && var) return f(GeneralKernels<Op, true, true>{});
+  if (jac) return f(GeneralKernels<Op, true, false>{});
+  if (var) return f(GeneralKernels<Op, false, true>{});
+  return cudaErrorInvalidValue;
+}
+
+int grid_for_general(const OpDesc& d, bool jac, bool var) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  int per_sm = 0;
+  with_op(d, [&](auto op) {
+    return with_general<std::decay_t<decltype(op)>>(jac, var, [&](auto K) {
+      per_sm = decltype(K)::blocks_per_sm();
+      return cudaSuccess;
+    });
+  });
+  if (per_sm <= 0) return 0;
+  const long long units = d.n / op_vec(d);
+  long long g = (long long)sms * per_sm;
+  const long long need = (units + kBlock - 1) / kBlock;
+  if (need < g) g = need;
+  if (g < 1) g = 1;
+  if (g > kMaxPartialBlocks * 2 / 3) g = kMaxPartialBlocks * 2 / 3;   // three partials per block
+  return (int)g;
+}
+
+cudaError_t launch_gen_w0(const OpDesc& d, const Launch& L, const GenVecs& v, State* st, Hist h, double* partials,
+                          bool jac, bool var) {
+  return with_op(d, [&](auto op) {
+    return with_general<std::decay_t<decltype(op)>>(jac, var,
+                                                    [&](auto K) { return K.w0(op, L, v, st, h, partials); });
+  });
+}
+cudaError_t launch_gen_iter(const OpDesc& d, const Launch& L, const GenVecs& v, State* st, Hist h, double* partials,
+                            bool jac, bool var) {
+  return with_op(d, [&](auto op) {
+    return with_general<std::decay_t<decltype(op)>>(jac, var,
+                                                    [&](auto K) { return K.iter(op, L, v, st, h, partials); });
+  });
+}
+
 int grid_for_persistent(const OpDesc& d) {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;

@@ -84,6 +84,15 @@ cudaError_t launch_cg_update(const OpDesc& op, const Launch& L, Vecs v, State* s
 cudaError_t launch_cg_p(const OpDesc& op, const Launch& L, Vecs v, State* st, Hist h);
 cudaError_t launch_apply(const OpDesc& op, const Launch& L, const double* x, double* y);
 
+// General iteration: Jacobi preconditioner and/or variable shift (pcg_general.cuh).
+struct GenVecs;
+// jac: D^{-1} recurrences; var: variable-shift correction terms (at least one is set)
+int grid_for_general(const OpDesc& op, bool jac, bool var);
+cudaError_t launch_gen_w0(const OpDesc& op, const Launch& L, const GenVecs& v, State* st, Hist h, double* partials,
+                          bool jac, bool var);
+cudaError_t launch_gen_iter(const OpDesc& op, const Launch& L, const GenVecs& v, State* st, Hist h, double* partials,
+                            bool jac, bool var);
+
 // Persistent cooperative form of the iteration (pcg_persistent.cuh).
 int grid_for_persistent(const OpDesc& op);
 cudaError_t launch_spcg_persistent(const OpDesc& op, int grid, cudaStream_t stream, Vecs v, State* st, Hist h,

@@ -31,6 +31,7 @@ PCG_STENCIL_FP64_SUM = 0x4
 # pcg_set_param parameters
 PCG_PARAM_MIXED_ETA, PCG_PARAM_MAX_RESTARTS, PCG_PARAM_BARRIER_TIMEOUT_MS, PCG_PARAM_TEST_BARRIER_PHANTOMS = 1, 2, 3, 4
 PCG_PERSISTENT = 0x8
+PCG_JACOBI = 0x10
 
 METHODS = {"cg": PCG_CG, "pcg": PCG_PCG, "spcg": PCG_SPCG}
 
@@ -80,6 +81,7 @@ def lib() -> ctypes.CDLL:
         L.pcg_psi.argtypes = [vp, vp, vp, i32, vp, i32, vp]
         L.pcg_apply.argtypes = [vp, vp, vp]
         L.pcg_set_param.argtypes = [vp, i32, f64]
+        L.pcg_set_shifts.argtypes = [vp, vp, i32]
         L.pcg_batch_create.argtypes = [vp, i32, ctypes.c_uint32, ctypes.POINTER(vp)]
         L.pcg_batch_solve.argtypes = [vp, vp, vp, i32, vp, f64, i32, vp, vp, vp]
         L.pcg_batch_autotune.argtypes = [vp, vp, vp, i32, vp, vp]
@@ -99,7 +101,7 @@ def lib() -> ctypes.CDLL:
         L.pcg_version.argtypes = []
         L.pcg_version.restype = ctypes.c_char_p
         for f in ("pcg_create", "pcg_set_stream", "pcg_solve", "pcg_solve_device", "pcg_select_sigma", "pcg_psi",
-                  "pcg_apply", "pcg_true_residual_noalloc", "pcg_set_param", "pcg_batch_create", "pcg_batch_solve",
+                  "pcg_apply", "pcg_true_residual_noalloc", "pcg_set_param", "pcg_set_shifts", "pcg_batch_create", "pcg_batch_solve",
                   "pcg_batch_autotune", "pcg_batch_set_cluster", "pcg_batch_last_kernel_ms", "pcg_server_create",
                   "pcg_submit", "pcg_poll", "pcg_server_stats",
                   "pcg_kernel_stats", "pcg_kernel_stats_reset"):
@@ -159,6 +161,13 @@ def pcg_solve_device(ctx, b, x0, method, sigma, tol, maxit, precision, x_out, re
 
 def pcg_set_param(ctx, param: int, value: float) -> int:
     return lib().pcg_set_param(ctx, param, value)
+
+
+def pcg_set_shifts(ctx, shifts) -> int:
+    if shifts is None:
+        return lib().pcg_set_shifts(ctx, None, 0)
+    a = np.ascontiguousarray(shifts, dtype=np.float64)
+    return lib().pcg_set_shifts(ctx, a.ctypes.data, a.size)
 
 
 def pcg_apply(ctx, x, y) -> int:
