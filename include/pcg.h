@@ -148,7 +148,10 @@ pcg_status pcg_set_stream(pcg_ctx *ctx, void *stream);
  *   restarts from the current x (iterative refinement).  tol applies to the true
  *   residual ||b - A x|| <= tol ||b||; the solve also ends at maxit iterations or
  *   when a restart does not lower the true residual (PCG_ENOTCONV).  true_hist
- *   holds the true residual at every restart and at exit.
+ *   holds the true residual at every restart and at exit.  On a PCG_JACOBI
+ *   context u, q, t, p and m = D^{-1} w are binary32 as well; the restart forms
+ *   u_0 = D^{-1} r rounded to binary32 and w_0 = A u_0 - sigma r in binary64.
+ *   A variable shift (pcg_set_shifts) with PCG_MIXED_IR gives PCG_ENOTIMPL.
  * Returns PCG_OK on convergence, PCG_ENOTCONV at maxit (always when tol = 0),
  * PCG_EBREAKDOWN; res may be NULL.  x_out is written in every non-error case. */
 pcg_status pcg_solve(pcg_ctx *ctx, const double *b, const double *x0, int32_t method, double sigma, double tol,

@@ -45,6 +45,8 @@ struct pcg_ctx {
   int mx_max_restarts = 200;
   // general iteration (Jacobi M^-1 and/or variable shift)
   double* gen_base = nullptr;           // u, q, p, m (two buffers); t is v.p
+  const float* dinv32 = nullptr;        // mixed precision with PCG_JACOBI
+  double* mx_u64 = nullptr;             // u_0 widened to binary64 at a restart
   double* d_dinv = nullptr;
   double* d_shifts = nullptr;
   int shifts_cap = 0;
@@ -477,7 +479,7 @@ pcg_status ensure_mixed(pcg_ctx* c) {
   if (c->mixed_ready) return PCG_OK;
   auto copy32 = [&](const double* src, const float** dst) -> pcg_status {
     void* p;
-    const long long count = src == c->op.val ? c->nnz : c->n;
+    const long long count = src == c->op.val ? c->nnz : (long long)c->n;
     pcg_status s = dev_alloc(c, &p, (size_t)(count > 0 ? count : 1) * sizeof(float));
     if (s != PCG_OK) return s;
     CUDA_TRY(c, launch_to_f32(src, (float*)p, count, c->stream));
@@ -492,6 +494,12 @@ pcg_status ensure_mixed(pcg_ctx* c) {
     if ((s = copy32(c->op.ax, &c->op.ax32)) != PCG_OK) return s;
     if ((s = copy32(c->op.ay, &c->op.ay32)) != PCG_OK) return s;
     if (c->op.layout == PCG_STENCIL7_3D && (s = copy32(c->op.az, &c->op.az32)) != PCG_OK) return s;
+  }
+  if (c->d_dinv) {
+    if ((s = copy32(c->d_dinv, &c->dinv32)) != PCG_OK) return s;
+    void* p;
+    if ((s = dev_alloc(c, &p, c->vec_stride * sizeof(double))) != PCG_OK) return s;
+    c->mx_u64 = (double*)p;
   }
   for (int k = 0; k < KM_NKINDS; ++k) {
     c->grid_mx[k] = grid_for_mixed(c->op, k, kBlockThreads);
@@ -527,13 +535,44 @@ pcg_status run_solve_mixed(pcg_ctx* c, bool has_x0, int method, double sigma, do
   CUDA_TRY(c, cudaMemcpyAsync(c->d_state, c->h_state, sizeof(State), cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(c->d_hist, 0xff, 7 * (size_t)c->hist_cap * sizeof(double), c->stream));  // NaN
   if (!has_x0) CUDA_TRY(c, cudaMemsetAsync(c->v.x, 0, (size_t)c->n * sizeof(double), c->stream));
+  const bool jac = c->d_dinv != nullptr;
   const Launch Lr{c->grid_mx[KM_RESTART], kBlockThreads, c->stream};
-  const Launch Lw{c->grid_mx[KM_W0], kBlockThreads, c->stream};
-  const Launch Li{c->grid_mx[KM_ITER], kBlockThreads, c->stream};
+  const Launch Lw{c->grid_mx[jac ? KM_W0_JAC : KM_W0], kBlockThreads, c->stream};
+  const Launch Li{c->grid_mx[jac ? KM_ITER_JAC : KM_ITER], kBlockThreads, c->stream};
+  GenVecs g{};
+  if (jac) {
+    if (!c->gen_base) {
+      void* p;
+      pcg_status s = dev_alloc(c, &p, 5 * c->vec_stride * sizeof(double));
+      if (s != PCG_OK) return s;
+      c->gen_base = (double*)p;
+    }
+    g.b = c->v.b;
+    g.x = c->v.x;
+    g.r = c->v.r;
+    g.w0 = c->v.w0;
+    g.w1 = c->v.w1;
+    g.z = c->v.z;
+    g.s = c->v.s;
+    g.t = c->v.p;
+    g.u = c->gen_base;
+    g.q = c->gen_base + c->vec_stride;
+    g.p = c->gen_base + 2 * c->vec_stride;
+    g.m0 = c->gen_base + 3 * c->vec_stride;
+    g.m1 = c->gen_base + 4 * c->vec_stride;
+    g.dinv = c->d_dinv;
+    g.dinv32 = c->dinv32;
+  }
   auto restart_pair = [&]() -> pcg_status {
     CUDA_TRY(c, launch_mx_restart(c->op, Lr, c->v, c->d_state, c->h, c->d_partials));
-    CUDA_TRY(c, launch_mx_w0(c->op, Lw, c->v, c->d_state, c->h, c->d_partials));
-    c->launches += 2;
+    if (jac) {
+      CUDA_TRY(c, launch_mxj_u0(g, c->mx_u64, (int)c->n, c->d_state, c->stream));
+      CUDA_TRY(c, launch_mxj_w0(c->op, Lw, g, c->mx_u64, c->d_state, c->h, c->d_partials));
+      c->launches += 3;
+    } else {
+      CUDA_TRY(c, launch_mx_w0(c->op, Lw, c->v, c->d_state, c->h, c->d_partials));
+      c->launches += 2;
+    }
     return PCG_OK;
   };
   pcg_status s = restart_pair();
@@ -549,7 +588,11 @@ pcg_status run_solve_mixed(pcg_ctx* c, bool has_x0, int method, double sigma, do
     if (stt != ST_RUNNING && stt != ST_RESTART) break;
     if (launched >= max_launches) break;
     for (int k = 0; k < chunk; ++k) {
-      CUDA_TRY(c, launch_mx_iter(c->op, Li, c->v, c->d_state, c->h, c->d_partials));
+      if (jac) {
+        CUDA_TRY(c, launch_mxj_iter(c->op, Li, g, c->d_state, c->h, c->d_partials));
+      } else {
+        CUDA_TRY(c, launch_mx_iter(c->op, Li, c->v, c->d_state, c->h, c->d_partials));
+      }
       ++c->launches;
       ++launched;
       if (launched % kRestartEvery == 0) {
@@ -701,8 +744,8 @@ pcg_status solve_common(pcg_ctx* c, const double* b, const double* x0, int32_t m
   }
   const bool general = c->d_dinv != nullptr || var;
   if (general && method == PCG_CG) return fail(c, PCG_ENOTIMPL, "PCG_JACOBI is implemented for Algorithms 2 and 3");
-  if (general && precision == PCG_MIXED_IR)
-    return fail(c, PCG_ENOTIMPL, "PCG_MIXED_IR with PCG_JACOBI or variable shifts is not implemented");
+  if (var && precision == PCG_MIXED_IR)
+    return fail(c, PCG_ENOTIMPL, "PCG_MIXED_IR with a variable shift is not implemented");
   CUDA_TRY(c, cudaSetDevice(c->device));
   pcg_status s;
   if ((s = ensure_vectors(c)) != PCG_OK) return s;

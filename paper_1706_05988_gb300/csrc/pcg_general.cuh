@@ -24,6 +24,7 @@ struct GenVecs {
   double *x, *r, *w0, *w1, *z, *s, *t;   // t doubles as p when M = I
   double *u, *q, *p, *m0, *m1;           // JAC only
   const double* dinv;                    // JAC only
+  const float* dinv32;                   // JAC, mixed precision only
   const double* shifts;                  // maxit + 1 shifts
 };
 

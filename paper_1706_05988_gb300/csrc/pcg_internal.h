@@ -99,13 +99,19 @@ cudaError_t launch_spcg_persistent(const OpDesc& op, int grid, cudaStream_t stre
                                    double* partials, unsigned long long timeout_ns, unsigned phantoms);
 
 // Mixed precision (pcg_mixed.cuh): FP32 w, z, s, p stored in the FP64 buffers of Vecs.
-enum { KM_RESTART = 0, KM_W0, KM_ITER, KM_NKINDS };
+enum { KM_RESTART = 0, KM_W0, KM_ITER, KM_W0_JAC, KM_ITER_JAC, KM_NKINDS };
 int mixed_vec(const OpDesc& op);
 int grid_for_mixed(const OpDesc& op, int kind, int block);
 cudaError_t launch_mx_restart(const OpDesc& op, const Launch& L, Vecs v, State* st, Hist h, double* partials);
 cudaError_t launch_mx_w0(const OpDesc& op, const Launch& L, Vecs v, State* st, Hist h, double* partials);
 cudaError_t launch_mx_iter(const OpDesc& op, const Launch& L, Vecs v, State* st, Hist h, double* partials);
 cudaError_t launch_to_f32(const double* src, float* dst, long long n, cudaStream_t stream);
+// Mixed precision with M^{-1} = D^{-1} (pcg_mixed_jacobi.cuh); v holds the binary32 vectors.
+cudaError_t launch_mxj_u0(const GenVecs& v, double* u64, int n, const State* st, cudaStream_t stream);
+cudaError_t launch_mxj_w0(const OpDesc& op, const Launch& L, const GenVecs& v, double* u64, State* st, Hist h,
+                         double* partials);
+cudaError_t launch_mxj_iter(const OpDesc& op, const Launch& L, const GenVecs& v, State* st, Hist h,
+                           double* partials);
 
 // psi_i(sigma) for every shift of sig[ngrid]; alpha/beta device arrays (>= i+1 entries).
 cudaError_t launch_psi(const double* alpha, const double* beta, int i, const double* sig, int ngrid, double* psi,

@@ -3,6 +3,7 @@
 #include <utility>
 
 #include "pcg_mixed.cuh"
+#include "pcg_mixed_jacobi.cuh"
 
 namespace pcgk {
 namespace {
@@ -62,7 +63,20 @@ cudaError_t launch_mx_iter(const OpDesc& d, const Launch& L, Vecs v, State* st, 
   return with_op32(d, [&](auto op) { return MixedIterKernels<decltype(op)>::iter(op, L, v, st, h, partials); });
 }
 
+cudaError_t launch_mxj_iter(const OpDesc& d, const Launch& L, const GenVecs& v, State* st, Hist h, double* partials) {
+  return with_op32(d, [&](auto op) { return MixedJacIterKernels<decltype(op)>::iter(op, L, v, st, h, partials); });
+}
+
 int grid_for_mixed(const OpDesc& d, int kind, int block);   // defined with the restart kernels
+
+int mixedj_iter_blocks_per_sm(const OpDesc& d) {
+  int nb = 0;
+  with_op32(d, [&](auto op) {
+    nb = MixedJacIterKernels<decltype(op)>::blocks_per_sm();
+    return cudaSuccess;
+  });
+  return nb;
+}
 
 int mixed_iter_blocks_per_sm(const OpDesc& d) {
   int nb = 0;

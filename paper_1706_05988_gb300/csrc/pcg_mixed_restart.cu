@@ -4,10 +4,12 @@
 #include <utility>
 
 #include "pcg_mixed.cuh"
+#include "pcg_mixed_jacobi.cuh"
 
 namespace pcgk {
 
-int mixed_iter_blocks_per_sm(const OpDesc& d);   // pcg_mixed_iter.cu
+int mixed_iter_blocks_per_sm(const OpDesc& d);    // pcg_mixed_iter.cu
+int mixedj_iter_blocks_per_sm(const OpDesc& d);   // pcg_mixed_iter.cu
 
 namespace {
 
@@ -65,15 +67,45 @@ cudaError_t launch_mx_w0(const OpDesc& d, const Launch& L, Vecs v, State* st, Hi
   return with_op64(d, [&](auto op) { return MixedRestartKernels<decltype(op)>::w0(op, L, v, st, h, partials); });
 }
 
+cudaError_t launch_mxj_w0(const OpDesc& d, const Launch& L, const GenVecs& v, double* u64, State* st, Hist h,
+                         double* partials) {
+  return with_op64(d,
+                   [&](auto op) { return MixedJacRestartKernels<decltype(op)>::w0(op, L, v, u64, st, h, partials); });
+}
+
+namespace {
+__global__ void k_mxj_u0(GenVecs v, double* __restrict__ u64, int n, const State* st) {
+  if (st->status != ST_RESTART) return;
+  float* __restrict__ uf = reinterpret_cast<float*>(v.u);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float u32 = f32_of(v.dinv[i] * v.r[i]);
+    uf[i] = u32;
+    u64[i] = f64_of(u32);
+  }
+}
+}  // namespace
+
+cudaError_t launch_mxj_u0(const GenVecs& v, double* u64, int n, const State* st, cudaStream_t stream) {
+  const int grid = n / 256 + 1 < 4096 ? n / 256 + 1 : 4096;
+  k_mxj_u0<<<grid, 256, 0, stream>>>(v, u64, n, st);
+  return cudaGetLastError();
+}
+
 int grid_for_mixed(const OpDesc& d, int kind, int block) {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   int per_sm = 0;
   long long units = 0;
-  if (kind == KM_ITER) {
-    per_sm = mixed_iter_blocks_per_sm(d);
+  if (kind == KM_ITER || kind == KM_ITER_JAC) {
+    per_sm = kind == KM_ITER ? mixed_iter_blocks_per_sm(d) : mixedj_iter_blocks_per_sm(d);
     units = d.n / mixed_vec(d);
+  } else if (kind == KM_W0_JAC) {
+    with_op64(d, [&](auto op) {
+      per_sm = MixedJacRestartKernels<decltype(op)>::blocks_per_sm();
+      return cudaSuccess;
+    });
+    units = d.n / op_vec(d);
   } else {
     with_op64(d, [&](auto op) {
       per_sm = MixedRestartKernels<decltype(op)>::blocks_per_sm(kind);

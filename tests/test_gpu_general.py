@@ -191,8 +191,6 @@ def test_general_errors(B):
     with B.Solver(P, flags=B.PCG_JACOBI) as s:
         r = s.solve(b, method="cg", maxit=10, raise_on_error=False)
         assert r.status == B.PCG_ENOTIMPL
-        r = s.solve(b, method="spcg", sigma=1.0, maxit=10, precision=B.PCG_MIXED_IR, raise_on_error=False)
-        assert r.status == B.PCG_ENOTIMPL
         assert B.pcg_set_shifts(s.ctx, np.array([1.0, -0.5])) == B.PCG_EINVAL
         assert B.pcg_set_shifts(s.ctx, np.array([1.0, np.nan])) == B.PCG_EINVAL
         assert B.pcg_set_shifts(s.ctx, np.full(5, 1.0)) == B.PCG_OK
