@@ -187,6 +187,38 @@ def batch_measure(pkg, S, nsys: int, seed: int = 0) -> dict:
             "speedup": (nsys / tb) / one_rate}
 
 
+def varcoef_measure(pkg, S) -> dict:
+    """128^3 FV diffusion, kappa = 10^U[-3,3] on 8^3 blocks, b ~ N(0,1), to a true relative residual
+    of 1e-10 with Jacobi: FP64 shifted p-CG against mixed precision with FP64 refinement (the same
+    shift, from the psi tool over a 30-iteration pilot), each timed once after a warm-up solve."""
+    import ctypes
+    import numpy as np
+    import torch
+    from paper_1706_05988_gb300 import pcg as C
+    P = S.varcoef_3d(128, block=8, seed=0)
+    b = S.normal(1, P.n)
+    out = {"workload": "128^3 7-point FV diffusion, kappa 10^U[-3,3] on 8^3 blocks, b ~ N(0,1), Jacobi M^-1, "
+                       "tol 1e-10 (true residual)"}
+    with pkg.Solver(P, flags=pkg.PCG_JACOBI) as s:
+        grid = np.linspace(0.0, 2.0, 41)
+        so = ctypes.c_double()
+        st = C.lib().pcg_select_sigma(s.ctx, np.ascontiguousarray(b).ctypes.data, 30, grid.ctypes.data, grid.size,
+                                      ctypes.byref(so), None)
+        sigma = so.value if st == C.PCG_OK else 1.0
+        out["sigma"] = sigma
+        for name, prec in (("fp64", C.PCG_FP64), ("mixed_ir", C.PCG_MIXED_IR)):
+            for rep in range(2):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = s.solve(b, method="spcg", sigma=sigma, tol=1e-10, maxit=40000, precision=prec,
+                            raise_on_error=False)
+                dt = time.perf_counter() - t0
+            out[name] = {"ms": dt * 1e3, "iters": int(r.iters), "status": int(r.status),
+                         "true_relres": float(r.final_true_relres)}
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["ms"] / out["mixed_ir"]["ms"]
+    return out
+
+
 def serving_trace(nreq: int, rate: float, seed: int = 0):
     """Seeded request stream: Poisson arrivals at `rate` per second; n log-uniform in
     [1e3, 1e5]; half stencils (2D/3D unscaled Laplacians), half random SDD CSR (7-27 entries
@@ -406,6 +438,10 @@ def run_ours(args):
     if not args.no_batch:
         batch = batch_measure(pkg, S, args.batch_systems)
 
+    varcoef = None
+    if not args.no_varcoef:
+        varcoef = varcoef_measure(pkg, S)
+
     serving = None
     if not args.no_serving:
         serving = serving_measure(pkg, args.serving_requests, args.serving_rate)
@@ -448,7 +484,8 @@ def run_ours(args):
                                       "per SM x 152 SMs x 2.07 GHz (ncu sm__sass_thread_inst_executed_op_dfma "
                                       "peak_sustained)"},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
-                "csr_int32": csr, "persistent": persistent, "batch": batch, "serving": serving}
+                "csr_int32": csr, "persistent": persistent, "varcoef_128": varcoef, "batch": batch,
+                "serving": serving}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -467,6 +504,7 @@ def main():
     ap.add_argument("--no-csr", action="store_true", help="skip the CSR form of the workload")
     ap.add_argument("--no-persistent", action="store_true", help="skip the persistent-kernel measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve measurement")
+    ap.add_argument("--no-varcoef", action="store_true", help="skip the 128^3 variable-coefficient measurement")
     ap.add_argument("--batch-systems", type=int, default=128, help="systems in the batched-solve measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serving-requests", type=int, default=400)

@@ -192,16 +192,22 @@ pcg_status pcg_psi(pcg_ctx *ctx, const double *alpha, const double *beta, int32_
  * variable coefficients, or CSR) but not their sizes. */
 typedef struct pcg_batch pcg_batch;
 
-/* Copy nsys operators (host arrays, pcg_matrix as for pcg_create) to the device.
- * flags must be 0.  Errors: PCG_EINVAL (mixed families, invalid description),
- * PCG_ENOMEM, PCG_ECUDA. */
+/* Copy nsys operators (host arrays, pcg_matrix as for pcg_create) to the device,
+ * with binary32 copies of their coefficients for mixed precision.  flags: 0 or
+ * PCG_JACOBI (M^{-1} = diag(A)^{-1} for every system, as for pcg_create).
+ * Errors: PCG_EINVAL (mixed families, invalid description, a non-positive diagonal
+ * with PCG_JACOBI), PCG_ENOMEM, PCG_ECUDA. */
 pcg_status pcg_batch_create(const pcg_matrix *systems, int32_t nsys, uint32_t flags, pcg_batch **out);
 
 /* Solve every system: b[k] and x_out[k] are host arrays of n_k doubles; method
  * PCG_PCG or PCG_SPCG with sigma[k] >= 0 (sigma may be NULL for PCG_PCG); x_0 = 0;
  * stop at ||r_i|| <= tol ||b_k|| or after maxit iterations.  iters[k], status[k]
  * (a pcg_status per system) and true_relres[k] = ||b_k - A_k x_k|| / ||b_k|| may be
- * NULL.  Returns PCG_OK when every system converged, else PCG_ENOTCONV. */
+ * NULL.  Returns PCG_OK when every system converged, else PCG_ENOTCONV.
+ * With precision PCG_MIXED_IR (pcg_batch_set_precision) each system runs the
+ * mixed-precision iteration with restarts of pcg_solve's PCG_MIXED_IR and tol
+ * applies to the true residual ||b_k - A_k x_k||; a restart that does not lower
+ * the true residual ends that system's solve as not converged. */
 pcg_status pcg_batch_solve(pcg_batch *batch, const double *const *b, double *const *x_out, int32_t method,
                            const double *sigma, double tol, int32_t maxit, int32_t *iters, int32_t *status,
                            double *true_relres);
@@ -214,6 +220,12 @@ pcg_status pcg_batch_autotune(pcg_batch *batch, const double *const *b, const do
                               int32_t *cluster_out, double *ms_out);
 pcg_status pcg_batch_set_cluster(pcg_batch *batch, int32_t cluster_size);
 
+/* Precision of later pcg_batch_solve calls: PCG_FP64 (default) or PCG_MIXED_IR.
+ * pcg_batch_set_param takes PCG_PARAM_MIXED_ETA and PCG_PARAM_MAX_RESTARTS with the
+ * meaning and defaults they have for pcg_set_param.  Errors: PCG_EINVAL. */
+pcg_status pcg_batch_set_precision(pcg_batch *batch, int32_t precision);
+pcg_status pcg_batch_set_param(pcg_batch *batch, int32_t param, double value);
+
 /* CUDA-event time (ms) of the last batch kernel. */
 pcg_status pcg_batch_last_kernel_ms(const pcg_batch *batch, double *ms);
 
@@ -225,7 +237,7 @@ void pcg_batch_destroy(pcg_batch *batch);
  * served); otherwise the request waits on the host until earlier requests are polled.
  * Admitted requests go to a persistent kernel whose thread-block clusters take them as
  * they come free, so requests that arrive while others run overlap on the device;
- * each request is solved by one cluster exactly as in pcg_batch (binary64, x_0 = 0),
+ * each request is solved by one cluster exactly as in pcg_batch (x_0 = 0),
  * so its result does not depend on what else runs.  With no work for 20 ms the kernel
  * exits and is relaunched by the next submit or poll.  The server is internally
  * synchronised (calls may come from several host threads). */
@@ -242,6 +254,17 @@ pcg_status pcg_server_create(size_t hbm_budget_bytes, int32_t max_slots, pcg_ser
  * never fit in the arena. */
 pcg_status pcg_submit(pcg_server *server, const pcg_matrix *A, const double *b, double tol, int32_t method,
                       double sigma, int32_t maxit, uint64_t *ticket);
+
+/* pcg_submit with a preconditioner and a precision for this request: flags 0 or
+ * PCG_JACOBI (M^{-1} = diag(A)^{-1}, as for pcg_create); precision PCG_FP64 or
+ * PCG_MIXED_IR (binary32 auxiliary vectors with binary64 restarts as in pcg_solve,
+ * eta = 2^-10, at most 200 restarts; tol then applies to the true residual).  The
+ * request's arena block also holds its Jacobi vectors and binary32 coefficients.
+ * With PCG_JACOBI, sigma < 0 selects 1, the mean diagonal entry of M^{-1} A.
+ * pcg_submit(...) is pcg_submit_ex(..., 0, PCG_FP64, ticket).  Errors as pcg_submit,
+ * and PCG_EINVAL for unknown flags or precision or a non-positive diagonal. */
+pcg_status pcg_submit_ex(pcg_server *server, const pcg_matrix *A, const double *b, double tol, int32_t method,
+                         double sigma, int32_t maxit, uint32_t flags, int32_t precision, uint64_t *ticket);
 
 /* PCG_PENDING until the request is done; then x_out (host, n doubles, may be NULL) and
  * res (iters, status, final_true_relres; may be NULL) are filled, the request's memory

@@ -22,15 +22,33 @@
 
 #define PCG_KERNELS_IMPL
 #include "../../include/pcg.h"
-#include "pcg_cluster_solve.cuh"
+#include "pcg_cluster_mixed.cuh"
 
 namespace pcgk {
 namespace {
 
-template <int F>
+// Solver per cluster: binary64 M = I, binary64 Jacobi, mixed M = I, mixed Jacobi.
+enum { BM_FP64 = 0, BM_JAC, BM_MX, BM_MXJ, BM_NMODES };
+
+struct BatchParams {
+  double tol, eta;
+  int maxit, max_restarts;
+};
+
+template <int F, int MODE>
+__device__ __forceinline__ void solve_one(cg::cluster_group& cl, double (*part)[4], int& slot, const BatchSys& d,
+                                          const BatchVecs& V, const BatchParams& prm, BatchOut& res) {
+  if constexpr (MODE == BM_FP64) cluster_solve<F>(cl, part, slot, d, V, prm.tol, prm.maxit, res);
+  if constexpr (MODE == BM_JAC) cluster_solve_jac<F>(cl, part, slot, d, V, prm.tol, prm.maxit, res);
+  if constexpr (MODE == BM_MX)
+    cluster_solve_mx<F, false>(cl, part, slot, d, V, prm.tol, prm.maxit, prm.eta, prm.max_restarts, res);
+  if constexpr (MODE == BM_MXJ)
+    cluster_solve_mx<F, true>(cl, part, slot, d, V, prm.tol, prm.maxit, prm.eta, prm.max_restarts, res);
+}
+
+template <int F, int MODE>
 __global__ void __launch_bounds__(kBlock) k_batch(const BatchSys* __restrict__ sys, const int* __restrict__ order,
-                                                  int nsys, int* next, BatchVecs V, BatchOut* out, double tol,
-                                                  int maxit) {
+                                                  int nsys, int* next, BatchVecs V, BatchOut* out, BatchParams prm) {
   cg::cluster_group cl = cg::this_cluster();
   const unsigned rank = cl.block_rank();
   __shared__ double part[2][4];
@@ -45,14 +63,14 @@ __global__ void __launch_bounds__(kBlock) k_batch(const BatchSys* __restrict__ s
     const int k = order[task];
     const BatchSys d = sys[k];
     BatchOut res;
-    cluster_solve<F>(cl, part, slot, d, V, tol, maxit, res);
+    solve_one<F, MODE>(cl, part, slot, d, V, prm, res);
     if (rank == 0 && threadIdx.x == 0) out[k] = res;
   }
 }
 
-template <int F>
+template <int F, int MODE>
 cudaError_t launch_batch(int clusters, int csize, cudaStream_t stream, const BatchSys* sys, const int* order,
-                         int nsys, int* next, BatchVecs V, BatchOut* out, double tol, int maxit) {
+                         int nsys, int* next, BatchVecs V, BatchOut* out, BatchParams prm) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(clusters * csize);
   cfg.blockDim = dim3(kBlock);
@@ -64,13 +82,14 @@ cudaError_t launch_batch(int clusters, int csize, cudaStream_t stream, const Bat
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_batch<F>, sys, order, nsys, next, V, out, tol, maxit);
+  return cudaLaunchKernelEx(&cfg, k_batch<F, MODE>, sys, order, nsys, next, V, out, prm);
 }
 
-template <int F>
+template <int F, int MODE>
 int max_clusters(int csize) {
   if (csize > 8) {
-    if (cudaFuncSetAttribute(k_batch<F>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) return 0;
+    if (cudaFuncSetAttribute(k_batch<F, MODE>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+      return 0;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(csize);
@@ -83,17 +102,29 @@ int max_clusters(int csize) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int n = 0;
-  return cudaOccupancyMaxActiveClusters(&n, k_batch<F>, &cfg) == cudaSuccess ? n : 0;
+  return cudaOccupancyMaxActiveClusters(&n, k_batch<F, MODE>, &cfg) == cudaSuccess ? n : 0;
 }
 
+template <int F, class Fn>
+cudaError_t with_mode(int mode, Fn&& fn) {
+  switch (mode) {
+    case BM_FP64: return fn(std::integral_constant<int, F>{}, std::integral_constant<int, BM_FP64>{});
+    case BM_JAC: return fn(std::integral_constant<int, F>{}, std::integral_constant<int, BM_JAC>{});
+    case BM_MX: return fn(std::integral_constant<int, F>{}, std::integral_constant<int, BM_MX>{});
+    case BM_MXJ: return fn(std::integral_constant<int, F>{}, std::integral_constant<int, BM_MXJ>{});
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// fn(family, mode) with both as compile-time constants
 template <class Fn>
-cudaError_t with_family(int fam, Fn&& fn) {
+cudaError_t with_family(int fam, int mode, Fn&& fn) {
   switch (fam) {
-    case 0: return fn(std::integral_constant<int, 0>{});
-    case 1: return fn(std::integral_constant<int, 1>{});
-    case 2: return fn(std::integral_constant<int, 2>{});
-    case 3: return fn(std::integral_constant<int, 3>{});
-    case 4: return fn(std::integral_constant<int, 4>{});
+    case 0: return with_mode<0>(mode, fn);
+    case 1: return with_mode<1>(mode, fn);
+    case 2: return with_mode<2>(mode, fn);
+    case 3: return with_mode<3>(mode, fn);
+    case 4: return with_mode<4>(mode, fn);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -116,7 +147,11 @@ struct pcg_batch {
   int* d_order = nullptr;
   int* d_next = nullptr;
   BatchOut* d_out = nullptr;
-  double* d_vec = nullptr;        // b, x, r, w0, w1, z, s, p
+  double* d_vec = nullptr;        // b, x, r, w0, w1, z, s, p (+ u, q, t, m0, m1, u64, dinv, dinv32)
+  bool jacobi = false;
+  int precision = PCG_FP64;
+  double eta = 1.0 / 1024.0;      // inner tolerance factor of the mixed-precision restarts
+  int max_restarts = 200;
   double* h_stage = nullptr;      // pinned staging of b / x (total doubles)
   cudaStream_t stream = nullptr;
   int csize = 8;
@@ -155,22 +190,35 @@ BatchVecs vecs_of(pcg_batch* B) {
   V.z = base + 5 * t;
   V.s = base + 6 * t;
   V.p = base + 7 * t;
+  V.u = V.q = V.t = V.m0 = V.m1 = V.u64 = nullptr;
+  V.dinv = V.dinv32 = nullptr;
+  if (B->jacobi) {
+    V.u = base + 8 * t;
+    V.q = base + 9 * t;
+    V.t = base + 10 * t;
+    V.m0 = base + 11 * t;
+    V.m1 = base + 12 * t;
+    V.u64 = base + 13 * t;
+    V.dinv = base + 14 * t;
+    V.dinv32 = base + 15 * t;
+  }
   return V;
 }
 
-int max_clusters_of(int fam, int csize) {
-  switch (fam) {
-    case 0: return max_clusters<0>(csize);
-    case 1: return max_clusters<1>(csize);
-    case 2: return max_clusters<2>(csize);
-    case 3: return max_clusters<3>(csize);
-    case 4: return max_clusters<4>(csize);
-    default: return 0;
-  }
+int mode_of(const pcg_batch* B) { return (B->precision == PCG_MIXED_IR ? BM_MX : BM_FP64) + (B->jacobi ? 1 : 0); }
+
+int max_clusters_of(int fam, int mode, int csize) {
+  int n = 0;
+  with_family(fam, mode, [&](auto F, auto M) {
+    n = max_clusters<decltype(F)::value, decltype(M)::value>(csize);
+    return cudaSuccess;
+  });
+  return n;
 }
 
 pcg_status run_batch(pcg_batch* B, int csize, double tol, int maxit) {
-  const int maxc = max_clusters_of(B->family, csize);
+  const int mode = mode_of(B);
+  const int maxc = max_clusters_of(B->family, mode, csize);
   if (maxc <= 0) {
     cudaGetLastError();
     return PCG_ECUDA;
@@ -179,9 +227,14 @@ pcg_status run_batch(pcg_batch* B, int csize, double tol, int maxit) {
   if (cudaMemsetAsync(B->d_next, 0, sizeof(int), B->stream) != cudaSuccess) return PCG_ECUDA;
   const BatchVecs V = vecs_of(B);
   if (cudaEventRecord(B->e0, B->stream) != cudaSuccess) return PCG_ECUDA;
-  const cudaError_t e = with_family(B->family, [&](auto F) {
-    return launch_batch<decltype(F)::value>(clusters, csize, B->stream, B->d_sys, B->d_order, B->nsys, B->d_next, V,
-                                            B->d_out, tol, maxit);
+  BatchParams prm;
+  prm.tol = tol;
+  prm.maxit = maxit;
+  prm.eta = B->eta;
+  prm.max_restarts = B->max_restarts;
+  const cudaError_t e = with_family(B->family, mode, [&](auto F, auto M) {
+    return launch_batch<decltype(F)::value, decltype(M)::value>(clusters, csize, B->stream, B->d_sys, B->d_order,
+                                                                B->nsys, B->d_next, V, B->d_out, prm);
   });
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -202,7 +255,7 @@ extern "C" {
 pcg_status pcg_batch_create(const pcg_matrix* systems, int32_t nsys, uint32_t flags, pcg_batch** out) {
   if (!out) return PCG_EINVAL;
   *out = nullptr;
-  if (!systems || nsys < 1 || flags != 0) return PCG_EINVAL;
+  if (!systems || nsys < 1 || (flags & ~PCG_JACOBI)) return PCG_EINVAL;
   const int fam = family_of(systems[0]);
   if (fam < 0) return PCG_EINVAL;
   pcg_batch* B = new (std::nothrow) pcg_batch();
@@ -213,6 +266,7 @@ pcg_status pcg_batch_create(const pcg_matrix* systems, int32_t nsys, uint32_t fl
   };
   B->family = fam;
   B->nsys = nsys;
+  B->jacobi = (flags & PCG_JACOBI) != 0;
   if (cudaGetDevice(&B->device) != cudaSuccess) return bail(PCG_ECUDA);
   long long total = 0;
   for (int k = 0; k < nsys; ++k) {
@@ -254,11 +308,18 @@ pcg_status pcg_batch_create(const pcg_matrix* systems, int32_t nsys, uint32_t fl
       *dst = p;
       return PCG_OK;
     };
+    // binary32 copy (round to nearest) for the mixed-precision inner iteration
+    auto put32 = [&](const double* src, long long count, const float** dst) -> pcg_status {
+      std::vector<float> f(count > 0 ? count : 1);
+      for (long long i = 0; i < count; ++i) f[i] = (float)src[i];
+      return put(f.data(), f.size() * sizeof(float), (const void**)dst);
+    };
     pcg_status s = PCG_OK;
     if (fam == 4) {
       s = put(A.row_ptr, (A.n + 1) * sizeof(int), (const void**)&d.row_ptr);
       if (s == PCG_OK) s = put(A.col, A.nnz * sizeof(int), (const void**)&d.col);
       if (s == PCG_OK) s = put(A.val, A.nnz * sizeof(double), (const void**)&d.val);
+      if (s == PCG_OK) s = put32(A.val, A.nnz, &d.val32);
     } else {
       d.nx = (int)A.nx;
       d.ny = (int)A.ny;
@@ -268,6 +329,10 @@ pcg_status pcg_batch_create(const pcg_matrix* systems, int32_t nsys, uint32_t fl
         if (s == PCG_OK) s = put(A.ax, d.n * sizeof(double), (const void**)&d.ax);
         if (s == PCG_OK) s = put(A.ay, d.n * sizeof(double), (const void**)&d.ay);
         if (s == PCG_OK && fam == 3) s = put(A.az, d.n * sizeof(double), (const void**)&d.az);
+        if (s == PCG_OK) s = put32(A.diag, d.n, &d.diag32);
+        if (s == PCG_OK) s = put32(A.ax, d.n, &d.ax32);
+        if (s == PCG_OK) s = put32(A.ay, d.n, &d.ay32);
+        if (s == PCG_OK && fam == 3) s = put32(A.az, d.n, &d.az32);
       }
     }
     if (s != PCG_OK) return bail(s);
@@ -282,10 +347,46 @@ pcg_status pcg_batch_create(const pcg_matrix* systems, int32_t nsys, uint32_t fl
   B->d_next = (int*)p;
   if (balloc(B, &p, nsys * sizeof(BatchOut)) != PCG_OK) return bail(PCG_ENOMEM);
   B->d_out = (BatchOut*)p;
-  if (balloc(B, &p, 8 * (size_t)total * sizeof(double)) != PCG_OK) return bail(PCG_ENOMEM);
+  const int nvec = B->jacobi ? 16 : 8;
+  if (balloc(B, &p, nvec * (size_t)total * sizeof(double)) != PCG_OK) return bail(PCG_ENOMEM);
   B->d_vec = (double*)p;
   if (cudaMallocHost(&p, (size_t)total * sizeof(double)) != cudaSuccess) return bail(PCG_ENOMEM);
   B->h_stage = (double*)p;
+  if (B->jacobi) {
+    // D^{-1} of every system (binary64, and rounded to binary32 in a binary32 slot)
+    const BatchVecs V = vecs_of(B);
+    std::fill(B->h_stage, B->h_stage + total, 0.0);
+    for (int k = 0; k < nsys; ++k) {
+      const pcg_matrix& A = systems[k];
+      double* dk = B->h_stage + B->off[k];
+      const int n = B->n[k];
+      for (int i = 0; i < n; ++i) {
+        double dg;
+        if (fam == 4) {
+          dg = 0.0;
+          for (int32_t e = A.row_ptr[i]; e < A.row_ptr[i + 1]; ++e)
+            if (A.col[e] == i) dg += A.val[e];
+        } else if (fam == 1 || fam == 3) {
+          dg = A.diag[i];
+        } else {
+          dg = fam == 2 ? 6.0 : 4.0;
+        }
+        if (!(dg > 0.0) || !isfinite(dg)) return bail(PCG_EINVAL);   // Jacobi needs a positive diagonal
+        dk[i] = 1.0 / dg;
+      }
+    }
+    if (cudaMemcpy((double*)V.dinv, B->h_stage, (size_t)total * sizeof(double), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      return bail(PCG_ECUDA);
+    std::vector<double> slot32(total, 0.0);
+    for (int k = 0; k < nsys; ++k) {
+      float* f = reinterpret_cast<float*>(slot32.data() + B->off[k]);
+      for (int i = 0; i < B->n[k]; ++i) f[i] = (float)B->h_stage[B->off[k] + i];
+    }
+    if (cudaMemcpy((double*)V.dinv32, slot32.data(), (size_t)total * sizeof(double), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      return bail(PCG_ECUDA);
+  }
   // largest systems first: the queue then balances the clusters' work
   std::vector<int> order(nsys);
   std::iota(order.begin(), order.end(), 0);
@@ -383,6 +484,27 @@ pcg_status pcg_batch_autotune(pcg_batch* B, const double* const* b, const double
   B->tuned = 1;
   if (cluster_out) *cluster_out = best_c;
   return PCG_OK;
+}
+
+pcg_status pcg_batch_set_precision(pcg_batch* B, int32_t precision) {
+  if (!B || (precision != PCG_FP64 && precision != PCG_MIXED_IR)) return PCG_EINVAL;
+  B->precision = precision;
+  return PCG_OK;
+}
+
+pcg_status pcg_batch_set_param(pcg_batch* B, int32_t param, double value) {
+  if (!B) return PCG_EINVAL;
+  if (param == PCG_PARAM_MIXED_ETA) {
+    if (!(value > 0.0 && value < 1.0)) return PCG_EINVAL;
+    B->eta = value;
+    return PCG_OK;
+  }
+  if (param == PCG_PARAM_MAX_RESTARTS) {
+    if (!(value >= 1.0 && value <= 1e9)) return PCG_EINVAL;
+    B->max_restarts = (int)value;
+    return PCG_OK;
+  }
+  return PCG_EINVAL;
 }
 
 pcg_status pcg_batch_set_cluster(pcg_batch* B, int32_t cluster_size) {

@@ -1,0 +1,406 @@
+// Per-cluster solves beyond the binary64, M = I case of pcg_cluster_solve.cuh, shared by
+// the batched launch and the serving kernel:
+//   cluster_solve_jac<F>      Algorithm 3 with M^{-1} = D^{-1}, binary64
+//   cluster_solve_mx<F, JAC>  mixed precision with restarts (iterative refinement),
+//                             M = I or M^{-1} = D^{-1}
+// The arithmetic per unknown follows the single-system kernels (pcg_general.cuh,
+// pcg_mixed.cuh, pcg_mixed_jacobi.cuh); the reductions are the cluster's (cluster_sum).
+#pragma once
+#include "pcg_cluster_solve.cuh"
+#include "pcg_mixed.cuh"
+
+namespace pcgk {
+
+template <int F>
+struct FamilyOp32;
+template <>
+struct FamilyOp32<0> {
+  using T = StencilOp32<2, false, 1>;
+};
+template <>
+struct FamilyOp32<1> {
+  using T = StencilOp32<2, true, 1>;
+};
+template <>
+struct FamilyOp32<2> {
+  using T = StencilOp32<3, false, 1>;
+};
+template <>
+struct FamilyOp32<3> {
+  using T = StencilOp32<3, true, 1>;
+};
+template <>
+struct FamilyOp32<4> {
+  using T = CsrOp32;
+};
+
+template <int F>
+__device__ __forceinline__ typename FamilyOp32<F>::T make_op32(const BatchSys& d) {
+  typename FamilyOp32<F>::T o;
+  if constexpr (F == 4) {
+    o.n = d.n;
+    o.row_ptr = d.row_ptr;
+    o.col = d.col;
+    o.val = d.val32;
+  } else {
+    o.n = d.n;
+    o.nx = d.nx;
+    o.ny = d.ny;
+    o.nz = d.nz;
+    o.nxny = d.nx * d.ny;
+    o.diag = d.diag32;
+    o.ax = d.ax32;
+    o.ay = d.ay32;
+    o.az = d.az32;
+  }
+  return o;
+}
+
+// ||b - A x|| in binary64 over the cluster.
+template <int F>
+__device__ __forceinline__ double cluster_true_res(cg::cluster_group& cl, double (*part)[4], int& slot,
+                                                   const typename FamilyOp<F>::T& op, const double* b,
+                                                   const double* x, unsigned nc, int first,
+                                                   const typename FamilyOp<F>::T::Step& stp) {
+  double tr = 0.0;
+  for (auto q = op.cursor(first); q.c0 < nc; op.advance(q, stp)) {
+    double xc[1], ax[1];
+    op.apply(x, q, xc, ax);
+    const double e = b[q.c0] - ax[0];
+    tr = fma(e, e, tr);
+  }
+  double t[1] = {tr}, o[1];
+  cluster_sum<1>(cl, t, part, slot, o);
+  slot ^= 1;
+  return sqrt(o[0]);
+}
+
+// Algorithm 3 with M^{-1} = D^{-1} (binary64, x_0 = 0) for one system on the calling cluster.
+template <int F>
+__device__ __forceinline__ void cluster_solve_jac(cg::cluster_group& cl, double (*part)[4], int& slot,
+                                                  const BatchSys& d, const BatchVecs& V, double tol, int maxit,
+                                                  BatchOut& res) {
+  using Op = typename FamilyOp<F>::T;
+  const unsigned rank = cl.block_rank(), C = cl.num_blocks();
+  const Op op = make_op<F>(d);
+  const double sigma = d.sigma;
+  const long long off = d.off;
+  const double* b = V.b + off;
+  const double* dinv = V.dinv + off;
+  double *x = V.x + off, *r = V.r + off, *w0 = V.w0 + off, *w1 = V.w1 + off, *z = V.z + off, *s = V.s + off,
+         *p = V.p + off, *u = V.u + off, *qv = V.q + off, *t = V.t + off, *m0 = V.m0 + off, *m1 = V.m1 + off;
+  const unsigned nc = (unsigned)d.n;
+  const auto stp = op.step(C * kBlock);
+  const int first = (int)(rank * kBlock + threadIdx.x);
+
+  // r_0 = b (x_0 = 0), u_0 = D^{-1} r_0, ||b||
+  double bb = 0.0;
+  for (unsigned i = first; i < nc; i += C * kBlock) {
+    const double bv = b[i];
+    r[i] = bv;
+    u[i] = dinv[i] * bv;
+    x[i] = 0.0;
+    bb = fma(bv, bv, bb);
+  }
+  double t1[1] = {bb}, o1[1];
+  cluster_sum<1>(cl, t1, part, slot, o1);
+  slot ^= 1;
+  const double bnorm = sqrt(o1[0]);
+  const double tol_abs = tol * bnorm;
+
+  // w_0 = A u_0 - sigma r_0, m_0 = D^{-1} w_0; z = q = s = t = p = 0
+  double ru = 0.0, wu = 0.0, rr = 0.0;
+  for (auto q = op.cursor(first); q.c0 < nc; op.advance(q, stp)) {
+    const unsigned c = q.c0;
+    double uc[1], au[1];
+    op.apply(u, q, uc, au);
+    const double rc = r[c];
+    const double wv = fma(-sigma, rc, au[0]);
+    w0[c] = wv;
+    m0[c] = dinv[c] * wv;
+    z[c] = 0.0;
+    qv[c] = 0.0;
+    s[c] = 0.0;
+    t[c] = 0.0;
+    p[c] = 0.0;
+    ru = fma(rc, uc[0], ru);
+    wu = fma(wv, uc[0], wu);
+    rr = fma(rc, rc, rr);
+  }
+  double t2[3] = {ru, wu, rr}, o2[3];
+  cluster_sum<3>(cl, t2, part, slot, o2);
+  slot ^= 1;
+  double gamma = o2[0], delta = o2[1] + sigma * o2[0];
+  int status = ST_RUNNING, it = 0;
+  double alpha = 0.0, beta = 0.0;
+  if (tol_abs > 0.0 && sqrt(o2[2]) <= tol_abs) {
+    status = ST_CONVERGED;
+  } else if (maxit <= 0) {
+    status = ST_MAXIT;
+  } else if (gamma == 0.0) {
+    status = ST_CONVERGED;
+  } else if (!(delta > 0.0) || !isfinite(delta)) {
+    status = ST_BREAKDOWN;
+  } else {
+    alpha = gamma / delta;
+  }
+  while (status == ST_RUNNING) {
+    const double asg = alpha * sigma;
+    const double* __restrict__ w = (it & 1) ? w1 : w0;
+    double* __restrict__ wn = (it & 1) ? w0 : w1;
+    const double* __restrict__ m = (it & 1) ? m1 : m0;
+    double* __restrict__ mn = (it & 1) ? m0 : m1;
+    ru = wu = rr = 0.0;
+    for (auto q = op.cursor(first); q.c0 < nc; op.advance(q, stp)) {
+      const unsigned c = q.c0;
+      double mc[1], nv[1];
+      op.apply(m, q, mc, nv);
+      const double wc = w[c], rc = r[c], uc = u[c];
+      const double tt = fma(beta, t[c], rc);
+      const double ss = fma(beta, s[c], wc);
+      const double zz = fma(beta, z[c], nv[0]);
+      const double rn = fma(-alpha, ss, fma(-asg, tt, rc));
+      const double wv = fma(-alpha, zz, wc);
+      const double pp = fma(beta, p[c], uc);
+      const double qq = fma(beta, qv[c], mc[0]);
+      x[c] = fma(alpha, pp, x[c]);
+      const double un = fma(-alpha, qq, fma(-asg, pp, uc));
+      t[c] = tt;
+      s[c] = ss;
+      z[c] = zz;
+      p[c] = pp;
+      qv[c] = qq;
+      r[c] = rn;
+      u[c] = un;
+      wn[c] = wv;
+      mn[c] = dinv[c] * wv;
+      ru = fma(rn, un, ru);
+      wu = fma(wv, un, wu);
+      rr = fma(rn, rn, rr);
+    }
+    double tv[3] = {ru, wu, rr}, to[3];
+    cluster_sum<3>(cl, tv, part, slot, to);
+    slot ^= 1;
+    ++it;
+    const double gn = to[0], dn = to[1] + sigma * to[0];
+    if (tol_abs > 0.0 && sqrt(to[2]) <= tol_abs) {
+      status = ST_CONVERGED;
+    } else if (it >= maxit) {
+      status = ST_MAXIT;
+    } else if (gn == 0.0) {
+      status = ST_CONVERGED;
+    } else {
+      const double bt = gn / gamma;
+      const double den = dn / gn - bt / alpha;
+      if (!(den > 0.0) || !isfinite(den)) {
+        status = ST_BREAKDOWN;
+      } else {
+        alpha = 1.0 / den;
+        beta = bt;
+      }
+    }
+    gamma = gn;
+  }
+  res.iters = it;
+  res.status = status;
+  res.bnorm = bnorm;
+  res.true_res = cluster_true_res<F>(cl, part, slot, op, b, x, nc, first, stp);
+}
+
+// Mixed precision with restarts (M = I, or M^{-1} = D^{-1} when JAC), x_0 = 0.
+// Storage as in the single-system kernels: x, r binary64; the auxiliary vectors binary32
+// (M = I: w, z, s, p; JAC: u, w, m, z, q, s, t, p).  A restart recomputes r = b - A x in
+// binary64 and restarts Algorithm 3 from x once the inner residual ||r_i|| reaches
+// max(eta * true residual, tol ||b|| / 2); the solve ends when the true residual reaches
+// tol ||b||, when a restart does not lower it (reported as maxit), or at maxit.
+template <int F, bool JAC>
+__device__ __forceinline__ void cluster_solve_mx(cg::cluster_group& cl, double (*part)[4], int& slot,
+                                                 const BatchSys& d, const BatchVecs& V, double tol, int maxit,
+                                                 double eta, int max_restarts, BatchOut& res) {
+  using Op = typename FamilyOp<F>::T;
+  using Op32 = typename FamilyOp32<F>::T;
+  const unsigned rank = cl.block_rank(), C = cl.num_blocks();
+  const Op op = make_op<F>(d);
+  const Op32 op32 = make_op32<F>(d);
+  const double sigma = d.sigma;
+  const long long off = d.off;
+  const double* b = V.b + off;
+  double *x = V.x + off, *r = V.r + off;
+  float* const wb0 = reinterpret_cast<float*>(V.w0 + off);
+  float* const wb1 = reinterpret_cast<float*>(V.w1 + off);
+  float* const zf = reinterpret_cast<float*>(V.z + off);
+  float* const sf = reinterpret_cast<float*>(V.s + off);
+  float* const pf = reinterpret_cast<float*>(V.p + off);
+  float *uf = nullptr, *qf = nullptr, *tf = nullptr, *mb0 = nullptr, *mb1 = nullptr;
+  const double* dinv = nullptr;
+  const float* d32 = nullptr;
+  double* u64 = nullptr;
+  if constexpr (JAC) {
+    uf = reinterpret_cast<float*>(V.u + off);
+    qf = reinterpret_cast<float*>(V.q + off);
+    tf = reinterpret_cast<float*>(V.t + off);
+    mb0 = reinterpret_cast<float*>(V.m0 + off);
+    mb1 = reinterpret_cast<float*>(V.m1 + off);
+    dinv = V.dinv + off;
+    d32 = reinterpret_cast<const float*>(V.dinv32 + off);
+    u64 = V.u64 + off;
+  }
+  const unsigned nc = (unsigned)d.n;
+  const auto stp = op.step(C * kBlock);
+  const auto stp32 = op32.step(C * kBlock);
+  const int first = (int)(rank * kBlock + threadIdx.x);
+
+  double bb = 0.0;
+  for (unsigned i = first; i < nc; i += C * kBlock) {
+    const double bv = b[i];
+    x[i] = 0.0;
+    bb = fma(bv, bv, bb);
+  }
+  double t1[1] = {bb}, o1[1];
+  cluster_sum<1>(cl, t1, part, slot, o1);
+  slot ^= 1;
+  const double bnorm = sqrt(o1[0]);
+  const double tol_abs = tol * bnorm;
+  int status = ST_RUNNING, it = 0, restarts = 0, par = 0;
+  double rprev = INFINITY, true_res = 0.0;
+  for (;;) {
+    // restart, part 1: r = b - A x (binary64); JAC: u = D^{-1} r rounded to binary32
+    double rr = 0.0;
+    for (auto q = op.cursor(first); q.c0 < nc; op.advance(q, stp)) {
+      const unsigned c = q.c0;
+      double xc[1], ax[1];
+      op.apply(x, q, xc, ax);
+      const double rv = b[c] - ax[0];
+      r[c] = rv;
+      rr = fma(rv, rv, rr);
+      if constexpr (JAC) {
+        const float u32 = f32_of(dinv[c] * rv);
+        uf[c] = u32;
+        u64[c] = f64_of(u32);
+      }
+    }
+    double t2[1] = {rr}, o2[1];
+    cluster_sum<1>(cl, t2, part, slot, o2);
+    slot ^= 1;
+    const double rt = sqrt(o2[0]);
+    true_res = rt;
+    if (rt <= tol_abs || o2[0] == 0.0) {
+      status = ST_CONVERGED;
+      break;
+    }
+    if ((restarts > 0 && !(rt < rprev)) || restarts >= max_restarts || it >= maxit) {
+      status = ST_MAXIT;
+      break;
+    }
+    const double inner = fmax(eta * rt, 0.5 * tol_abs);
+    rprev = rt;
+    ++restarts;
+    // restart, part 2: w_0 = A u_0 - sigma r (binary64 operator), auxiliary vectors zero
+    double g = 0.0, o = 0.0, rr0 = 0.0;
+    for (auto q = op.cursor(first); q.c0 < nc; op.advance(q, stp)) {
+      const unsigned c = q.c0;
+      double uc[1], au[1];
+      op.apply(JAC ? u64 : r, q, uc, au);
+      const double rv = r[c];
+      const float w32 = f32_of(fma(-sigma, rv, au[0]));
+      (par ? wb1 : wb0)[c] = w32;
+      zf[c] = 0.f;
+      sf[c] = 0.f;
+      pf[c] = 0.f;
+      if constexpr (JAC) {
+        (par ? mb1 : mb0)[c] = d32[c] * w32;
+        qf[c] = 0.f;
+        tf[c] = 0.f;
+      }
+      g = fma(rv, uc[0], g);
+      o = fma(f64_of(w32), uc[0], o);
+      rr0 = fma(rv, rv, rr0);
+    }
+    double t3[3] = {g, o, rr0}, o3[3];
+    cluster_sum<3>(cl, t3, part, slot, o3);
+    slot ^= 1;
+    double gamma = o3[0], delta = o3[1] + sigma * o3[0];
+    if (!(delta > 0.0) || !isfinite(delta)) {
+      status = ST_BREAKDOWN;
+      break;
+    }
+    double alpha = gamma / delta, beta = 0.0;
+    // inner iterations
+    for (;;) {
+      const double asg = alpha * sigma;
+      const float alpha32 = f32_of(alpha), beta32 = f32_of(beta), asg32 = f32_of(asg);
+      const float* __restrict__ w = par ? wb1 : wb0;
+      float* __restrict__ wn = par ? wb0 : wb1;
+      const float* __restrict__ m = par ? mb1 : mb0;
+      float* __restrict__ mn = par ? mb0 : mb1;
+      double ru = 0.0, wu = 0.0, rn2 = 0.0;
+      for (auto q = op32.cursor(first); q.c0 < nc; op32.advance(q, stp32)) {
+        const unsigned c = q.c0;
+        float mc[1], nv[1];
+        op32.apply(JAC ? m : w, q, mc, nv);
+        const float wc = JAC ? w[c] : mc[0];
+        const double rc = r[c];
+        const float zz = fmaf(beta32, zf[c], nv[0]);
+        const float ss = fmaf(beta32, sf[c], wc);
+        zf[c] = zz;
+        sf[c] = ss;
+        const float w1 = fmaf(-alpha32, zz, wc);
+        wn[c] = w1;
+        if constexpr (JAC) {
+          const float uc = uf[c];
+          const float tt = fmaf(beta32, tf[c], f32_of(rc));
+          const float pp = fmaf(beta32, pf[c], uc);
+          const float qq = fmaf(beta32, qf[c], mc[0]);
+          x[c] = fma(alpha, f64_of(pp), x[c]);
+          const double rn = fma(-alpha, f64_of(ss), fma(-asg, f64_of(tt), rc));
+          const float un = fmaf(-alpha32, qq, fmaf(-asg32, pp, uc));
+          tf[c] = tt;
+          pf[c] = pp;
+          qf[c] = qq;
+          uf[c] = un;
+          r[c] = rn;
+          mn[c] = d32[c] * w1;
+          const double ud = f64_of(un);
+          ru = fma(rn, ud, ru);
+          wu = fma(f64_of(w1), ud, wu);
+          rn2 = fma(rn, rn, rn2);
+        } else {
+          const float pp = fmaf(beta32, pf[c], f32_of(rc));
+          pf[c] = pp;
+          const double pd = f64_of(pp);
+          x[c] = fma(alpha, pd, x[c]);
+          const double rn = fma(-alpha, f64_of(ss), fma(-asg, pd, rc));
+          r[c] = rn;
+          ru = fma(rn, rn, ru);
+          wu = fma(f64_of(w1), rn, wu);
+          rn2 = ru;
+        }
+      }
+      double t4[3] = {ru, wu, rn2}, o4[3];
+      cluster_sum<3>(cl, t4, part, slot, o4);
+      slot ^= 1;
+      ++it;
+      par ^= 1;
+      if (it >= maxit) break;
+      const double gn = o4[0], dn = o4[1] + sigma * o4[0];
+      if (sqrt(o4[2]) <= inner || gn == 0.0) break;
+      const double bt = gn / gamma;
+      const double den = dn / gn - bt / alpha;
+      if (!(den > 0.0) || !isfinite(den)) break;
+      alpha = 1.0 / den;
+      beta = bt;
+      gamma = gn;
+    }
+    if (it >= maxit) {
+      true_res = cluster_true_res<F>(cl, part, slot, op, b, x, nc, first, stp);
+      status = true_res <= tol_abs ? ST_CONVERGED : ST_MAXIT;
+      break;
+    }
+  }
+  res.iters = it;
+  res.status = status;
+  res.bnorm = bnorm;
+  res.true_res = true_res;
+}
+
+}  // namespace pcgk

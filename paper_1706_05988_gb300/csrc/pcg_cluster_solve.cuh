@@ -25,6 +25,7 @@ struct BatchSys {
   const double *diag, *ax, *ay, *az;   // variable coefficients (stencils)
   const int *row_ptr, *col;            // CSR
   const double* val;
+  const float *diag32, *ax32, *ay32, *az32, *val32;   // binary32 copies (mixed precision)
   long long off;                       // offset of the system's unknowns in every batch vector
   double sigma;
 };
@@ -35,9 +36,14 @@ struct BatchOut {
   double bnorm, true_res;
 };
 
+// Every vector holds the batch's systems at their offsets.  Mixed precision keeps the
+// binary32 vectors in the first half of a system's binary64-sized slot.
 struct BatchVecs {
   const double* b;
   double *x, *r, *w0, *w1, *z, *s, *p;
+  double *u, *q, *t, *m0, *m1, *u64;   // Jacobi only (u64: binary64 scratch of a mixed restart)
+  const double* dinv;                  // Jacobi: D^{-1}
+  const double* dinv32;                // Jacobi, mixed: D^{-1} rounded to binary32 (binary32 slot)
 };
 
 

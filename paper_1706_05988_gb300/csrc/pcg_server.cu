@@ -25,7 +25,7 @@
 
 #define PCG_KERNELS_IMPL
 #include "../../include/pcg.h"
-#include "pcg_cluster_solve.cuh"
+#include "pcg_cluster_mixed.cuh"
 
 namespace pcgk {
 namespace {
@@ -34,7 +34,8 @@ constexpr unsigned long long kIdleNs = 20ull * 1000 * 1000;   // an idle kernel 
 
 struct WorkItem {
   int family, maxit;
-  double tol;
+  int mode, max_restarts;    // mode: 0 binary64, 1 binary64 + Jacobi, 2 mixed, 3 mixed + Jacobi
+  double tol, eta;
   BatchSys sys;        // operator (device pointers), sigma; off = 0
   BatchVecs vec;       // the request's vectors in the arena
 };
@@ -56,8 +57,17 @@ __device__ __forceinline__ unsigned long long now_ns() {
 
 template <int F>
 __device__ __forceinline__ void solve_item(cg::cluster_group& cl, double (*part)[4], int& slot, const WorkItem& w,
-                                           BatchOut& res) {
-  cluster_solve<F>(cl, part, slot, w.sys, w.vec, w.tol, w.maxit, res);
+                                        BatchOut& res) {
+  switch (w.mode) {
+    case 1: cluster_solve_jac<F>(cl, part, slot, w.sys, w.vec, w.tol, w.maxit, res); break;
+    case 2:
+      cluster_solve_mx<F, false>(cl, part, slot, w.sys, w.vec, w.tol, w.maxit, w.eta, w.max_restarts, res);
+      break;
+    case 3:
+      cluster_solve_mx<F, true>(cl, part, slot, w.sys, w.vec, w.tol, w.maxit, w.eta, w.max_restarts, res);
+      break;
+    default: cluster_solve<F>(cl, part, slot, w.sys, w.vec, w.tol, w.maxit, res); break;
+  }
 }
 
 // Copy of a work item from mapped host memory, bypassing the caches (a ring slot is reused).
@@ -68,7 +78,7 @@ __device__ __forceinline__ void load_item(const WorkItem* src, WorkItem* dst) {
   for (unsigned i = 0; i < sizeof(WorkItem) / 8; ++i) b[i] = __ldcv(a + i);
 }
 
-__global__ void __launch_bounds__(kBlock) k_server(ServerShared* sh, const WorkItem* items, BatchOut* results,
+__global__ void __launch_bounds__(kBlock, 2) k_server(ServerShared* sh, const WorkItem* items, BatchOut* results,
                                                    unsigned int* done, unsigned int cap, unsigned int* claim,
                                                    unsigned int* left) {
   cg::cluster_group cl = cg::this_cluster();
@@ -167,6 +177,8 @@ struct Request {
   std::vector<double> val, diag, ax, ay, az;
   double tol, sigma;
   int method, maxit, family;
+  int mode;                         // 0 binary64, 1 + Jacobi, 2 mixed, 3 mixed + Jacobi
+  std::vector<double> dinv;         // Jacobi: D^{-1}
   long long n, nnz;
   size_t bytes;                     // arena bytes
   size_t arena_off = 0;
@@ -240,9 +252,10 @@ size_t pad256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 size_t request_bytes(const Request& R) {
   const size_t n = (size_t)R.n, npad = (n + 31) & ~(size_t)31;
-  size_t b = 8 * npad * sizeof(double);                       // b, x, r, w0, w1, z, s, p
-  if (R.family == 4) b += pad256((n + 1) * 4) + pad256(R.nnz * 4) + pad256(R.nnz * 8);
-  if (R.family == 1 || R.family == 3) b += 4 * pad256(n * 8);
+  const bool jac = R.mode & 1, mixed = R.mode >= 2;
+  size_t b = (jac ? 16 : 8) * npad * sizeof(double);   // b, x, r, w0, w1, z, s, p (+ Jacobi vectors)
+  if (R.family == 4) b += pad256((n + 1) * 4) + pad256(R.nnz * 4) + pad256(R.nnz * 8) + (mixed ? pad256(R.nnz * 4) : 0);
+  if (R.family == 1 || R.family == 3) b += 4 * pad256(n * 8) + (mixed ? 4 * pad256(n * 4) : 0);
   return b;
 }
 
@@ -257,8 +270,20 @@ int family_of(const pcg_matrix& A) {
 pcg_status upload(pcg_server* S, Request* R, WorkItem* w) {
   char* base = S->arena + R->arena_off;
   const size_t n = (size_t)R->n, npad = (n + 31) & ~(size_t)31;
+  const bool jac = R->mode & 1, mixed = R->mode >= 2;
   double* v = (double*)base;
-  size_t at = 8 * npad * sizeof(double);
+  size_t at = (jac ? 16 : 8) * npad * sizeof(double);
+  std::deque<std::vector<float>> stage;   // binary32 copies, alive until the final synchronisation
+  auto put32 = [&](const double* src, size_t count) -> const float* {
+    stage.emplace_back(count ? count : 1);
+    std::vector<float>& f = stage.back();
+    for (size_t i = 0; i < count; ++i) f[i] = (float)src[i];
+    const void* dst = base + at;
+    at += pad256(count * 4);
+    if (count && cudaMemcpyAsync((void*)dst, f.data(), count * 4, cudaMemcpyHostToDevice, S->cstream) != cudaSuccess)
+      return nullptr;
+    return (const float*)dst;
+  };
   auto put = [&](const void* src, size_t bytes) -> void* {
     void* dst = base + at;
     at += pad256(bytes);
@@ -275,6 +300,7 @@ pcg_status upload(pcg_server* S, Request* R, WorkItem* w) {
     d.col = (const int*)put(R->col.data(), R->nnz * 4);
     d.val = (const double*)put(R->val.data(), R->nnz * 8);
     if (!d.row_ptr || !d.col || !d.val) return PCG_ECUDA;
+    if (mixed && !(d.val32 = put32(R->val.data(), R->nnz))) return PCG_ECUDA;
   } else {
     d.nx = (int)R->A.nx;
     d.ny = (int)R->A.ny;
@@ -284,12 +310,31 @@ pcg_status upload(pcg_server* S, Request* R, WorkItem* w) {
       d.ax = (const double*)put(R->ax.data(), n * 8);
       d.ay = (const double*)put(R->ay.data(), n * 8);
       d.az = R->family == 3 ? (const double*)put(R->az.data(), n * 8) : nullptr;
+      if (mixed) {
+        d.diag32 = put32(R->diag.data(), n);
+        d.ax32 = put32(R->ax.data(), n);
+        d.ay32 = put32(R->ay.data(), n);
+        d.az32 = R->family == 3 ? put32(R->az.data(), n) : nullptr;
+        if (!d.diag32 || !d.ax32 || !d.ay32 || (R->family == 3 && !d.az32)) return PCG_ECUDA;
+      }
     }
   }
   if (cudaMemcpyAsync(v, R->b.data(), n * 8, cudaMemcpyHostToDevice, S->cstream) != cudaSuccess) return PCG_ECUDA;
+  if (jac) {
+    if (cudaMemcpyAsync(v + 14 * npad, R->dinv.data(), n * 8, cudaMemcpyHostToDevice, S->cstream) != cudaSuccess)
+      return PCG_ECUDA;
+    stage.emplace_back(n);
+    std::vector<float>& f = stage.back();
+    for (size_t i = 0; i < n; ++i) f[i] = (float)R->dinv[i];
+    if (cudaMemcpyAsync(v + 15 * npad, f.data(), n * 4, cudaMemcpyHostToDevice, S->cstream) != cudaSuccess)
+      return PCG_ECUDA;
+  }
   if (cudaStreamSynchronize(S->cstream) != cudaSuccess) return PCG_ECUDA;
   w->family = R->family;
   w->maxit = R->maxit;
+  w->mode = R->mode;
+  w->max_restarts = 200;
+  w->eta = 1.0 / 1024.0;
   w->tol = R->tol;
   w->sys = d;
   w->vec.b = v;
@@ -300,6 +345,18 @@ pcg_status upload(pcg_server* S, Request* R, WorkItem* w) {
   w->vec.z = v + 5 * npad;
   w->vec.s = v + 6 * npad;
   w->vec.p = v + 7 * npad;
+  w->vec.u = w->vec.q = w->vec.t = w->vec.m0 = w->vec.m1 = w->vec.u64 = nullptr;
+  w->vec.dinv = w->vec.dinv32 = nullptr;
+  if (jac) {
+    w->vec.u = v + 8 * npad;
+    w->vec.q = v + 9 * npad;
+    w->vec.t = v + 10 * npad;
+    w->vec.m0 = v + 11 * npad;
+    w->vec.m1 = v + 12 * npad;
+    w->vec.u64 = v + 13 * npad;
+    w->vec.dinv = v + 14 * npad;
+    w->vec.dinv32 = v + 15 * npad;
+  }
   return PCG_OK;
 }
 
@@ -367,6 +424,7 @@ pcg_status pump(pcg_server* S) {
     R->ay.clear(); R->ay.shrink_to_fit();
     R->az.clear(); R->az.shrink_to_fit();
     R->b.clear(); R->b.shrink_to_fit();
+    R->dinv.clear(); R->dinv.shrink_to_fit();
   }
   cuda::atomic_ref<unsigned, cuda::thread_scope_system> live(S->sh->live);
   if (S->published > S->sh->claimed && live.load(cuda::memory_order_acquire) == 0) {
@@ -453,8 +511,14 @@ void pcg_server_destroy(pcg_server* S) {
 
 pcg_status pcg_submit(pcg_server* S, const pcg_matrix* A, const double* b, double tol, int32_t method, double sigma,
                       int32_t maxit, uint64_t* ticket) {
+  return pcg_submit_ex(S, A, b, tol, method, sigma, maxit, 0, PCG_FP64, ticket);
+}
+
+pcg_status pcg_submit_ex(pcg_server* S, const pcg_matrix* A, const double* b, double tol, int32_t method,
+                         double sigma, int32_t maxit, uint32_t flags, int32_t precision, uint64_t* ticket) {
   if (!S || !A || !b || !ticket) return PCG_EINVAL;
   if (method != PCG_PCG && method != PCG_SPCG) return PCG_EINVAL;
+  if ((flags & ~PCG_JACOBI) || (precision != PCG_FP64 && precision != PCG_MIXED_IR)) return PCG_EINVAL;
   if (!(tol >= 0.0) || !isfinite(tol) || maxit < 0 || !isfinite(sigma)) return PCG_EINVAL;
   const int fam = family_of(*A);
   if (fam < 0) return PCG_EINVAL;
@@ -465,6 +529,8 @@ pcg_status pcg_submit(pcg_server* S, const pcg_matrix* A, const double* b, doubl
   R->tol = tol;
   R->method = method;
   R->maxit = maxit;
+  R->mode = (precision == PCG_MIXED_IR ? 2 : 0) + ((flags & PCG_JACOBI) ? 1 : 0);
+  const bool jac = (flags & PCG_JACOBI) != 0;
   long long n;
   double diag_sum = 0.0;
   if (fam == 4) {
@@ -508,9 +574,31 @@ pcg_status pcg_submit(pcg_server* S, const pcg_matrix* A, const double* b, doubl
     }
   }
   R->n = n;
+  if (jac) {
+    // D^{-1}: the diagonal as for pcg_create(..., PCG_JACOBI)
+    R->dinv.resize(n);
+    for (long long i = 0; i < n; ++i) {
+      double dg;
+      if (fam == 4) {
+        dg = 0.0;
+        for (int k = A->row_ptr[i]; k < A->row_ptr[i + 1]; ++k)
+          if (A->col[k] == i) dg += A->val[k];
+      } else if (fam == 1 || fam == 3) {
+        dg = A->diag[i];
+      } else {
+        dg = fam == 2 ? 6.0 : 4.0;
+      }
+      if (!(dg > 0.0) || !isfinite(dg)) {
+        delete R;
+        return PCG_EINVAL;
+      }
+      R->dinv[i] = 1.0 / dg;
+    }
+  }
   // sigma < 0: the mean diagonal entry (for the unscaled Laplacians half the top of
   // the spectrum, the shift Table 1 uses for lapl200)
-  R->sigma = sigma >= 0.0 ? sigma : diag_sum / (double)n;
+  // (with Jacobi, of M^{-1} A, which is 1)
+  R->sigma = sigma >= 0.0 ? sigma : jac ? 1.0 : diag_sum / (double)n;
   R->b.assign(b, b + n);
   R->bytes = request_bytes(*R);
   std::lock_guard<std::mutex> lock(S->mu);

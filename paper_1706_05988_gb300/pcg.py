@@ -86,11 +86,15 @@ def lib() -> ctypes.CDLL:
         L.pcg_batch_solve.argtypes = [vp, vp, vp, i32, vp, f64, i32, vp, vp, vp]
         L.pcg_batch_autotune.argtypes = [vp, vp, vp, i32, vp, vp]
         L.pcg_batch_set_cluster.argtypes = [vp, i32]
+        L.pcg_batch_set_precision.argtypes = [vp, i32]
+        L.pcg_batch_set_param.argtypes = [vp, i32, f64]
         L.pcg_batch_last_kernel_ms.argtypes = [vp, ctypes.POINTER(f64)]
         L.pcg_batch_destroy.argtypes = [vp]
         L.pcg_batch_destroy.restype = None
         L.pcg_server_create.argtypes = [ctypes.c_size_t, i32, ctypes.POINTER(vp)]
         L.pcg_submit.argtypes = [vp, ctypes.POINTER(pcg_matrix), vp, f64, i32, f64, i32, ctypes.POINTER(ctypes.c_uint64)]
+        L.pcg_submit_ex.argtypes = [vp, ctypes.POINTER(pcg_matrix), vp, f64, i32, f64, i32, ctypes.c_uint32, i32,
+                                    ctypes.POINTER(ctypes.c_uint64)]
         L.pcg_poll.argtypes = [vp, ctypes.c_uint64, vp, ctypes.POINTER(pcg_result)]
         L.pcg_server_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_size_t)]
         L.pcg_server_destroy.argtypes = [vp]
@@ -101,9 +105,10 @@ def lib() -> ctypes.CDLL:
         L.pcg_version.argtypes = []
         L.pcg_version.restype = ctypes.c_char_p
         for f in ("pcg_create", "pcg_set_stream", "pcg_solve", "pcg_solve_device", "pcg_select_sigma", "pcg_psi",
-                  "pcg_apply", "pcg_true_residual_noalloc", "pcg_set_param", "pcg_set_shifts", "pcg_batch_create", "pcg_batch_solve",
-                  "pcg_batch_autotune", "pcg_batch_set_cluster", "pcg_batch_last_kernel_ms", "pcg_server_create",
-                  "pcg_submit", "pcg_poll", "pcg_server_stats",
+                  "pcg_apply", "pcg_true_residual_noalloc", "pcg_set_param", "pcg_set_shifts",
+                  "pcg_batch_create", "pcg_batch_solve", "pcg_batch_autotune", "pcg_batch_set_cluster",
+                  "pcg_batch_set_precision", "pcg_batch_set_param", "pcg_batch_last_kernel_ms", "pcg_server_create",
+                  "pcg_submit", "pcg_submit_ex", "pcg_poll", "pcg_server_stats",
                   "pcg_kernel_stats", "pcg_kernel_stats_reset"):
             getattr(L, f).restype = st
         _lib = L
@@ -319,16 +324,26 @@ class Solver:
 class Batch:
     """pcg_batch over a list of problems of one operator family (host arrays)."""
 
-    def __init__(self, problems):
+    def __init__(self, problems, flags: int = 0, precision: int = PCG_FP64):
         self.mats = [Matrix(P) for P in problems]
         self.n = [P.n for P in problems]
         arr = (pcg_matrix * len(problems))(*[m.m for m in self.mats])
         self._arr = arr
         out = ctypes.c_void_p()
-        s = lib().pcg_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(problems), 0, ctypes.byref(out))
+        s = lib().pcg_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(problems), flags, ctypes.byref(out))
         if s != PCG_OK:
             raise PcgError(s, "pcg_batch_create")
         self.h = out.value
+        if precision != PCG_FP64:
+            s = lib().pcg_batch_set_precision(self.h, precision)
+            if s != PCG_OK:
+                raise PcgError(s, "pcg_batch_set_precision")
+
+    def set_precision(self, precision: int) -> int:
+        return lib().pcg_batch_set_precision(self.h, precision)
+
+    def set_param(self, param: int, value: float) -> int:
+        return lib().pcg_batch_set_param(self.h, param, value)
 
     def close(self):
         if getattr(self, "h", None):
@@ -408,11 +423,12 @@ class Server:
     def __exit__(self, *a):
         self.close()
 
-    def submit(self, P, b, tol=1e-8, method=PCG_SPCG, sigma=-1.0, maxit=100000) -> int:
+    def submit(self, P, b, tol=1e-8, method=PCG_SPCG, sigma=-1.0, maxit=100000, flags=0, precision=PCG_FP64) -> int:
         m = Matrix(P)
         b = np.ascontiguousarray(b, dtype=np.float64)
         t = ctypes.c_uint64()
-        s = lib().pcg_submit(self.h, ctypes.byref(m.m), b.ctypes.data, tol, method, sigma, maxit, ctypes.byref(t))
+        s = lib().pcg_submit_ex(self.h, ctypes.byref(m.m), b.ctypes.data, tol, method, sigma, maxit, flags, precision,
+                                ctypes.byref(t))
         if s != PCG_OK:
             raise PcgError(s, "pcg_submit")
         self.n[t.value] = P.n

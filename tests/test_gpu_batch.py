@@ -80,3 +80,82 @@ def test_batch_rejects_mixed_families(B):
     from paper_1706_05988_gb300 import pcg as C
     with pytest.raises(C.PcgError):
         B.Batch([S.laplacian_2d(8), S.laplacian_3d(4)])
+
+
+# ------------------------------------------------------------------ Jacobi and mixed precision
+
+def diag_of(P):
+    c = S.to_csr(P) if P.layout != S.CSR32 else P
+    rows = np.repeat(np.arange(c.n), np.diff(c.row_ptr))
+    d = np.zeros(c.n)
+    np.add.at(d, rows[c.col == rows], c.val[c.col == rows])
+    return d
+
+
+def test_batch_jacobi_first_iterations_vs_oracle(B):
+    probs, bs = var2d_batch(k=6, seed=3)
+    with B.Batch(probs, flags=B.PCG_JACOBI) as bt:
+        xs, it, st, tr = bt.solve(bs, [1.0] * len(probs), tol=0.0, maxit=15)
+    for P, b, x, i in zip(probs, bs, xs, it):
+        o = oracle.pcg_sh(P, b, sigma=1.0, maxit=15, minv=1.0 / diag_of(P), log_every=0)
+        assert i == o.iters
+        assert np.linalg.norm(x - o.x) <= 1e-9 * np.linalg.norm(o.x)
+
+
+def test_batch_jacobi_matches_single_solver(B):
+    probs, bs = var2d_batch(k=8, seed=5)
+    with B.Batch(probs, flags=B.PCG_JACOBI) as bt:
+        xs, it, st, tr = bt.solve(bs, [1.0] * len(probs), tol=1e-9, maxit=5000)
+    for P, b, x, i, code in zip(probs, bs, xs, it, st):
+        with B.Solver(P, flags=B.PCG_JACOBI) as one:
+            r = one.solve(b, method="spcg", sigma=1.0, tol=1e-9, maxit=5000)
+        assert code == B.PCG_OK and r.status == B.PCG_OK
+        assert abs(int(i) - r.iters) <= 0.02 * r.iters + 2
+        assert np.linalg.norm(b - oracle.apply(P, x)) <= 3e-9 * np.linalg.norm(b)
+
+
+MIXED_CASES = [
+    ("var2d_jacobi", lambda: var2d_batch(k=10, seed=7), True, 1.0),
+    ("lapl3d_identity", lambda: ([S.laplacian_3d(n, n + 3, n - 2) for n in (6, 11, 17, 24)],
+                                 [S.normal(40 + i, n * (n + 3) * (n - 2)) for i, n in enumerate((6, 11, 17, 24))]),
+     False, 6.0),
+    ("csr_jacobi", lambda: ([S.random_sdd_csr(n, seed=n) for n in (500, 2003, 7001)],
+                            [S.normal(50 + i, n) for i, n in enumerate((500, 2003, 7001))]), True, 1.0),
+]
+
+
+@pytest.mark.parametrize("name,maker,jac,sigma", MIXED_CASES, ids=[c[0] for c in MIXED_CASES])
+def test_batch_mixed_reaches_tolerance(B, name, maker, jac, sigma):
+    """Mixed precision with restarts in the batched launch: every system reaches 1e-8 in the
+    binary64 true residual, recomputed here by the oracle's operator."""
+    probs, bs = maker()
+    with B.Batch(probs, flags=B.PCG_JACOBI if jac else 0, precision=B.PCG_MIXED_IR) as bt:
+        xs, it, st, tr = bt.solve(bs, [sigma] * len(probs), tol=1e-8, maxit=20000)
+    assert np.all(st == B.PCG_OK), st
+    for P, b, x, t in zip(probs, bs, xs, tr):
+        tt = np.linalg.norm(b - oracle.apply(P, x)) / np.linalg.norm(b)
+        assert tt <= 1e-8 and abs(t - tt) <= 1e-6 * tt + 1e-16
+
+
+def test_batch_mixed_matches_single_mixed(B):
+    probs, bs = var2d_batch(k=5, seed=9)
+    with B.Batch(probs, flags=B.PCG_JACOBI, precision=B.PCG_MIXED_IR) as bt:
+        xs, it, st, tr = bt.solve(bs, [1.0] * len(probs), tol=1e-9, maxit=20000)
+    for P, b, x, i, code in zip(probs, bs, xs, it, st):
+        with B.Solver(P, flags=B.PCG_JACOBI) as one:
+            r = one.solve(b, method="spcg", sigma=1.0, tol=1e-9, maxit=20000, precision=B.PCG_MIXED_IR)
+        assert code == B.PCG_OK and r.status == B.PCG_OK
+        assert abs(int(i) - r.iters) <= 0.05 * r.iters + 10, (int(i), r.iters)
+        assert np.linalg.norm(x - r.x) <= 1e-5 * np.linalg.norm(r.x)
+
+
+def test_batch_jacobi_rejects_zero_diagonal(B):
+    from paper_1706_05988_gb300 import pcg as C
+    P = S.Problem(layout=S.CSR32, nx=0, ny=0, nz=0, row_ptr=np.array([0, 1, 2], dtype=np.int32),
+                  col=np.array([1, 0], dtype=np.int32), val=np.array([1.0, 1.0]), n_csr=2)
+    with pytest.raises(C.PcgError):
+        B.Batch([P], flags=B.PCG_JACOBI)
+    with B.Batch([S.laplacian_2d(8)]) as bt:
+        assert bt.set_precision(7) == B.PCG_EINVAL
+        assert bt.set_param(C.PCG_PARAM_MIXED_ETA, 2.0) == B.PCG_EINVAL
+        assert bt.set_param(C.PCG_PARAM_MAX_RESTARTS, 3) == B.PCG_OK

@@ -136,3 +136,58 @@ def test_server_rejects_bad_requests(B):
             srv.submit(S.laplacian_2d(8), np.ones(64), method=C.PCG_CG)
     with pytest.raises(C.PcgError):
         B.Server(100, 1)
+
+
+# ------------------------------------------------------------------ mixed precision and Jacobi
+
+MODES = [(0, 0), ("jac", 0), (0, "mixed"), ("jac", "mixed")]
+
+
+def _mode(B, jac, prec):
+    return (B.PCG_JACOBI if jac else 0), (B.PCG_MIXED_IR if prec else B.PCG_FP64)
+
+
+def test_mixed_jacobi_alone_and_in_the_mix(B):
+    """Requests of all four kinds (binary64 / mixed, M = I / Jacobi) in one stream: each result
+    is bit-identical to the same request served alone and reaches its tolerance."""
+    probs, bs = request_mix()
+    kinds = [MODES[i % 4] for i in range(len(probs))]
+    alone = []
+    for P, b, (jac, prec) in zip(probs, bs, kinds):
+        fl, pr = _mode(B, jac, prec)
+        with B.Server(256 << 20, 4) as srv:
+            alone.append(wait(srv, srv.submit(P, b, tol=1e-9, flags=fl, precision=pr)))
+    with B.Server(256 << 20, 16) as srv:
+        tickets = []
+        for P, b, (jac, prec) in zip(probs, bs, kinds):
+            fl, pr = _mode(B, jac, prec)
+            tickets.append(srv.submit(P, b, tol=1e-9, flags=fl, precision=pr))
+        mixed = [wait(srv, t) for t in tickets]
+    for P, b, a, m in zip(probs, bs, alone, mixed):
+        assert a[0] == m[0] and a[2] == m[2] and np.array_equal(a[1], m[1])
+        assert m[0] == B.PCG_OK
+        tr = np.linalg.norm(b - oracle.apply(P, m[1])) / np.linalg.norm(b)
+        assert tr <= 2e-9 and abs(tr - m[3]) <= 1e-6 * tr + 1e-16
+
+
+def test_served_modes_match_batch(B):
+    """A served request and the same system in a batch run the same per-cluster solver."""
+    P = S.varcoef_2d(45, 38, seed=11)
+    b = S.normal(12, P.n)
+    for jac, prec in MODES:
+        fl, pr = _mode(B, jac, prec)
+        with B.Server(64 << 20, 2) as srv:
+            st, x, it, tr = wait(srv, srv.submit(P, b, tol=1e-9, sigma=1.0 if jac else 2.0, flags=fl, precision=pr))
+        with B.Batch([P], flags=fl, precision=pr) as bt:
+            assert bt.set_cluster(2) == B.PCG_OK
+            xs, its, sts, trs = bt.solve([b], [1.0 if jac else 2.0], tol=1e-9, maxit=100000)
+        assert st == sts[0] == B.PCG_OK and it == its[0] and np.array_equal(x, xs[0]), (jac, prec)
+
+
+def test_submit_ex_rejects_bad_modes(B):
+    from paper_1706_05988_gb300 import pcg as C
+    with B.Server(16 << 20, 2) as srv:
+        with pytest.raises(C.PcgError):
+            srv.submit(S.laplacian_2d(8), np.ones(64), flags=0x4000)
+        with pytest.raises(C.PcgError):
+            srv.submit(S.laplacian_2d(8), np.ones(64), precision=9)
