@@ -34,7 +34,9 @@ FALLBACK_HBM_GBS = 6800.0
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_spcg_iter launch (ncu), keyed by the
 # SHA-256 of the kernel source it was measured on; a changed kernel reports null.
-NCU_TRAFFIC = {}
+# k_spcg_iter<StencilOp<3, ST_LAP_FIXED, 2>> on 256^3: dram__bytes_read.sum + dram__bytes_write.sum of one launch
+# (811.23 + 750.12 MB; a one-pass capture, profiles/spcg_iter_stencil7_256cubed_traffic.md)
+NCU_TRAFFIC = {"db28dd47f9fa25b7": 1561.35e6}
 
 
 def kernel_source_sha() -> str:
@@ -149,42 +151,48 @@ def cpu_oracle_rate(P, b, iters: int) -> tuple[float, float]:
 
 def batch_measure(pkg, S, nsys: int, seed: int = 0) -> dict:
     """Solves/s of nsys 2D FV systems (sides U{32..128}, kappa = 10^U[-2,2] per cell, b ~ N(0,1),
-    tol 1e-8, FP64 shifted p-CG with sigma = half the median diagonal): one batched launch against
-    the single-system entry point (sampled), both through host buffers."""
+    tol 1e-8) in one batched launch, in two forms: FP64 shifted p-CG (M = I, sigma = half the median
+    diagonal) and mixed precision with FP64 refinement and Jacobi M^-1 (sigma = 1); against plain FP64
+    solves one at a time through the single-system entry point (sampled), all through host buffers."""
     import numpy as np
     import torch
+    from paper_1706_05988_gb300 import pcg as C
     rng = np.random.default_rng(seed)
     sides = rng.integers(32, 129, size=nsys)
     probs = [S.varcoef_2d(int(L), int(L), seed=seed + i) for i, L in enumerate(sides)]
     bs = [S.normal(1000 + i, P.n) for i, P in enumerate(probs)]
-    sig = [0.5 * float(np.median(P.diag)) for P in probs]
-    with pkg.Batch(probs) as bt:
-        c, _ = bt.autotune(bs, sig, probe_iters=100)
-        bt.solve(bs, sig, tol=1e-8, maxit=100000)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        _, it, st, tr = bt.solve(bs, sig, tol=1e-8, maxit=100000)
-        torch.cuda.synchronize()
-        tb = time.perf_counter() - t0
-        kms = bt.last_kernel_ms()
+    sig_plain = [0.5 * float(np.median(P.diag)) for P in probs]
+    out = {"workload": f"{nsys} 2D variable-coefficient 5-point systems, sides U{{32..128}}, kappa 10^U[-2,2] "
+                       "per cell, b ~ N(0,1), tol 1e-8"}
+    for name, flags, prec, sig in (("fp64", 0, C.PCG_FP64, sig_plain),
+                                   ("mixed_jacobi", pkg.PCG_JACOBI, C.PCG_MIXED_IR, [1.0] * nsys)):
+        with pkg.Batch(probs, flags=flags, precision=prec) as bt:
+            c, _ = bt.autotune(bs, sig, probe_iters=100)
+            bt.solve(bs, sig, tol=1e-8, maxit=100000)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, it, st, tr = bt.solve(bs, sig, tol=1e-8, maxit=100000)
+            torch.cuda.synchronize()
+            tb = time.perf_counter() - t0
+            out[name] = {"solves_per_s": nsys / tb, "kernel_ms": bt.last_kernel_ms(), "cluster_size": c,
+                         "converged": int(np.sum(st == 0)), "max_true_relres": float(np.max(tr)),
+                         "mean_iters": float(np.mean(it))}
     k = min(nsys, 16)
     idx = np.linspace(0, nsys - 1, k).astype(int)
     t1 = 0.0
     for i in idx:
         with pkg.Solver(probs[i]) as one:
-            one.solve(bs[i], method="spcg", sigma=sig[i], tol=1e-8, maxit=100000)
+            one.solve(bs[i], method="spcg", sigma=sig_plain[i], tol=1e-8, maxit=100000)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            one.solve(bs[i], method="spcg", sigma=sig[i], tol=1e-8, maxit=100000)
+            one.solve(bs[i], method="spcg", sigma=sig_plain[i], tol=1e-8, maxit=100000)
             torch.cuda.synchronize()
             t1 += time.perf_counter() - t0
     one_rate = k / t1
-    return {"workload": f"{nsys} 2D variable-coefficient 5-point systems, sides U{{32..128}}, kappa 10^U[-2,2] "
-                        "per cell, b ~ N(0,1), tol 1e-8, FP64",
-            "solves_per_s": nsys / tb, "kernel_ms": kms, "cluster_size": c, "converged": int(np.sum(st == 0)),
-            "max_true_relres": float(np.max(tr)), "mean_iters": float(np.mean(it)),
-            "one_at_a_time_solves_per_s": one_rate, "one_at_a_time_sample": int(k),
-            "speedup": (nsys / tb) / one_rate}
+    out["one_at_a_time_fp64"] = {"solves_per_s": one_rate, "sample": int(k)}
+    out["speedup_fp64"] = out["fp64"]["solves_per_s"] / one_rate
+    out["speedup_mixed_jacobi"] = out["mixed_jacobi"]["solves_per_s"] / one_rate
+    return out
 
 
 def varcoef_measure(pkg, S) -> dict:
@@ -244,12 +252,10 @@ def serving_trace(nreq: int, rate: float, seed: int = 0):
     return reqs
 
 
-def serving_measure(pkg, nreq: int, rate: float) -> dict:
-    """p50/p99 latency and solves/s of the request stream through the continuous-batching
-    server, against the same stream served one request at a time by the single-system
-    solver (FP64, same shift rule and tolerances)."""
+def serve_stream(pkg, reqs, flags: int, precision: int):
+    """Runs the request stream through one server; returns (latencies, span)."""
     import numpy as np
-    reqs = serving_trace(nreq, rate)
+    nreq = len(reqs)
     lat = np.zeros(nreq)
     with pkg.Server(8 << 30, 512) as srv:
         pending = {}
@@ -259,7 +265,7 @@ def serving_measure(pkg, nreq: int, rate: float) -> dict:
         while done < nreq:
             now = time.perf_counter() - t0
             while i < nreq and reqs[i][0] <= now:
-                pending[srv.submit(reqs[i][1], reqs[i][2], tol=reqs[i][3])] = i
+                pending[srv.submit(reqs[i][1], reqs[i][2], tol=reqs[i][3], flags=flags, precision=precision)] = i
                 i += 1
             for t in list(pending):
                 r = srv.poll(t)
@@ -270,6 +276,26 @@ def serving_measure(pkg, nreq: int, rate: float) -> dict:
             if not pending and i < nreq:
                 time.sleep(max(0.0, min(0.001, reqs[i][0] - (time.perf_counter() - t0))))
         span = time.perf_counter() - t0
+    return lat, span
+
+
+def serving_measure(pkg, nreq: int, rate: float) -> dict:
+    """p50/p99 latency and solves/s of the request stream through the continuous-batching
+    server, in FP64 (M = I) and in mixed precision with FP64 refinement and Jacobi M^-1, against
+    the same stream served one request at a time by plain FP64 solves of the single-system
+    solver (same shift rule and tolerances)."""
+    import numpy as np
+    from paper_1706_05988_gb300 import pcg as C
+    reqs = serving_trace(nreq, rate)
+    out = {"workload": f"{nreq} requests, Poisson arrivals {rate:g}/s, n log-uniform [1e3, 1e5], half 2D/3D "
+                       "Laplacian stencils, half random SDD CSR (7-27 nnz/row), tol log-uniform [1e-10, 1e-6]"}
+
+    def summary(lat, span):
+        return {"solves_per_s": nreq / span, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                "p99_ms": 1e3 * float(np.percentile(lat, 99))}
+
+    out["served_fp64"] = summary(*serve_stream(pkg, reqs, 0, C.PCG_FP64))
+    out["served_mixed_jacobi"] = summary(*serve_stream(pkg, reqs, pkg.PCG_JACOBI, C.PCG_MIXED_IR))
     # one at a time: each request starts when it has arrived and the previous one is done
     lat1 = np.zeros(nreq)
     t0 = time.perf_counter()
@@ -282,13 +308,8 @@ def serving_measure(pkg, nreq: int, rate: float) -> dict:
                 np.arange(P.n), np.diff(P.row_ptr))]))
             one.solve(b, method="spcg", sigma=diag, tol=tol, maxit=100000)
         lat1[k] = time.perf_counter() - t0 - arr
-    span1 = time.perf_counter() - t0
-    return {"workload": f"{nreq} requests, Poisson arrivals {rate:g}/s, n log-uniform [1e3, 1e5], half 2D/3D "
-                        "Laplacian stencils, half random SDD CSR (7-27 nnz/row), tol log-uniform [1e-10, 1e-6], FP64",
-            "solves_per_s": nreq / span, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
-            "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-            "one_at_a_time": {"solves_per_s": nreq / span1, "p50_ms": 1e3 * float(np.percentile(lat1, 50)),
-                              "p99_ms": 1e3 * float(np.percentile(lat1, 99))}}
+    out["one_at_a_time_fp64"] = summary(lat1, time.perf_counter() - t0)
+    return out
 
 
 def run_reference(args):

@@ -279,6 +279,13 @@ pcg_status pcg_server_stats(pcg_server *server, int64_t *waiting, int64_t *infli
 void pcg_server_destroy(pcg_server *server);
 
 /* Largest n accepted by pcg_true_residual_noalloc. */
+/* Self-check of the binary32 <-> binary64 conversions that the mixed-precision
+ * kernels perform with integer operations (the paper has no counterpart):
+ * f_out[i] = (float)d_in[i] (round to nearest even) and d_out[i] = (double)f_in[i],
+ * for i < n, on device arrays; synchronises the device.  NaN inputs give a quiet NaN.
+ * Errors: PCG_EINVAL (n < 0 or a NULL array with n > 0), PCG_ECUDA. */
+pcg_status pcg_convert_check(const double *d_in, float *f_out, const float *f_in, double *d_out, int64_t n);
+
 #define PCG_NOALLOC_MAX_N 16777216
 
 /* ||b - A x||_2 and ||(b - A x) - r||_2 without allocating anything.

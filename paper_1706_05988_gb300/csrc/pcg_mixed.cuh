@@ -15,6 +15,17 @@
 #include "pcg_convert.cuh"
 #include "pcg_kernels.cuh"
 
+// Resident blocks per SM the inner-iteration kernels are compiled for (register cap
+// 65536 / (256 * this)): they stream memory with little arithmetic, so occupancy
+// hides latency better than the registers that a wider cap would give.
+#ifndef PCG_MIXED_MIN_BLOCKS
+#define PCG_MIXED_MIN_BLOCKS 3
+#endif
+// Most unknowns per thread of the Jacobi inner iteration.
+#ifndef PCG_MIXED_JAC_MAX_VEC
+#define PCG_MIXED_JAC_MAX_VEC 2
+#endif
+
 namespace pcgk {
 
 // ---------------------------------------------------------------- binary32 operators
@@ -270,7 +281,7 @@ __device__ __forceinline__ void finish_mixed(State* st, Hist h, double gamma, do
 
 // One inner iteration (M = I): binary32 auxiliary recurrences, binary64 x, r and dots.
 template <class Op32>
-__global__ void __launch_bounds__(kBlock) k_mx_iter(Op32 op, Vecs v, State* st, Hist h, double* partials) {
+__global__ void __launch_bounds__(kBlock, PCG_MIXED_MIN_BLOCKS) k_mx_iter(Op32 op, Vecs v, State* st, Hist h, double* partials) {
   constexpr int VEC = Op32::VEC;
   if (st->status != ST_RUNNING) return;
   const int it = st->iter;

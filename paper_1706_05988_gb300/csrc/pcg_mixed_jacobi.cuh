@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kBlock) k_mxj_w0(Op64 op, GenVecs v, const dou
 
 // One inner iteration with M^{-1} = D^{-1}: binary32 auxiliary recurrences, binary64 x, r, dots.
 template <class Op32>
-__global__ void __launch_bounds__(kBlock) k_mxj_iter(Op32 op, GenVecs v, State* st, Hist h, double* partials) {
+__global__ void __launch_bounds__(kBlock, PCG_MIXED_MIN_BLOCKS) k_mxj_iter(Op32 op, GenVecs v, State* st, Hist h, double* partials) {
   constexpr int VEC = Op32::VEC;
   if (st->status != ST_RUNNING) return;
   const int it = st->iter;

@@ -10,6 +10,7 @@ namespace pcgk {
 
 int mixed_iter_blocks_per_sm(const OpDesc& d);    // pcg_mixed_iter.cu
 int mixedj_iter_blocks_per_sm(const OpDesc& d);   // pcg_mixed_iter.cu
+int mixedj_vec(const OpDesc& d);                  // pcg_mixed_iter.cu
 
 namespace {
 
@@ -99,7 +100,7 @@ int grid_for_mixed(const OpDesc& d, int kind, int block) {
   long long units = 0;
   if (kind == KM_ITER || kind == KM_ITER_JAC) {
     per_sm = kind == KM_ITER ? mixed_iter_blocks_per_sm(d) : mixedj_iter_blocks_per_sm(d);
-    units = d.n / mixed_vec(d);
+    units = d.n / (kind == KM_ITER ? mixed_vec(d) : mixedj_vec(d));
   } else if (kind == KM_W0_JAC) {
     with_op64(d, [&](auto op) {
       per_sm = MixedJacRestartKernels<decltype(op)>::blocks_per_sm();

@@ -99,13 +99,14 @@ def lib() -> ctypes.CDLL:
         L.pcg_server_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_size_t)]
         L.pcg_server_destroy.argtypes = [vp]
         L.pcg_server_destroy.restype = None
+        L.pcg_convert_check.argtypes = [vp, vp, vp, vp, i64]
         L.pcg_true_residual_noalloc.argtypes = [ctypes.POINTER(pcg_matrix), vp, vp, vp, vp, vp]
         L.pcg_kernel_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(f64)]
         L.pcg_kernel_stats_reset.argtypes = [vp]
         L.pcg_version.argtypes = []
         L.pcg_version.restype = ctypes.c_char_p
         for f in ("pcg_create", "pcg_set_stream", "pcg_solve", "pcg_solve_device", "pcg_select_sigma", "pcg_psi",
-                  "pcg_apply", "pcg_true_residual_noalloc", "pcg_set_param", "pcg_set_shifts",
+                  "pcg_apply", "pcg_true_residual_noalloc", "pcg_set_param", "pcg_set_shifts", "pcg_convert_check",
                   "pcg_batch_create", "pcg_batch_solve", "pcg_batch_autotune", "pcg_batch_set_cluster",
                   "pcg_batch_set_precision", "pcg_batch_set_param", "pcg_batch_last_kernel_ms", "pcg_server_create",
                   "pcg_submit", "pcg_submit_ex", "pcg_poll", "pcg_server_stats",
