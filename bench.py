@@ -514,8 +514,33 @@ def run_ours(args):
     return 0
 
 
+def profile_case(kind: str, n: int) -> int:
+    """A short solve for an ncu capture (no timing, no JSON): `spcg` runs 8 iterations of the
+    main kernel on the n^3 Laplacian; `jacobi-fp64` and `jacobi-mixed` run 12 iterations of the
+    Jacobi sweeps (sigma = 1; the mixed one with eta = 1e-30, so no restart interrupts)."""
+    import synthetic as S
+    import paper_1706_05988_gb300 as pkg
+    from paper_1706_05988_gb300 import pcg as C
+    pkg.build.build()
+    P, b = S.poisson3d_manufactured(n)[:2]
+    if kind == "spcg":
+        with pkg.Solver(P) as s:
+            r = s.solve(b, method="spcg", sigma=6.0, maxit=8)
+    else:
+        with pkg.Solver(P, flags=pkg.PCG_JACOBI) as s:
+            if kind == "jacobi-fp64":
+                r = s.solve(b, method="spcg", sigma=1.0, maxit=12)
+            else:
+                C.pcg_set_param(s.ctx, C.PCG_PARAM_MIXED_ETA, 1e-30)
+                r = s.solve(b, method="spcg", sigma=1.0, maxit=12, precision=C.PCG_MIXED_IR)
+    print(kind, n, r.status, r.iters)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--profile-case", choices=["spcg", "jacobi-fp64", "jacobi-mixed"], default=None,
+                    help="run one short solve of --size^3 for an ncu capture, then exit")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
@@ -532,6 +557,8 @@ def main():
     ap.add_argument("--serving-rate", type=float, default=2000.0, help="Poisson arrival rate, requests/s")
     ap.add_argument("--size", type=int, default=N_SIDE, help="grid side (default: the 256^3 workload)")
     args = ap.parse_args()
+    if args.profile_case:
+        return profile_case(args.profile_case, args.size)
     globals()["N_SIDE"] = args.size
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
