@@ -112,15 +112,22 @@ class ClockSampler:
                 "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
 
 
-def dist_setup(gpus: int):
+def dist_setup(gpus: int, backend: str = "nccl"):
+    """Rank, world size and local rank from the torchrun environment; joins the process group
+    when there is more than one rank (NCCL on the GPUs; gloo for the host-side tests)."""
     import torch
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != gpus:
+        raise SystemExit(f"--gpus {gpus} but WORLD_SIZE {world}")
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group(backend)
     return rank, world, local
 
 
@@ -131,13 +138,21 @@ def barrier(world):
 
 
 def max_over_ranks(world, v: float) -> float:
+    """The largest of the ranks' values (the job's time is its slowest rank's)."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job throughput: every rank's units (independent systems, no data-path
+    collective) over the slowest rank's time."""
+    return units_per_rank * world / (ms_max / 1e3)
 
 
 def cpu_oracle_rate(P, b, iters: int) -> tuple[float, float]:
@@ -383,7 +398,7 @@ def run_ours(args):
     launches, iter_launches, iter_ms = C.pcg_kernel_stats(solver.ctx)
     ms_max = max_over_ranks(world, ms)
     total_iters = world * args.steps * ITERS_PER_STEP
-    value = total_iters / (ms_max / 1e3)
+    value = job_throughput(args.steps * ITERS_PER_STEP, world, ms_max)
 
     # roofline of the dominant kernel (the fused iteration), from its own CUDA events
     avg_launch_s = iter_ms / max(iter_launches, 1) / 1e3
@@ -522,6 +537,21 @@ def profile_case(kind: str, n: int) -> int:
     import paper_1706_05988_gb300 as pkg
     from paper_1706_05988_gb300 import pcg as C
     pkg.build.build()
+    if kind.startswith("batch"):
+        # one batched launch: 128 2D FV systems (sides U{32..128}) to 1e-8, cluster size 4
+        import numpy as np
+        rng = np.random.default_rng(0)
+        probs = [S.varcoef_2d(int(L), int(L), seed=i) for i, L in enumerate(rng.integers(32, 129, size=128))]
+        bs = [S.normal(1000 + i, P.n) for i, P in enumerate(probs)]
+        jac = kind == "batch-mixed-jacobi"
+        sig = [1.0] * len(probs) if jac else [0.5 * float(np.median(P.diag)) for P in probs]
+        with pkg.Batch(probs, flags=pkg.PCG_JACOBI if jac else 0,
+                       precision=C.PCG_MIXED_IR if jac else C.PCG_FP64) as bt:
+            bt.set_cluster(4)
+            for _ in range(2):
+                _, it, st, _ = bt.solve(bs, sig, tol=1e-8, maxit=100000)
+        print(kind, int(np.sum(st == 0)), float(np.mean(it)))
+        return 0
     P, b = S.poisson3d_manufactured(n)[:2]
     if kind == "spcg":
         with pkg.Solver(P) as s:
@@ -539,7 +569,8 @@ def profile_case(kind: str, n: int) -> int:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile-case", choices=["spcg", "jacobi-fp64", "jacobi-mixed"], default=None,
+    ap.add_argument("--profile-case", choices=["spcg", "jacobi-fp64", "jacobi-mixed", "batch-fp64",
+                                               "batch-mixed-jacobi"], default=None,
                     help="run one short solve of --size^3 for an ncu capture, then exit")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)

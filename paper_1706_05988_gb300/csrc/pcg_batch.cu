@@ -47,7 +47,7 @@ __device__ __forceinline__ void solve_one(cg::cluster_group& cl, double (*part)[
 }
 
 template <int F, int MODE>
-__global__ void __launch_bounds__(kBlock) k_batch(const BatchSys* __restrict__ sys, const int* __restrict__ order,
+__global__ void __launch_bounds__(kBlock, 2) k_batch(const BatchSys* __restrict__ sys, const int* __restrict__ order,
                                                   int nsys, int* next, BatchVecs V, BatchOut* out, BatchParams prm) {
   cg::cluster_group cl = cg::this_cluster();
   const unsigned rank = cl.block_rank();
