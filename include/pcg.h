@@ -189,7 +189,11 @@ pcg_status pcg_psi(pcg_ctx *ctx, const double *alpha, const double *beta, int32_
  * sharing the unknowns; the dot products reduce through distributed shared memory
  * and one cluster barrier per iteration replaces the paper's global reduction.
  * All systems of a batch share one operator family (2D or 3D stencil, constant or
- * variable coefficients, or CSR) but not their sizes. */
+ * variable coefficients, or CSR) but not their sizes.  Systems are grouped into
+ * three size classes (n < 8,192; < 65,536; larger), each with its own queue and
+ * cluster size (default 2, 4, 8); the classes run concurrently, one kernel each,
+ * launched together as one CUDA graph that is captured once and replayed while
+ * the solve parameters stay the same. */
 typedef struct pcg_batch pcg_batch;
 
 /* Copy nsys operators (host arrays, pcg_matrix as for pcg_create) to the device,
@@ -212,10 +216,11 @@ pcg_status pcg_batch_solve(pcg_batch *batch, const double *const *b, double *con
                            const double *sigma, double tol, int32_t maxit, int32_t *iters, int32_t *status,
                            double *true_relres);
 
-/* Autotuner: times probe_iters iterations of every system for each cluster size in
- * {1, 2, 4, 8, 16} and keeps the fastest for later solves; cluster_out (may be NULL)
- * receives it, ms_out[5] (may be NULL) the kernel time of each candidate (NaN where a
- * size cannot be launched).  pcg_batch_set_cluster sets the size directly. */
+/* Autotuner: times probe_iters iterations of the whole batch with one cluster size in
+ * {1, 2, 4, 8, 16} for every class (ms_out[5], may be NULL: the time of each candidate,
+ * NaN where a size cannot be launched; cluster_out, may be NULL: the fastest), then
+ * times each size class alone for every candidate and keeps the fastest size per
+ * class for later solves.  pcg_batch_set_cluster sets one size for every class. */
 pcg_status pcg_batch_autotune(pcg_batch *batch, const double *const *b, const double *sigma, int32_t probe_iters,
                               int32_t *cluster_out, double *ms_out);
 pcg_status pcg_batch_set_cluster(pcg_batch *batch, int32_t cluster_size);

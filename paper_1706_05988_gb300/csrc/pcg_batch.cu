@@ -13,6 +13,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cmath>
 #include <new>
 #include <numeric>
 #include <string>
@@ -134,6 +135,40 @@ cudaError_t with_family(int fam, int mode, Fn&& fn) {
 
 using namespace pcgk;
 
+namespace {
+
+// Systems are grouped into size classes by unknowns; each class has its own work queue
+// (largest first), cluster size and kernel launch, and the classes run concurrently on
+// their own streams inside one captured CUDA graph.  Large systems then get large
+// clusters while small ones keep small clusters, instead of one cluster size for all.
+constexpr int kNumClasses = 3;
+constexpr long long kClassBound[kNumClasses] = {8192, 65536, 1LL << 40};   // n below the bound
+
+struct SizeClass {
+  int nsys = 0;
+  int csize = 4;
+  int* d_order = nullptr;       // the class's systems, largest first (device)
+  int* d_next = nullptr;        // queue head (device)
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+};
+
+// Parameters the captured graph was built for.
+struct GraphKey {
+  int mode = -1, mask = 0;
+  int csize[kNumClasses] = {0, 0, 0};
+  double tol = 0.0, eta = 0.0;
+  int maxit = 0, max_restarts = 0;
+  bool operator==(const GraphKey& o) const {
+    for (int k = 0; k < kNumClasses; ++k)
+      if (csize[k] != o.csize[k]) return false;
+    return mode == o.mode && mask == o.mask && tol == o.tol && eta == o.eta && maxit == o.maxit &&
+           max_restarts == o.max_restarts;
+  }
+};
+
+}  // namespace
+
 struct pcg_batch {
   int device = 0;
   int family = -1;
@@ -144,8 +179,10 @@ struct pcg_batch {
   std::vector<void*> owned;
   std::vector<BatchSys> host_sys;
   BatchSys* d_sys = nullptr;
-  int* d_order = nullptr;
-  int* d_next = nullptr;
+  SizeClass cls[kNumClasses];
+  cudaEvent_t fork = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  GraphKey graph_key;
   BatchOut* d_out = nullptr;
   double* d_vec = nullptr;        // b, x, r, w0, w1, z, s, p (+ u, q, t, m0, m1, u64, dinv, dinv32)
   bool jacobi = false;
@@ -154,7 +191,6 @@ struct pcg_batch {
   int max_restarts = 200;
   double* h_stage = nullptr;      // pinned staging of b / x (total doubles)
   cudaStream_t stream = nullptr;
-  int csize = 8;
   int tuned = 0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   double last_kernel_ms = 0.0;
@@ -216,27 +252,77 @@ int max_clusters_of(int fam, int mode, int csize) {
   return n;
 }
 
-pcg_status run_batch(pcg_batch* B, int csize, double tol, int maxit) {
+// Builds (or reuses) the graph that launches every class in `mask` on its own stream, then
+// replays it; records the CUDA-event time of the whole graph.
+pcg_status run_batch(pcg_batch* B, int mask, double tol, int maxit) {
   const int mode = mode_of(B);
-  const int maxc = max_clusters_of(B->family, mode, csize);
-  if (maxc <= 0) {
-    cudaGetLastError();
-    return PCG_ECUDA;
+  GraphKey key;
+  key.mode = mode;
+  key.mask = mask;
+  for (int k = 0; k < kNumClasses; ++k) key.csize[k] = B->cls[k].csize;
+  key.tol = tol;
+  key.maxit = maxit;
+  key.eta = B->eta;
+  key.max_restarts = B->max_restarts;
+  if (!B->graph || !(key == B->graph_key)) {
+    if (B->graph) {
+      cudaGraphExecDestroy(B->graph);
+      B->graph = nullptr;
+    }
+    // grid per class: as many clusters as can be resident (at most one per system).  The
+    // largest class is launched first and fills the GPU; the smaller classes' blocks start
+    // as its clusters run out of systems, so they fill its tail.
+    int clusters[kNumClasses] = {0, 0, 0};
+    for (int k = 0; k < kNumClasses; ++k) {
+      const SizeClass& c = B->cls[k];
+      if (!((mask >> k) & 1) || c.nsys == 0) continue;
+      const int maxc = max_clusters_of(B->family, mode, c.csize);
+      if (maxc <= 0) {
+        cudaGetLastError();
+        return PCG_ECUDA;
+      }
+      clusters[k] = std::min(maxc, c.nsys);
+    }
+    BatchParams prm;
+    prm.tol = tol;
+    prm.maxit = maxit;
+    prm.eta = B->eta;
+    prm.max_restarts = B->max_restarts;
+    const BatchVecs V = vecs_of(B);
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PCG_ECUDA;
+    cudaError_t e = cudaEventRecord(B->fork, B->stream);
+    for (int kk = kNumClasses - 1; kk >= 0 && e == cudaSuccess; --kk) {   // largest class first
+      const int k = kk;
+      SizeClass& c = B->cls[k];
+      if (clusters[k] == 0) continue;
+      e = cudaStreamWaitEvent(c.stream, B->fork, 0);
+      if (e == cudaSuccess) e = cudaMemsetAsync(c.d_next, 0, sizeof(int), c.stream);
+      if (e == cudaSuccess)
+        e = with_family(B->family, mode, [&](auto F, auto M) {
+          return launch_batch<decltype(F)::value, decltype(M)::value>(clusters[k], c.csize, c.stream, B->d_sys,
+                                                                      c.d_order, c.nsys, c.d_next, V, B->d_out, prm);
+        });
+      if (e == cudaSuccess) e = cudaEventRecord(c.done, c.stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(B->stream, c.done, 0);
+    }
+    const cudaError_t ee = cudaStreamEndCapture(B->stream, &g);
+    if (e != cudaSuccess || ee != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return PCG_ECUDA;
+    }
+    e = cudaGraphInstantiate(&B->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      B->graph = nullptr;
+      cudaGetLastError();
+      return PCG_ECUDA;
+    }
+    B->graph_key = key;
   }
-  const int clusters = std::min(maxc, B->nsys);
-  if (cudaMemsetAsync(B->d_next, 0, sizeof(int), B->stream) != cudaSuccess) return PCG_ECUDA;
-  const BatchVecs V = vecs_of(B);
   if (cudaEventRecord(B->e0, B->stream) != cudaSuccess) return PCG_ECUDA;
-  BatchParams prm;
-  prm.tol = tol;
-  prm.maxit = maxit;
-  prm.eta = B->eta;
-  prm.max_restarts = B->max_restarts;
-  const cudaError_t e = with_family(B->family, mode, [&](auto F, auto M) {
-    return launch_batch<decltype(F)::value, decltype(M)::value>(clusters, csize, B->stream, B->d_sys, B->d_order,
-                                                                B->nsys, B->d_next, V, B->d_out, prm);
-  });
-  if (e != cudaSuccess) {
+  if (cudaGraphLaunch(B->graph, B->stream) != cudaSuccess) {
     cudaGetLastError();
     return PCG_ECUDA;
   }
@@ -246,6 +332,13 @@ pcg_status run_batch(pcg_batch* B, int csize, double tol, int maxit) {
   cudaEventElapsedTime(&ms, B->e0, B->e1);
   B->last_kernel_ms = ms;
   return PCG_OK;
+}
+
+int all_classes(const pcg_batch* B) {
+  int m = 0;
+  for (int k = 0; k < kNumClasses; ++k)
+    if (B->cls[k].nsys > 0) m |= 1 << k;
+  return m;
 }
 
 }  // namespace
@@ -341,10 +434,6 @@ pcg_status pcg_batch_create(const pcg_matrix* systems, int32_t nsys, uint32_t fl
   void* p;
   if (balloc(B, &p, nsys * sizeof(BatchSys)) != PCG_OK) return bail(PCG_ENOMEM);
   B->d_sys = (BatchSys*)p;
-  if (balloc(B, &p, nsys * sizeof(int)) != PCG_OK) return bail(PCG_ENOMEM);
-  B->d_order = (int*)p;
-  if (balloc(B, &p, sizeof(int)) != PCG_OK) return bail(PCG_ENOMEM);
-  B->d_next = (int*)p;
   if (balloc(B, &p, nsys * sizeof(BatchOut)) != PCG_OK) return bail(PCG_ENOMEM);
   B->d_out = (BatchOut*)p;
   const int nvec = B->jacobi ? 16 : 8;
@@ -387,14 +476,33 @@ pcg_status pcg_batch_create(const pcg_matrix* systems, int32_t nsys, uint32_t fl
         cudaSuccess)
       return bail(PCG_ECUDA);
   }
-  // largest systems first: the queue then balances the clusters' work
+  // size classes, each with its queue ordered largest first (the queue then balances the
+  // clusters' work), its own stream and a default cluster size growing with the class
   std::vector<int> order(nsys);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return B->n[a] > B->n[b]; });
-  if (cudaMemcpy(B->d_order, order.data(), nsys * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
-    return bail(PCG_ECUDA);
   if (cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(PCG_ECUDA);
   if (cudaEventCreate(&B->e0) != cudaSuccess || cudaEventCreate(&B->e1) != cudaSuccess) return bail(PCG_ECUDA);
+  if (cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) != cudaSuccess) return bail(PCG_ECUDA);
+  static const int kDefaultCluster[kNumClasses] = {2, 4, 8};
+  for (int c = 0; c < kNumClasses; ++c) {
+    SizeClass& sc = B->cls[c];
+    const long long lo = c == 0 ? 0 : kClassBound[c - 1];
+    std::vector<int> mine;
+    for (int k : order)
+      if (B->n[k] >= lo && B->n[k] < kClassBound[c]) mine.push_back(k);
+    sc.nsys = (int)mine.size();
+    sc.csize = kDefaultCluster[c];
+    if (balloc(B, &p, (mine.empty() ? 1 : mine.size()) * sizeof(int)) != PCG_OK) return bail(PCG_ENOMEM);
+    sc.d_order = (int*)p;
+    if (!mine.empty() &&
+        cudaMemcpy(sc.d_order, mine.data(), mine.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(PCG_ECUDA);
+    if (balloc(B, &p, sizeof(int)) != PCG_OK) return bail(PCG_ENOMEM);
+    sc.d_next = (int*)p;
+    if (cudaStreamCreateWithFlags(&sc.stream, cudaStreamNonBlocking) != cudaSuccess) return bail(PCG_ECUDA);
+    if (cudaEventCreateWithFlags(&sc.done, cudaEventDisableTiming) != cudaSuccess) return bail(PCG_ECUDA);
+  }
   *out = B;
   return PCG_OK;
 }
@@ -404,6 +512,15 @@ void pcg_batch_destroy(pcg_batch* B) {
   if (B->stream) cudaStreamSynchronize(B->stream);
   for (void* p : B->owned) cudaFree(p);
   if (B->h_stage) cudaFreeHost(B->h_stage);
+  if (B->graph) cudaGraphExecDestroy(B->graph);
+  for (SizeClass& sc : B->cls) {
+    if (sc.stream) {
+      cudaStreamSynchronize(sc.stream);
+      cudaStreamDestroy(sc.stream);
+    }
+    if (sc.done) cudaEventDestroy(sc.done);
+  }
+  if (B->fork) cudaEventDestroy(B->fork);
   if (B->e0) cudaEventDestroy(B->e0);
   if (B->e1) cudaEventDestroy(B->e1);
   if (B->stream) cudaStreamDestroy(B->stream);
@@ -433,7 +550,7 @@ pcg_status pcg_batch_solve(pcg_batch* B, const double* const* b, double* const* 
   if (cudaMemcpyAsync((double*)V.b, B->h_stage, (size_t)B->total * sizeof(double), cudaMemcpyHostToDevice,
                       B->stream) != cudaSuccess)
     return PCG_ECUDA;
-  pcg_status s = run_batch(B, B->csize, tol, maxit);
+  pcg_status s = run_batch(B, all_classes(B), tol, maxit);
   if (s != PCG_OK) return s;
   if (cudaMemcpyAsync(B->h_stage, V.x, (size_t)B->total * sizeof(double), cudaMemcpyDeviceToHost, B->stream) !=
       cudaSuccess)
@@ -466,11 +583,14 @@ pcg_status pcg_batch_autotune(pcg_batch* B, const double* const* b, const double
     xs[k] = store[k].data();
   }
   const int cand[] = {1, 2, 4, 8, 16};
+  // 1. one size for every class: the whole batch per candidate (ms_out, cluster_out)
   double best = INFINITY;
-  int best_c = B->csize;
+  int best_c = B->cls[1].csize;
+  int saved[kNumClasses];
+  for (int k = 0; k < kNumClasses; ++k) saved[k] = B->cls[k].csize;
   for (int ci = 0; ci < 5; ++ci) {
     const int c = cand[ci];
-    B->csize = c;
+    for (SizeClass& sc : B->cls) sc.csize = c;
     if (ms_out) ms_out[ci] = NAN;
     pcg_status s = pcg_batch_solve(B, b, xs.data(), PCG_SPCG, sigma, 0.0, probe_iters, nullptr, nullptr, nullptr);
     if (s != PCG_OK && s != PCG_ENOTCONV) continue;   // a shape this GPU cannot launch is skipped
@@ -480,7 +600,36 @@ pcg_status pcg_batch_autotune(pcg_batch* B, const double* const* b, const double
       best_c = c;
     }
   }
-  B->csize = best_c;
+  if (!std::isfinite(best)) {
+    for (int k = 0; k < kNumClasses; ++k) B->cls[k].csize = saved[k];
+    return PCG_ECUDA;
+  }
+  // 2. each size class alone: its fastest cluster size (the per-class shape cache)
+  for (SizeClass& sc : B->cls) sc.csize = best_c;
+  for (int k = 0; k < kNumClasses; ++k) {
+    SizeClass& sc = B->cls[k];
+    if (sc.nsys == 0) continue;
+    double bk = INFINITY;
+    int ck = best_c;
+    for (int ci = 0; ci < 5; ++ci) {
+      sc.csize = cand[ci];
+      pcg_status s = PCG_OK;
+      for (int j = 0; j < B->nsys; ++j) B->host_sys[j].sigma = sigma[j];
+      if (cudaMemcpyAsync(B->d_sys, B->host_sys.data(), B->nsys * sizeof(BatchSys), cudaMemcpyHostToDevice,
+                          B->stream) != cudaSuccess)
+        return PCG_ECUDA;
+      s = run_batch(B, 1 << k, 0.0, probe_iters);
+      if (s != PCG_OK) {
+        cudaGetLastError();
+        continue;
+      }
+      if (B->last_kernel_ms < bk) {
+        bk = B->last_kernel_ms;
+        ck = cand[ci];
+      }
+    }
+    sc.csize = ck;
+  }
   B->tuned = 1;
   if (cluster_out) *cluster_out = best_c;
   return PCG_OK;
@@ -511,7 +660,7 @@ pcg_status pcg_batch_set_cluster(pcg_batch* B, int32_t cluster_size) {
   if (!B) return PCG_EINVAL;
   if (cluster_size != 1 && cluster_size != 2 && cluster_size != 4 && cluster_size != 8 && cluster_size != 16)
     return PCG_EINVAL;
-  B->csize = cluster_size;
+  for (SizeClass& sc : B->cls) sc.csize = cluster_size;
   return PCG_OK;
 }
 

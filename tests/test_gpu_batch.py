@@ -159,3 +159,24 @@ def test_batch_jacobi_rejects_zero_diagonal(B):
         assert bt.set_precision(7) == B.PCG_EINVAL
         assert bt.set_param(C.PCG_PARAM_MIXED_ETA, 2.0) == B.PCG_EINVAL
         assert bt.set_param(C.PCG_PARAM_MAX_RESTARTS, 3) == B.PCG_OK
+
+
+def test_batch_size_classes_after_autotune(B):
+    """Systems in all three size classes (n from 400 to 90,000) run concurrently, each class with
+    the cluster size the autotuner picked for it; every result matches the single-system solver."""
+    sides = [20, 33, 47, 64, 90, 120, 181, 256, 300]
+    probs = [S.laplacian_2d(L, L + 3) for L in sides]
+    bs = [S.normal(300 + i, P.n) for i, P in enumerate(probs)]
+    sig = [4.0] * len(probs)
+    with B.Batch(probs) as bt:
+        c, ms = bt.autotune(bs, sig, probe_iters=30)
+        assert c in (1, 2, 4, 8, 16) and np.isfinite(ms).any()
+        xs, it, st, tr = bt.solve(bs, sig, tol=1e-9, maxit=20000)
+        xs2, it2, _, _ = bt.solve(bs, sig, tol=1e-9, maxit=20000)      # the graph replayed
+    assert np.all(st == B.PCG_OK)
+    for P, b, x, x2, i, i2 in zip(probs, bs, xs, xs2, it, it2):
+        assert i == i2 and np.array_equal(x, x2)
+        with B.Solver(P) as one:
+            r = one.solve(b, method="spcg", sigma=4.0, tol=1e-9, maxit=20000)
+        assert abs(int(i) - r.iters) <= 0.02 * r.iters + 2
+        assert np.linalg.norm(b - oracle.apply(P, x)) <= 3e-9 * np.linalg.norm(b)
