@@ -245,8 +245,14 @@ void pcg_batch_destroy(pcg_batch *batch);
  * served); otherwise the request waits on the host until earlier requests are polled.
  * Admitted requests go to a persistent kernel whose thread-block clusters take them as
  * they come free, so requests that arrive while others run overlap on the device;
- * each request is solved by one cluster exactly as in pcg_batch (x_0 = 0),
- * so its result does not depend on what else runs.  With no work for 20 ms the kernel
+ * each request is solved by one cluster exactly as in pcg_batch (x_0 = 0).  There are
+ * two such kernels side by side on a fixed split of the GPU: requests with
+ * n < 32,768 go to one with many clusters of 2 blocks, larger requests to one with
+ * 16 clusters of 8 blocks (a large request on a small cluster would set the tail
+ * latency).  Host data of an admitted request is packed into a pinned staging ring
+ * and copied without blocking; a request is published to its kernel when its copies
+ * are done.  A request's arithmetic is fixed by its own cluster, so its result does
+ * not depend on what else runs.  With no work for 20 ms the kernel
  * exits and is relaunched by the next submit or poll.  The server is internally
  * synchronised (calls may come from several host threads). */
 typedef struct pcg_server pcg_server;

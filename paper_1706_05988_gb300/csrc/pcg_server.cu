@@ -70,6 +70,50 @@ __device__ __forceinline__ void solve_item(cg::cluster_group& cl, double (*part)
   }
 }
 
+// Before a request is solved, its cluster derives the binary32 coefficient copies and, with
+// Jacobi, D^{-1} in binary64 and binary32 (the diagonal of a CSR row found by column) from
+// the binary64 data the host uploaded: the admission's host work stays one pass over the
+// data, and no extra kernel has to wait for SMs the persistent clusters hold.
+__device__ __forceinline__ void prepare_item(cg::cluster_group& cl, const WorkItem& w) {
+  const int family = w.family, mode = w.mode;
+  const bool jac = mode & 1, mixed = mode >= 2;
+  if (!jac && !(mixed && family != 0 && family != 2)) return;   // nothing to derive
+  const BatchSys& d = w.sys;
+  double* dinv = const_cast<double*>(w.vec.dinv);
+  float* dinv32 = reinterpret_cast<float*>(const_cast<double*>(w.vec.dinv32));
+  const int n = d.n;
+  const int stride = (int)(cl.num_blocks() * kBlock);
+  for (int i = (int)(cl.block_rank() * kBlock + threadIdx.x); i < n; i += stride) {
+    if (family == 4) {
+      const int beg = d.row_ptr[i], end = d.row_ptr[i + 1];
+      double dg = 0.0;
+      for (int k = beg; k < end; ++k) {
+        if (d.col[k] == i) dg += d.val[k];
+        if (mixed) const_cast<float*>(d.val32)[k] = f32_of(d.val[k]);
+      }
+      if (jac) {
+        dinv[i] = 1.0 / dg;
+        dinv32[i] = f32_of(dinv[i]);
+      }
+    } else if (family == 1 || family == 3) {
+      if (mixed) {
+        const_cast<float*>(d.diag32)[i] = f32_of(d.diag[i]);
+        const_cast<float*>(d.ax32)[i] = f32_of(d.ax[i]);
+        const_cast<float*>(d.ay32)[i] = f32_of(d.ay[i]);
+        if (family == 3) const_cast<float*>(d.az32)[i] = f32_of(d.az[i]);
+      }
+      if (jac) {
+        dinv[i] = 1.0 / d.diag[i];
+        dinv32[i] = f32_of(dinv[i]);
+      }
+    } else {
+      dinv[i] = family == 2 ? 1.0 / 6.0 : 1.0 / 4.0;
+      dinv32[i] = f32_of(dinv[i]);
+    }
+  }
+  cl.sync();   // cluster-scope release/acquire: every block sees the derived arrays
+}
+
 // Copy of a work item from mapped host memory, bypassing the caches (a ring slot is reused).
 __device__ __forceinline__ void load_item(const WorkItem* src, WorkItem* dst) {
   static_assert(sizeof(WorkItem) % 8 == 0, "word copy");
@@ -127,6 +171,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_server(ServerShared* sh, const Wo
       return;
     }
     const WorkItem w = s_item;
+    prepare_item(cl, w);
     BatchOut res;
     switch (w.family) {
       case 0: solve_item<0>(cl, part, slot, w, res); break;
@@ -171,32 +216,79 @@ namespace {
 
 struct Request {
   uint64_t ticket;
-  pcg_matrix A;                     // host arrays, kept by the request until admitted
+  pcg_matrix A;                     // layout and dimensions (array pointers: see src below)
+  // The request's arrays.  At submission they point at the caller's arrays; a request
+  // that cannot be admitted at once copies them into the vectors below and points there.
+  const double* b_src = nullptr;
+  const int32_t *row_ptr_src = nullptr, *col_src = nullptr;
+  const double *val_src = nullptr, *diag_src = nullptr, *ax_src = nullptr, *ay_src = nullptr, *az_src = nullptr;
   std::vector<double> b;
   std::vector<int32_t> row_ptr, col;
   std::vector<double> val, diag, ax, ay, az;
   double tol, sigma;
   int method, maxit, family;
   int mode;                         // 0 binary64, 1 + Jacobi, 2 mixed, 3 mixed + Jacobi
-  std::vector<double> dinv;         // Jacobi: D^{-1}
   long long n, nnz;
   size_t bytes;                     // arena bytes
   size_t arena_off = 0;
-  long long ring = -1;              // work-item index once published
+  long long ring = -1;              // work-item index (in its lane's ring) once published
+  int lane = 0;
+  WorkItem item;                    // filled at admission, published when its copies are done
+  cudaEvent_t uploaded = nullptr;   // staged admission: the copies' completion
+  size_t stage_off = 0, stage_end = 0;
 };
+
+// Keeps the request's own copies of its arrays (it waits for memory; the caller's may go).
+void own_arrays(Request* R) {
+  const long long n = R->n;
+  if (R->b.empty()) R->b.assign(R->b_src, R->b_src + n);
+  R->b_src = R->b.data();
+  if (R->family == 4) {
+    R->row_ptr.assign(R->row_ptr_src, R->row_ptr_src + n + 1);
+    R->col.assign(R->col_src, R->col_src + R->nnz);
+    R->val.assign(R->val_src, R->val_src + R->nnz);
+    R->row_ptr_src = R->row_ptr.data();
+    R->col_src = R->col.data();
+    R->val_src = R->val.data();
+  } else if (R->family == 1 || R->family == 3) {
+    R->diag.assign(R->diag_src, R->diag_src + n);
+    R->ax.assign(R->ax_src, R->ax_src + n);
+    R->ay.assign(R->ay_src, R->ay_src + n);
+    R->diag_src = R->diag.data();
+    R->ax_src = R->ax.data();
+    R->ay_src = R->ay.data();
+    if (R->family == 3) {
+      R->az.assign(R->az_src, R->az_src + n);
+      R->az_src = R->az.data();
+    }
+  }
+}
+
+void release_arrays(Request* R) {
+  R->b_src = nullptr;
+  R->row_ptr_src = R->col_src = nullptr;
+  R->val_src = R->diag_src = R->ax_src = R->ay_src = R->az_src = nullptr;
+  std::vector<int32_t>().swap(R->row_ptr);
+  std::vector<int32_t>().swap(R->col);
+  for (std::vector<double>* v : {&R->b, &R->val, &R->diag, &R->ax, &R->ay, &R->az})
+    std::vector<double>().swap(*v);
+}
 
 }  // namespace
 
-struct pcg_server {
-  std::mutex mu;
-  int device = 0;
-  size_t budget = 0;
-  int max_slots = 0;
-  unsigned cap = 0;                 // ring capacity
-  int csize = 2;
-  int clusters = 0;
-  char* arena = nullptr;            // device
-  std::map<size_t, size_t> free_blocks;   // offset -> size (first fit, coalesced)
+namespace {
+
+// A lane is one persistent server kernel with its own cluster size, work ring and stream.
+// Small requests go to a lane of many small clusters, large ones to a lane of few large
+// clusters (a large request on a small cluster would set the tail latency); the two
+// kernels run side by side on a fixed split of the GPU's resident blocks.
+constexpr int kLanes = 2;
+constexpr long long kLargeN = 32768;           // n at and above: the large lane
+constexpr int kLaneCluster[kLanes] = {2, 8};
+constexpr int kLargeLaneClusters = 16;         // clusters of the large lane (8 blocks each)
+
+struct Lane {
+  int csize = 2, clusters = 0;
   ServerShared* sh = nullptr;       // mapped host
   ServerShared* d_sh = nullptr;
   WorkItem* items = nullptr;        // mapped host
@@ -208,12 +300,32 @@ struct pcg_server {
   unsigned* d_claim = nullptr;      // device: items taken
   unsigned* d_left = nullptr;       // device: clusters still running
   std::vector<char> occupied;       // ring slot holds an item that was not polled yet
-  cudaStream_t kstream = nullptr, cstream = nullptr;
-  uint64_t next_ticket = 1;
+  cudaStream_t kstream = nullptr;
   unsigned published = 0;
+};
+
+}  // namespace
+
+struct pcg_server {
+  std::mutex mu;
+  int device = 0;
+  size_t budget = 0;
+  int max_slots = 0;
+  unsigned cap = 0;                 // ring capacity (per lane)
+  char* arena = nullptr;            // device
+  std::map<size_t, size_t> free_blocks;   // offset -> size (first fit, coalesced)
+  Lane lane[kLanes];
+  cudaStream_t cstream = nullptr;   // copies
+  uint64_t next_ticket = 1;
   std::deque<Request*> waiting;                 // not yet admitted
+  std::deque<Request*> uploading;               // admitted, copies in flight, not yet published
   std::map<uint64_t, Request*> inflight;        // admitted, not yet polled
   std::map<uint64_t, Request*> all;
+  // pinned staging ring for admissions (one DMA per array instead of pageable copies
+  // and a synchronisation per request); requests larger than the ring go the slow way
+  char* stage = nullptr;
+  size_t stage_cap = 0, stage_head = 0, stage_tail = 0;
+  std::vector<cudaEvent_t> free_events;
 };
 
 namespace {
@@ -266,29 +378,72 @@ int family_of(const pcg_matrix& A) {
   return -1;
 }
 
-// Places the request's data in its arena block and fills its work item.
-pcg_status upload(pcg_server* S, Request* R, WorkItem* w) {
+// Stage allocation in the pinned ring (FIFO: copies complete in submission order).
+bool stage_alloc(pcg_server* S, size_t sz, size_t* off) {
+  if (S->uploading.empty()) S->stage_head = S->stage_tail = 0;
+  size_t& h = S->stage_head;
+  const size_t t = S->stage_tail;
+  if (h >= t) {
+    if (S->stage_cap - h >= sz) {
+      *off = h;
+      h += sz;
+      return true;
+    }
+    if (t > sz) {              // wrap to the front (strictly below the tail: head == tail means empty)
+      *off = 0;
+      h = sz;
+      return true;
+    }
+    return false;
+  }
+  if (t - h > sz) {
+    *off = h;
+    h += sz;
+    return true;
+  }
+  return false;
+}
+
+// Host bytes of an admission: b, then the binary64 operator arrays laid out as on the device.
+size_t op64_bytes(const Request& R) {
+  const size_t n = (size_t)R.n;
+  if (R.family == 4) return pad256((n + 1) * 4) + pad256(R.nnz * 4) + pad256(R.nnz * 8);
+  if (R.family == 1 || R.family == 3) return (R.family == 3 ? 4 : 3) * pad256(n * 8);
+  return 0;
+}
+
+size_t stage_bytes(const Request& R) { return pad256((size_t)R.n * 8) + op64_bytes(R); }
+
+// Places the request's data in its arena block and fills its work item.  With `staged`,
+// b and the binary64 operator arrays are packed into the pinned ring at R->stage_off and
+// copied with one DMA each, and R->uploaded marks the completion of the copies; otherwise the copies come straight from the request's arrays
+// and are waited for here.  The binary32 copies and D^{-1} are derived on the device by the
+// cluster that solves the request.
+pcg_status upload(pcg_server* S, Request* R, bool staged) {
   char* base = S->arena + R->arena_off;
   const size_t n = (size_t)R->n, npad = (n + 31) & ~(size_t)31;
   const bool jac = R->mode & 1, mixed = R->mode >= 2;
   double* v = (double*)base;
-  size_t at = (jac ? 16 : 8) * npad * sizeof(double);
-  std::deque<std::vector<float>> stage;   // binary32 copies, alive until the final synchronisation
-  auto put32 = [&](const double* src, size_t count) -> const float* {
-    stage.emplace_back(count ? count : 1);
-    std::vector<float>& f = stage.back();
-    for (size_t i = 0; i < count; ++i) f[i] = (float)src[i];
-    const void* dst = base + at;
-    at += pad256(count * 4);
-    if (count && cudaMemcpyAsync((void*)dst, f.data(), count * 4, cudaMemcpyHostToDevice, S->cstream) != cudaSuccess)
-      return nullptr;
-    return (const float*)dst;
-  };
+  const size_t at0 = (jac ? 16 : 8) * npad * sizeof(double);
+  size_t at = at0;
+  char* hs = staged ? S->stage + R->stage_off : nullptr;   // host staging: [b | operator arrays]
+  const size_t h_op = pad256(n * 8);
   auto put = [&](const void* src, size_t bytes) -> void* {
+    if (at + pad256(bytes) > R->bytes) return nullptr;   // never: the layout is request_bytes'
     void* dst = base + at;
+    if (staged) {
+      if (bytes) memcpy(hs + h_op + (at - at0), src, bytes);
+    } else if (bytes && cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, S->cstream) != cudaSuccess) {
+      return nullptr;
+    }
     at += pad256(bytes);
-    if (bytes && cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, S->cstream) != cudaSuccess) return nullptr;
     return dst;
+  };
+  auto reserve32 = [&](size_t count) -> const float* {   // filled on the device by prepare_item
+    if (at + pad256(count * 4) > R->bytes) return nullptr;
+    void* dst = base + at;
+    at += pad256(count * 4);
+    return (const float*)dst;
   };
   BatchSys d{};
   d.layout = R->A.layout;
@@ -296,40 +451,45 @@ pcg_status upload(pcg_server* S, Request* R, WorkItem* w) {
   d.off = 0;
   d.sigma = R->method == PCG_SPCG ? R->sigma : 0.0;
   if (R->family == 4) {
-    d.row_ptr = (const int*)put(R->row_ptr.data(), (n + 1) * 4);
-    d.col = (const int*)put(R->col.data(), R->nnz * 4);
-    d.val = (const double*)put(R->val.data(), R->nnz * 8);
+    d.row_ptr = (const int*)put(R->row_ptr_src, (n + 1) * 4);
+    d.col = (const int*)put(R->col_src, R->nnz * 4);
+    d.val = (const double*)put(R->val_src, R->nnz * 8);
     if (!d.row_ptr || !d.col || !d.val) return PCG_ECUDA;
-    if (mixed && !(d.val32 = put32(R->val.data(), R->nnz))) return PCG_ECUDA;
+    if (mixed && !(d.val32 = reserve32(R->nnz))) return PCG_ECUDA;
   } else {
     d.nx = (int)R->A.nx;
     d.ny = (int)R->A.ny;
     d.nz = R->A.layout == PCG_STENCIL7_3D ? (int)R->A.nz : 1;
     if (R->family == 1 || R->family == 3) {
-      d.diag = (const double*)put(R->diag.data(), n * 8);
-      d.ax = (const double*)put(R->ax.data(), n * 8);
-      d.ay = (const double*)put(R->ay.data(), n * 8);
-      d.az = R->family == 3 ? (const double*)put(R->az.data(), n * 8) : nullptr;
+      d.diag = (const double*)put(R->diag_src, n * 8);
+      d.ax = (const double*)put(R->ax_src, n * 8);
+      d.ay = (const double*)put(R->ay_src, n * 8);
+      d.az = R->family == 3 ? (const double*)put(R->az_src, n * 8) : nullptr;
+      if (!d.diag || !d.ax || !d.ay || (R->family == 3 && !d.az)) return PCG_ECUDA;
       if (mixed) {
-        d.diag32 = put32(R->diag.data(), n);
-        d.ax32 = put32(R->ax.data(), n);
-        d.ay32 = put32(R->ay.data(), n);
-        d.az32 = R->family == 3 ? put32(R->az.data(), n) : nullptr;
+        d.diag32 = reserve32(n);
+        d.ax32 = reserve32(n);
+        d.ay32 = reserve32(n);
+        d.az32 = R->family == 3 ? reserve32(n) : nullptr;
         if (!d.diag32 || !d.ax32 || !d.ay32 || (R->family == 3 && !d.az32)) return PCG_ECUDA;
       }
     }
   }
-  if (cudaMemcpyAsync(v, R->b.data(), n * 8, cudaMemcpyHostToDevice, S->cstream) != cudaSuccess) return PCG_ECUDA;
-  if (jac) {
-    if (cudaMemcpyAsync(v + 14 * npad, R->dinv.data(), n * 8, cudaMemcpyHostToDevice, S->cstream) != cudaSuccess)
+  const size_t op64 = op64_bytes(*R);
+  if (staged) {
+    memcpy(hs, R->b_src, n * 8);
+    if (cudaMemcpyAsync(v, hs, n * 8, cudaMemcpyHostToDevice, S->cstream) != cudaSuccess) return PCG_ECUDA;
+    if (op64 && cudaMemcpyAsync(base + at0, hs + h_op, op64, cudaMemcpyHostToDevice, S->cstream) != cudaSuccess)
       return PCG_ECUDA;
-    stage.emplace_back(n);
-    std::vector<float>& f = stage.back();
-    for (size_t i = 0; i < n; ++i) f[i] = (float)R->dinv[i];
-    if (cudaMemcpyAsync(v + 15 * npad, f.data(), n * 4, cudaMemcpyHostToDevice, S->cstream) != cudaSuccess)
-      return PCG_ECUDA;
+  } else if (cudaMemcpyAsync(v, R->b_src, n * 8, cudaMemcpyHostToDevice, S->cstream) != cudaSuccess) {
+    return PCG_ECUDA;
   }
-  if (cudaStreamSynchronize(S->cstream) != cudaSuccess) return PCG_ECUDA;
+  if (staged) {
+    if (cudaEventRecord(R->uploaded, S->cstream) != cudaSuccess) return PCG_ECUDA;
+  } else if (cudaStreamSynchronize(S->cstream) != cudaSuccess) {
+    return PCG_ECUDA;
+  }
+  WorkItem* w = &R->item;
   w->family = R->family;
   w->maxit = R->maxit;
   w->mode = R->mode;
@@ -360,27 +520,27 @@ pcg_status upload(pcg_server* S, Request* R, WorkItem* w) {
   return PCG_OK;
 }
 
-pcg_status launch_server(pcg_server* S) {
-  const unsigned left = (unsigned)S->clusters;
-  if (cudaMemcpyAsync(S->d_left, &left, sizeof(unsigned), cudaMemcpyHostToDevice, S->kstream) != cudaSuccess)
+pcg_status launch_lane(pcg_server* S, Lane& L) {
+  const unsigned left = (unsigned)L.clusters;
+  if (cudaMemcpyAsync(L.d_left, &left, sizeof(unsigned), cudaMemcpyHostToDevice, L.kstream) != cudaSuccess)
     return PCG_ECUDA;
-  if (cudaStreamSynchronize(S->kstream) != cudaSuccess) return PCG_ECUDA;
-  S->sh->stop = 0;
-  cuda::atomic_ref<unsigned, cuda::thread_scope_system> live(S->sh->live);
+  if (cudaStreamSynchronize(L.kstream) != cudaSuccess) return PCG_ECUDA;
+  L.sh->stop = 0;
+  cuda::atomic_ref<unsigned, cuda::thread_scope_system> live(L.sh->live);
   live.store(1u, cuda::memory_order_release);
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(S->clusters * S->csize);
+  cfg.gridDim = dim3(L.clusters * L.csize);
   cfg.blockDim = dim3(kBlock);
-  cfg.stream = S->kstream;
+  cfg.stream = L.kstream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = S->csize;
+  attr[0].val.clusterDim.x = L.csize;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (cudaLaunchKernelEx(&cfg, k_server, S->d_sh, (const WorkItem*)S->d_items, S->d_results, S->d_done, S->cap,
-                         S->d_claim, S->d_left) != cudaSuccess) {
+  if (cudaLaunchKernelEx(&cfg, k_server, L.d_sh, (const WorkItem*)L.d_items, L.d_results, L.d_done, S->cap,
+                         L.d_claim, L.d_left) != cudaSuccess) {
     cudaGetLastError();
     live.store(0u, cuda::memory_order_release);
     return PCG_ECUDA;
@@ -388,49 +548,103 @@ pcg_status launch_server(pcg_server* S) {
   return PCG_OK;
 }
 
-// Admits waiting requests (FIFO) while memory and ring slots allow; publishes them;
-// makes sure a kernel runs while published work is unclaimed.
+// Publishes a request whose copies are done: its work item goes to the next ring slot.
+void publish(pcg_server* S, Request* R) {
+  Lane& L = S->lane[R->lane];
+  const unsigned idx = L.published;
+  L.items[idx % S->cap] = R->item;
+  L.done[idx % S->cap] = 0;
+  L.occupied[idx % S->cap] = 1;
+  R->ring = idx;
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  cuda::atomic_ref<unsigned, cuda::thread_scope_system> tail(L.sh->tail);
+  tail.store(idx + 1, cuda::memory_order_release);
+  L.published = idx + 1;
+}
+
+bool slot_busy(const pcg_server* S, const Request* R) {
+  const Lane& L = S->lane[R->lane];
+  return L.occupied[L.published % S->cap] != 0;
+}
+
+// Publishes staged requests whose copies have completed (in order), admits waiting
+// requests (FIFO) while arena memory, slots and staging allow, and makes sure a kernel
+// runs while published work is unclaimed.
 pcg_status pump(pcg_server* S) {
-  while (!S->waiting.empty()) {
+  for (;;) {
+    while (!S->uploading.empty()) {
+      Request* R = S->uploading.front();
+      if (slot_busy(S, R)) break;                      // its ring slot still holds an unpolled request
+      const cudaError_t q = cudaEventQuery(R->uploaded);
+      if (q == cudaErrorNotReady) break;
+      if (q != cudaSuccess) return PCG_ECUDA;
+      publish(S, R);
+      S->stage_tail = R->stage_end;
+      S->free_events.push_back(R->uploaded);
+      R->uploaded = nullptr;
+      S->uploading.pop_front();
+      if (S->uploading.empty()) S->stage_head = S->stage_tail = 0;
+    }
+    if (S->waiting.empty()) break;
     Request* R = S->waiting.front();
     if ((int)S->inflight.size() >= S->max_slots) break;
-    if (S->occupied[S->published % S->cap]) break;   // its ring slot still holds an unpolled request
+    const size_t sb = stage_bytes(*R);
+    const bool staged = sb <= S->stage_cap;
+    size_t soff = 0;
+    const size_t head0 = S->stage_head, tail0 = S->stage_tail;
+    if (staged && !stage_alloc(S, sb, &soff)) break;   // the ring drains as copies complete
+    if (!staged && (!S->uploading.empty() || slot_busy(S, R))) break;
     size_t off;
-    if (!arena_alloc(S, R->bytes, &off)) break;
+    if (!arena_alloc(S, R->bytes, &off)) {
+      S->stage_head = head0;                           // give the staging back
+      S->stage_tail = tail0;
+      break;
+    }
     R->arena_off = off;
-    const unsigned idx = S->published;
-    WorkItem w;
-    pcg_status s = upload(S, R, &w);
+    if (staged) {
+      if (S->free_events.empty()) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+          arena_free(S, off, R->bytes);
+          S->stage_head = head0;
+          S->stage_tail = tail0;
+          return PCG_ECUDA;
+        }
+        S->free_events.push_back(e);
+      }
+      R->uploaded = S->free_events.back();
+      S->free_events.pop_back();
+      R->stage_off = soff;
+      R->stage_end = soff + sb;
+    }
+    pcg_status s = upload(S, R, staged);
     if (s != PCG_OK) {
       arena_free(S, off, R->bytes);
+      if (staged) {
+        S->stage_head = head0;
+        S->stage_tail = tail0;
+        S->free_events.push_back(R->uploaded);
+        R->uploaded = nullptr;
+      }
       return s;
     }
-    S->items[idx % S->cap] = w;
-    S->done[idx % S->cap] = 0;
-    S->occupied[idx % S->cap] = 1;
-    R->ring = idx;
-    std::atomic_thread_fence(std::memory_order_seq_cst);
-    cuda::atomic_ref<unsigned, cuda::thread_scope_system> tail(S->sh->tail);
-    tail.store(idx + 1, cuda::memory_order_release);
-    S->published = idx + 1;
     S->waiting.pop_front();
     S->inflight[R->ticket] = R;
-    // host copies of the operator are no longer needed
-    R->row_ptr.clear(); R->row_ptr.shrink_to_fit();
-    R->col.clear(); R->col.shrink_to_fit();
-    R->val.clear(); R->val.shrink_to_fit();
-    R->diag.clear(); R->diag.shrink_to_fit();
-    R->ax.clear(); R->ax.shrink_to_fit();
-    R->ay.clear(); R->ay.shrink_to_fit();
-    R->az.clear(); R->az.shrink_to_fit();
-    R->b.clear(); R->b.shrink_to_fit();
-    R->dinv.clear(); R->dinv.shrink_to_fit();
+    release_arrays(R);                 // the data is staged or on the device
+    if (staged) {
+      S->uploading.push_back(R);
+    } else {
+      publish(S, R);
+    }
   }
-  cuda::atomic_ref<unsigned, cuda::thread_scope_system> live(S->sh->live);
-  if (S->published > S->sh->claimed && live.load(cuda::memory_order_acquire) == 0) {
-    // the previous kernel (if any) has exited: wait for its stream, then relaunch
-    if (cudaStreamSynchronize(S->kstream) != cudaSuccess) return PCG_ECUDA;
-    return launch_server(S);
+  for (Lane& L : S->lane) {
+    cuda::atomic_ref<unsigned, cuda::thread_scope_system> live(L.sh->live);
+    if (L.published > L.sh->claimed && live.load(cuda::memory_order_acquire) == 0) {
+      // the lane's previous kernel (if any) has exited: wait for its stream, then relaunch
+      if (cudaStreamSynchronize(L.kstream) != cudaSuccess) return PCG_ECUDA;
+      const pcg_status s = launch_lane(S, L);
+      if (s != PCG_OK) return s;
+    }
   }
   return PCG_OK;
 }
@@ -453,7 +667,6 @@ pcg_status pcg_server_create(size_t hbm_budget_bytes, int32_t max_slots, pcg_ser
   S->budget = hbm_budget_bytes & ~(size_t)255;
   S->max_slots = max_slots;
   S->cap = (unsigned)(4 * max_slots);
-  S->occupied.assign(S->cap, 0);
   void* p;
   if (cudaMalloc(&p, S->budget) != cudaSuccess) {
     cudaGetLastError();
@@ -461,49 +674,71 @@ pcg_status pcg_server_create(size_t hbm_budget_bytes, int32_t max_slots, pcg_ser
   }
   S->arena = (char*)p;
   S->free_blocks[0] = S->budget;
-  if (cudaHostAlloc(&p, sizeof(ServerShared), cudaHostAllocMapped) != cudaSuccess) return bail(PCG_ENOMEM);
-  S->sh = (ServerShared*)p;
-  memset(S->sh, 0, sizeof(ServerShared));
-  if (cudaHostGetDevicePointer((void**)&S->d_sh, S->sh, 0) != cudaSuccess) return bail(PCG_ECUDA);
-  if (cudaHostAlloc(&p, S->cap * sizeof(WorkItem), cudaHostAllocMapped) != cudaSuccess) return bail(PCG_ENOMEM);
-  S->items = (WorkItem*)p;
-  if (cudaHostGetDevicePointer((void**)&S->d_items, S->items, 0) != cudaSuccess) return bail(PCG_ECUDA);
-  if (cudaHostAlloc(&p, S->cap * sizeof(unsigned), cudaHostAllocMapped) != cudaSuccess) return bail(PCG_ENOMEM);
-  S->done = (unsigned*)p;
-  memset(S->done, 0, S->cap * sizeof(unsigned));
-  if (cudaHostGetDevicePointer((void**)&S->d_done, S->done, 0) != cudaSuccess) return bail(PCG_ECUDA);
-  if (cudaHostAlloc(&p, S->cap * sizeof(BatchOut), cudaHostAllocMapped) != cudaSuccess) return bail(PCG_ENOMEM);
-  S->results = (BatchOut*)p;
-  if (cudaHostGetDevicePointer((void**)&S->d_results, S->results, 0) != cudaSuccess) return bail(PCG_ECUDA);
-  if (cudaMalloc(&p, 2 * sizeof(unsigned)) != cudaSuccess) return bail(PCG_ENOMEM);
-  S->d_claim = (unsigned*)p;
-  S->d_left = S->d_claim + 1;
-  if (cudaMemset(S->d_claim, 0, 2 * sizeof(unsigned)) != cudaSuccess) return bail(PCG_ECUDA);
-  if (cudaStreamCreateWithFlags(&S->kstream, cudaStreamNonBlocking) != cudaSuccess) return bail(PCG_ECUDA);
+  S->stage_cap = std::min<size_t>(S->budget / 2, (size_t)128 << 20) & ~(size_t)255;
+  if (cudaHostAlloc(&p, S->stage_cap, cudaHostAllocDefault) != cudaSuccess) return bail(PCG_ENOMEM);
+  S->stage = (char*)p;
   if (cudaStreamCreateWithFlags(&S->cstream, cudaStreamNonBlocking) != cudaSuccess) return bail(PCG_ECUDA);
-  const int mc = server_max_clusters(S->csize);
-  if (mc <= 0) return bail(PCG_ECUDA);
-  S->clusters = mc;
+  // the GPU's resident blocks of k_server, split between the lanes
+  const int small_max = server_max_clusters(kLaneCluster[0]);
+  const int large_max = server_max_clusters(kLaneCluster[1]);
+  if (small_max <= 0 || large_max <= 0) return bail(PCG_ECUDA);
+  const int blocks = small_max * kLaneCluster[0];
+  const int large = std::min(kLargeLaneClusters, std::max(1, large_max / 2));
+  for (int l = 0; l < kLanes; ++l) {
+    Lane& L = S->lane[l];
+    L.csize = kLaneCluster[l];
+    L.clusters = l == 1 ? large : std::max(1, (blocks - large * kLaneCluster[1]) / kLaneCluster[0]);
+    L.occupied.assign(S->cap, 0);
+    if (cudaHostAlloc(&p, sizeof(ServerShared), cudaHostAllocMapped) != cudaSuccess) return bail(PCG_ENOMEM);
+    L.sh = (ServerShared*)p;
+    memset(L.sh, 0, sizeof(ServerShared));
+    if (cudaHostGetDevicePointer((void**)&L.d_sh, L.sh, 0) != cudaSuccess) return bail(PCG_ECUDA);
+    if (cudaHostAlloc(&p, S->cap * sizeof(WorkItem), cudaHostAllocMapped) != cudaSuccess) return bail(PCG_ENOMEM);
+    L.items = (WorkItem*)p;
+    if (cudaHostGetDevicePointer((void**)&L.d_items, L.items, 0) != cudaSuccess) return bail(PCG_ECUDA);
+    if (cudaHostAlloc(&p, S->cap * sizeof(unsigned), cudaHostAllocMapped) != cudaSuccess) return bail(PCG_ENOMEM);
+    L.done = (unsigned*)p;
+    memset(L.done, 0, S->cap * sizeof(unsigned));
+    if (cudaHostGetDevicePointer((void**)&L.d_done, L.done, 0) != cudaSuccess) return bail(PCG_ECUDA);
+    if (cudaHostAlloc(&p, S->cap * sizeof(BatchOut), cudaHostAllocMapped) != cudaSuccess) return bail(PCG_ENOMEM);
+    L.results = (BatchOut*)p;
+    if (cudaHostGetDevicePointer((void**)&L.d_results, L.results, 0) != cudaSuccess) return bail(PCG_ECUDA);
+    if (cudaMalloc(&p, 2 * sizeof(unsigned)) != cudaSuccess) return bail(PCG_ENOMEM);
+    L.d_claim = (unsigned*)p;
+    L.d_left = L.d_claim + 1;
+    if (cudaMemset(L.d_claim, 0, 2 * sizeof(unsigned)) != cudaSuccess) return bail(PCG_ECUDA);
+    if (cudaStreamCreateWithFlags(&L.kstream, cudaStreamNonBlocking) != cudaSuccess) return bail(PCG_ECUDA);
+  }
   *out = S;
   return PCG_OK;
 }
 
 void pcg_server_destroy(pcg_server* S) {
   if (!S) return;
-  if (S->sh) {
-    cuda::atomic_ref<unsigned, cuda::thread_scope_system> stop(S->sh->stop);
-    stop.store(1u, cuda::memory_order_release);
+  for (Lane& L : S->lane) {
+    if (L.sh) {
+      cuda::atomic_ref<unsigned, cuda::thread_scope_system> stop(L.sh->stop);
+      stop.store(1u, cuda::memory_order_release);
+    }
   }
-  if (S->kstream) cudaStreamSynchronize(S->kstream);
+  for (Lane& L : S->lane)
+    if (L.kstream) cudaStreamSynchronize(L.kstream);
   if (S->cstream) cudaStreamSynchronize(S->cstream);
-  for (auto& kv : S->all) delete kv.second;
+  for (auto& kv : S->all) {
+    if (kv.second->uploaded) cudaEventDestroy(kv.second->uploaded);
+    delete kv.second;
+  }
+  for (cudaEvent_t e : S->free_events) cudaEventDestroy(e);
+  if (S->stage) cudaFreeHost(S->stage);
   if (S->arena) cudaFree(S->arena);
-  if (S->d_claim) cudaFree(S->d_claim);
-  if (S->sh) cudaFreeHost(S->sh);
-  if (S->items) cudaFreeHost(S->items);
-  if (S->done) cudaFreeHost(S->done);
-  if (S->results) cudaFreeHost(S->results);
-  if (S->kstream) cudaStreamDestroy(S->kstream);
+  for (Lane& L : S->lane) {
+    if (L.d_claim) cudaFree(L.d_claim);
+    if (L.sh) cudaFreeHost(L.sh);
+    if (L.items) cudaFreeHost(L.items);
+    if (L.done) cudaFreeHost(L.done);
+    if (L.results) cudaFreeHost(L.results);
+    if (L.kstream) cudaStreamDestroy(L.kstream);
+  }
   if (S->cstream) cudaStreamDestroy(S->cstream);
   cudaGetLastError();
   delete S;
@@ -541,17 +776,26 @@ pcg_status pcg_submit_ex(pcg_server* S, const pcg_matrix* A, const double* b, do
     }
     n = A->n;
     R->nnz = A->nnz;
-    R->row_ptr.assign(A->row_ptr, A->row_ptr + n + 1);
-    R->col.assign(A->col, A->col + A->nnz);
-    R->val.assign(A->val, A->val + A->nnz);
-    for (long long i = 0; i < n; ++i)
+    R->row_ptr_src = A->row_ptr;
+    R->col_src = A->col;
+    R->val_src = A->val;
+    bool diag_ok = true;
+    for (long long i = 0; i < n; ++i) {
+      double dg = 0.0;
       for (int k = A->row_ptr[i]; k < A->row_ptr[i + 1]; ++k) {
         if (A->col[k] < 0 || A->col[k] >= n) {
           delete R;
           return PCG_EINVAL;
         }
-        if (A->col[k] == i) diag_sum += A->val[k];
+        if (A->col[k] == i) dg += A->val[k];
       }
+      diag_sum += dg;
+      diag_ok = diag_ok && dg > 0.0 && isfinite(dg);
+    }
+    if (jac && !diag_ok) {                       // Jacobi needs a positive diagonal
+      delete R;
+      return PCG_EINVAL;
+    }
   } else {
     const long long nz = A->layout == PCG_STENCIL7_3D ? A->nz : 1;
     if (A->nx < 1 || A->ny < 1 || nz < 1 || A->nx * A->ny * nz > INT32_MAX - 64) {
@@ -564,43 +808,31 @@ pcg_status pcg_submit_ex(pcg_server* S, const pcg_matrix* A, const double* b, do
         delete R;
         return PCG_EINVAL;
       }
-      R->diag.assign(A->diag, A->diag + n);
-      R->ax.assign(A->ax, A->ax + n);
-      R->ay.assign(A->ay, A->ay + n);
-      if (fam == 3) R->az.assign(A->az, A->az + n);
-      for (long long i = 0; i < n; ++i) diag_sum += A->diag[i];
+      R->diag_src = A->diag;
+      R->ax_src = A->ax;
+      R->ay_src = A->ay;
+      R->az_src = fam == 3 ? A->az : nullptr;
+      bool diag_ok = true;
+      for (long long i = 0; i < n; ++i) {
+        diag_sum += A->diag[i];
+        diag_ok = diag_ok && A->diag[i] > 0.0 && isfinite(A->diag[i]);
+      }
+      if (jac && !diag_ok) {
+        delete R;
+        return PCG_EINVAL;
+      }
     } else {
       diag_sum = (double)n * (fam == 2 ? 6.0 : 4.0);
     }
   }
   R->n = n;
-  if (jac) {
-    // D^{-1}: the diagonal as for pcg_create(..., PCG_JACOBI)
-    R->dinv.resize(n);
-    for (long long i = 0; i < n; ++i) {
-      double dg;
-      if (fam == 4) {
-        dg = 0.0;
-        for (int k = A->row_ptr[i]; k < A->row_ptr[i + 1]; ++k)
-          if (A->col[k] == i) dg += A->val[k];
-      } else if (fam == 1 || fam == 3) {
-        dg = A->diag[i];
-      } else {
-        dg = fam == 2 ? 6.0 : 4.0;
-      }
-      if (!(dg > 0.0) || !isfinite(dg)) {
-        delete R;
-        return PCG_EINVAL;
-      }
-      R->dinv[i] = 1.0 / dg;
-    }
-  }
   // sigma < 0: the mean diagonal entry (for the unscaled Laplacians half the top of
   // the spectrum, the shift Table 1 uses for lapl200)
   // (with Jacobi, of M^{-1} A, which is 1)
   R->sigma = sigma >= 0.0 ? sigma : jac ? 1.0 : diag_sum / (double)n;
-  R->b.assign(b, b + n);
+  R->b_src = b;
   R->bytes = request_bytes(*R);
+  R->lane = n >= kLargeN ? 1 : 0;
   std::lock_guard<std::mutex> lock(S->mu);
   if (R->bytes > S->budget) {
     delete R;
@@ -614,7 +846,11 @@ pcg_status pcg_submit_ex(pcg_server* S, const pcg_matrix* A, const double* b, do
   S->all[R->ticket] = R;
   S->waiting.push_back(R);
   *ticket = R->ticket;
-  return pump(S);
+  // admitted at once: its data went from the caller's arrays straight to staging or the
+  // device; otherwise it keeps copies until memory comes free
+  const pcg_status s = pump(S);
+  if (!S->inflight.count(R->ticket)) own_arrays(R);
+  return s;
 }
 
 pcg_status pcg_poll(pcg_server* S, uint64_t ticket, double* x_out, pcg_result* res) {
@@ -628,10 +864,11 @@ pcg_status pcg_poll(pcg_server* S, uint64_t ticket, double* x_out, pcg_result* r
   if (s != PCG_OK) return s;
   if (R->ring < 0) return PCG_PENDING;
   const unsigned k = (unsigned)(R->ring % S->cap);
-  cuda::atomic_ref<unsigned, cuda::thread_scope_system> d(S->done[k]);
+  Lane& L = S->lane[R->lane];
+  cuda::atomic_ref<unsigned, cuda::thread_scope_system> d(L.done[k]);
   if (d.load(cuda::memory_order_acquire) == 0) return PCG_PENDING;
-  const BatchOut o = S->results[k];
-  const WorkItem& w = S->items[k];
+  const BatchOut o = L.results[k];
+  const WorkItem& w = L.items[k];
   if (x_out && cudaMemcpyAsync(x_out, w.vec.x, (size_t)R->n * 8, cudaMemcpyDeviceToHost, S->cstream) != cudaSuccess)
     return PCG_ECUDA;
   if (cudaStreamSynchronize(S->cstream) != cudaSuccess) return PCG_ECUDA;
@@ -643,7 +880,7 @@ pcg_status pcg_poll(pcg_server* S, uint64_t ticket, double* x_out, pcg_result* r
     res->final_rec_relres = NAN;
   }
   arena_free(S, R->arena_off, R->bytes);
-  S->occupied[k] = 0;
+  L.occupied[k] = 0;
   S->inflight.erase(ticket);
   S->all.erase(it);
   delete R;

@@ -191,3 +191,42 @@ def test_submit_ex_rejects_bad_modes(B):
             srv.submit(S.laplacian_2d(8), np.ones(64), flags=0x4000)
         with pytest.raises(C.PcgError):
             srv.submit(S.laplacian_2d(8), np.ones(64), precision=9)
+
+
+def dense_rows_sdd(n, per_row, seed):
+    """SDD CSR with many entries per row (a request whose staging is large)."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(seed)
+    rows = np.repeat(np.arange(n), per_row)
+    cols = rng.integers(0, n, size=rows.size)
+    keep = rows != cols
+    U = sp.coo_matrix((-rng.random(keep.sum()), (rows[keep], cols[keep])), shape=(n, n)).tocsr()
+    A = (U + U.T).tocsr()
+    A.sum_duplicates()
+    d = np.asarray(np.abs(A).sum(axis=1)).ravel() * 1.01 + 1e-3
+    A = (A + sp.diags(d)).tocsr()
+    A.sort_indices()
+    return S.Problem(S.CSR32, row_ptr=A.indptr.astype(np.int32), col=A.indices.astype(np.int32),
+                     val=A.data.astype(np.float64), n_csr=n)
+
+
+def test_waiting_request_keeps_its_own_copy(B):
+    """A request that has to wait for memory copies its arrays at submission: the caller may
+    overwrite them at once.  A request whose host data is too large for the staging ring takes
+    the direct path.  Both results solve the systems as submitted."""
+    import copy
+    first = S.laplacian_2d(400, 400)                   # 10.3 MB of arena, staged
+    big = dense_rows_sdd(10000, 60, 5)                 # 14.4 MB of arena, 13.9 MB of host data > 12 MB ring
+    b1, b2 = S.normal(90, first.n), S.normal(91, big.n)
+    orig = [(first, b1.copy()), (copy.deepcopy(big), b2.copy())]
+    with B.Server(24 << 20, 4) as srv:
+        t1 = srv.submit(first, b1, tol=1e-10)
+        t2 = srv.submit(big, b2, tol=1e-10)            # waits: both do not fit in 24 MB
+        b1[:] = 7.0                                    # the caller reuses its buffers
+        b2[:] = -3.0
+        big.val[:] = 1.0
+        r1 = wait(srv, t1)
+        r2 = wait(srv, t2)
+    for (P, b), r in zip(orig, (r1, r2)):
+        assert r[0] == B.PCG_OK
+        assert np.linalg.norm(b - oracle.apply(P, r[1])) <= 2e-10 * np.linalg.norm(b)
