@@ -242,10 +242,10 @@ def varcoef_measure(pkg, S) -> dict:
     return out
 
 
-def serving_trace(nreq: int, rate: float, seed: int = 0):
+def serving_trace(nreq: int, rate: float, seed: int = 0, n_max_exp: float = 5.0):
     """Seeded request stream: Poisson arrivals at `rate` per second; n log-uniform in
-    [1e3, 1e5]; half stencils (2D/3D unscaled Laplacians), half random SDD CSR (7-27 entries
-    per row, off-diagonals U[-1,0]); tolerance log-uniform in [1e-10, 1e-6]; b ~ N(0,1)."""
+    [1e3, 10^n_max_exp]; half stencils (2D/3D unscaled Laplacians), half random SDD CSR (7-27
+    entries per row, off-diagonals U[-1,0]); tolerance log-uniform in [1e-10, 1e-6]; b ~ N(0,1)."""
     import numpy as np
     import synthetic as S
     u = S.uniform01(seed, 4 * nreq).reshape(nreq, 4)
@@ -253,7 +253,7 @@ def serving_trace(nreq: int, rate: float, seed: int = 0):
     arrive = np.cumsum(gaps)
     reqs = []
     for i in range(nreq):
-        n = int(10 ** (3 + 2 * u[i, 1]))
+        n = int(10 ** (3 + (n_max_exp - 3) * u[i, 1]))
         if u[i, 2] < 0.25:
             side = max(int(round(n ** 0.5)), 4)
             P = S.laplacian_2d(side)
@@ -294,7 +294,7 @@ def serve_stream(pkg, reqs, flags: int, precision: int):
     return lat, span
 
 
-def serving_measure(pkg, nreq: int, rate: float, tol=None) -> dict:
+def serving_measure(pkg, nreq: int, rate: float, tol=None, n_max_exp: float = 5.0) -> dict:
     """p50/p99 latency and solves/s of the request stream through the continuous-batching
     server, in FP64 (M = I) and in mixed precision with FP64 refinement and Jacobi M^-1, against
     the same stream served one request at a time by plain FP64 solves of the single-system
@@ -302,11 +302,11 @@ def serving_measure(pkg, nreq: int, rate: float, tol=None) -> dict:
     the trace's own."""
     import numpy as np
     from paper_1706_05988_gb300 import pcg as C
-    reqs = serving_trace(nreq, rate)
+    reqs = serving_trace(nreq, rate, n_max_exp=n_max_exp)
     if tol is not None:
         reqs = [(a, P, b, tol) for a, P, b, _ in reqs]
     tol_text = "tol log-uniform [1e-10, 1e-6]" if tol is None else f"tol {tol:g} for every request"
-    out = {"workload": f"{nreq} requests, Poisson arrivals {rate:g}/s, n log-uniform [1e3, 1e5], half 2D/3D "
+    out = {"workload": f"{nreq} requests, Poisson arrivals {rate:g}/s, n log-uniform [1e3, 1e{n_max_exp:g}], half 2D/3D "
                        f"Laplacian stencils, half random SDD CSR (7-27 nnz/row), {tol_text}"}
 
     def summary(lat, span):
@@ -484,8 +484,9 @@ def run_ours(args):
 
     serving = serving_1e8 = None
     if not args.no_serving:
-        serving = serving_measure(pkg, args.serving_requests, args.serving_rate)
-        serving_1e8 = serving_measure(pkg, args.serving_requests, args.serving_rate, tol=1e-8)
+        serving = serving_measure(pkg, args.serving_requests, args.serving_rate, n_max_exp=args.serving_n_max_exp)
+        serving_1e8 = serving_measure(pkg, args.serving_requests, args.serving_rate, tol=1e-8,
+                                      n_max_exp=args.serving_n_max_exp)
 
     # the same workload as CSR (int32 indices): config's second form, one timed step
     csr = None
@@ -591,6 +592,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serving-requests", type=int, default=400)
     ap.add_argument("--serving-rate", type=float, default=2000.0, help="Poisson arrival rate, requests/s")
+    ap.add_argument("--serving-n-max-exp", type=float, default=5.0,
+                    help="serving requests have n log-uniform in [1e3, 10^this] (config 5 goes to 7)")
     ap.add_argument("--size", type=int, default=N_SIDE, help="grid side (default: the 256^3 workload)")
     args = ap.parse_args()
     if args.profile_case:

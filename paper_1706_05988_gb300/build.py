@@ -64,7 +64,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
     tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.check_call([nvcc, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", tmp, *objs])
+    subprocess.check_call([nvcc, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", tmp, *objs,
+                           "-lpthread"])
     os.replace(tmp, LIB)
     return LIB
 

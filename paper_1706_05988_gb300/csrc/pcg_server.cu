@@ -15,12 +15,15 @@
 #include <math.h>
 
 #include <algorithm>
+#include <chrono>
+#include <condition_variable>
 #include <deque>
 #include <map>
 #include <mutex>
 #include <atomic>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <vector>
 
 #define PCG_KERNELS_IMPL
@@ -234,6 +237,13 @@ struct Request {
   long long ring = -1;              // work-item index (in its lane's ring) once published
   int lane = 0;
   WorkItem item;                    // filled at admission, published when its copies are done
+  uint32_t flags = 0;
+  int precision = PCG_FP64;
+  // device lane: the whole GPU, the single-system solver, a host worker thread
+  bool device = false, device_done = false;
+  std::vector<double> x_host;
+  pcg_result device_res{};
+  pcg_status device_status = PCG_OK;
   cudaEvent_t uploaded = nullptr;   // staged admission: the copies' completion
   size_t stage_off = 0, stage_end = 0;
 };
@@ -286,6 +296,10 @@ constexpr int kLanes = 2;
 constexpr long long kLargeN = 32768;           // n at and above: the large lane
 constexpr int kLaneCluster[kLanes] = {2, 8};
 constexpr int kLargeLaneClusters = 16;         // clusters of the large lane (8 blocks each)
+// n at and above: the device lane.  Such a request needs the whole GPU's bandwidth, which
+// no cluster has: the lanes finish their current requests and exit, the request runs on
+// the single-system solver, and the lanes are relaunched.
+constexpr long long kDeviceN = 1LL << 19;
 
 struct Lane {
   int csize = 2, clusters = 0;
@@ -316,6 +330,12 @@ struct pcg_server {
   std::map<size_t, size_t> free_blocks;   // offset -> size (first fit, coalesced)
   Lane lane[kLanes];
   cudaStream_t cstream = nullptr;   // copies
+  // device lane
+  std::thread worker;
+  std::condition_variable cv;
+  std::deque<Request*> device_queue;
+  bool quit = false, device_busy = false;
+  pcg_status worker_error = PCG_OK;
   uint64_t next_ticket = 1;
   std::deque<Request*> waiting;                 // not yet admitted
   std::deque<Request*> uploading;               // admitted, copies in flight, not yet published
@@ -637,6 +657,7 @@ pcg_status pump(pcg_server* S) {
       publish(S, R);
     }
   }
+  if (S->device_busy) return PCG_OK;   // the lanes stay down while the device lane runs
   for (Lane& L : S->lane) {
     cuda::atomic_ref<unsigned, cuda::thread_scope_system> live(L.sh->live);
     if (L.published > L.sh->claimed && live.load(cuda::memory_order_acquire) == 0) {
@@ -647,6 +668,54 @@ pcg_status pump(pcg_server* S) {
     }
   }
   return PCG_OK;
+}
+
+// The device lane's host thread: for each request, drains the lanes (their clusters
+// finish what they hold and exit; every wait of theirs is bounded), solves the request
+// with the single-system solver on the whole GPU, then lets pump() relaunch the lanes.
+void device_worker(pcg_server* S) {
+  cudaSetDevice(S->device);
+  std::unique_lock<std::mutex> lk(S->mu);
+  for (;;) {
+    S->cv.wait(lk, [&] { return S->quit || !S->device_queue.empty(); });
+    if (S->quit) return;
+    Request* R = S->device_queue.front();
+    S->device_queue.pop_front();
+    S->device_busy = true;
+    for (Lane& L : S->lane) {
+      cuda::atomic_ref<unsigned, cuda::thread_scope_system> stop(L.sh->stop);
+      stop.store(1u, cuda::memory_order_release);
+    }
+    lk.unlock();
+    for (Lane& L : S->lane) {
+      cuda::atomic_ref<unsigned, cuda::thread_scope_system> live(L.sh->live);
+      while (live.load(cuda::memory_order_acquire) != 0) std::this_thread::sleep_for(std::chrono::microseconds(50));
+      cudaStreamSynchronize(L.kstream);
+    }
+    pcg_matrix A = R->A;
+    A.row_ptr = R->row_ptr.empty() ? nullptr : R->row_ptr.data();
+    A.col = R->col.empty() ? nullptr : R->col.data();
+    A.val = R->val.empty() ? nullptr : R->val.data();
+    A.diag = R->diag.empty() ? nullptr : R->diag.data();
+    A.ax = R->ax.empty() ? nullptr : R->ax.data();
+    A.ay = R->ay.empty() ? nullptr : R->ay.data();
+    A.az = R->az.empty() ? nullptr : R->az.data();
+    R->x_host.assign((size_t)R->n, 0.0);
+    pcg_ctx* c = nullptr;
+    pcg_status st = pcg_create(&A, R->flags, &c);
+    if (st == PCG_OK) {
+      st = pcg_solve(c, R->b.data(), nullptr, R->method, R->method == PCG_SPCG ? R->sigma : 0.0, R->tol, R->maxit,
+                     R->precision, R->x_host.data(), &R->device_res);
+      pcg_destroy(c);
+    }
+    lk.lock();
+    R->device_status = st;
+    R->device_done = true;
+    release_arrays(R);
+    S->device_busy = false;
+    const pcg_status s = pump(S);     // the lanes come back for published work
+    if (s != PCG_OK) S->worker_error = s;
+  }
 }
 
 }  // namespace
@@ -709,12 +778,25 @@ pcg_status pcg_server_create(size_t hbm_budget_bytes, int32_t max_slots, pcg_ser
     if (cudaMemset(L.d_claim, 0, 2 * sizeof(unsigned)) != cudaSuccess) return bail(PCG_ECUDA);
     if (cudaStreamCreateWithFlags(&L.kstream, cudaStreamNonBlocking) != cudaSuccess) return bail(PCG_ECUDA);
   }
+  try {
+    S->worker = std::thread(device_worker, S);
+  } catch (...) {
+    return bail(PCG_ENOMEM);
+  }
   *out = S;
   return PCG_OK;
 }
 
 void pcg_server_destroy(pcg_server* S) {
   if (!S) return;
+  if (S->worker.joinable()) {
+    {
+      std::lock_guard<std::mutex> lock(S->mu);
+      S->quit = true;
+    }
+    S->cv.notify_all();
+    S->worker.join();
+  }
   for (Lane& L : S->lane) {
     if (L.sh) {
       cuda::atomic_ref<unsigned, cuda::thread_scope_system> stop(L.sh->stop);
@@ -833,6 +915,23 @@ pcg_status pcg_submit_ex(pcg_server* S, const pcg_matrix* A, const double* b, do
   R->b_src = b;
   R->bytes = request_bytes(*R);
   R->lane = n >= kLargeN ? 1 : 0;
+  R->flags = flags;
+  R->precision = precision;
+  if (n >= kDeviceN) {
+    R->device = true;
+    own_arrays(R);                     // solved later by the device lane's thread
+    std::lock_guard<std::mutex> lock(S->mu);
+    if (S->worker_error != PCG_OK) {
+      delete R;
+      return S->worker_error;
+    }
+    R->ticket = S->next_ticket++;
+    S->all[R->ticket] = R;
+    S->device_queue.push_back(R);
+    *ticket = R->ticket;
+    S->cv.notify_one();
+    return PCG_OK;
+  }
   std::lock_guard<std::mutex> lock(S->mu);
   if (R->bytes > S->budget) {
     delete R;
@@ -862,6 +961,22 @@ pcg_status pcg_poll(pcg_server* S, uint64_t ticket, double* x_out, pcg_result* r
   if (cudaSetDevice(S->device) != cudaSuccess) return PCG_ECUDA;
   pcg_status s = pump(S);
   if (s != PCG_OK) return s;
+  if (R->device) {
+    if (!R->device_done) return PCG_PENDING;
+    const pcg_status st = R->device_status;
+    if (st == PCG_OK || st == PCG_ENOTCONV || st == PCG_EBREAKDOWN) {
+      if (x_out) memcpy(x_out, R->x_host.data(), (size_t)R->n * 8);
+      if (res) {
+        res->iters = R->device_res.iters;
+        res->status = st;
+        res->final_true_relres = R->device_res.final_true_relres;
+        res->final_rec_relres = R->device_res.final_rec_relres;
+      }
+    }
+    S->all.erase(it);
+    delete R;
+    return st;
+  }
   if (R->ring < 0) return PCG_PENDING;
   const unsigned k = (unsigned)(R->ring % S->cap);
   Lane& L = S->lane[R->lane];
@@ -892,7 +1007,7 @@ pcg_status pcg_poll(pcg_server* S, uint64_t ticket, double* x_out, pcg_result* r
 pcg_status pcg_server_stats(pcg_server* S, int64_t* waiting, int64_t* inflight, size_t* free_bytes) {
   if (!S) return PCG_EINVAL;
   std::lock_guard<std::mutex> lock(S->mu);
-  if (waiting) *waiting = (int64_t)S->waiting.size();
+  if (waiting) *waiting = (int64_t)(S->waiting.size() + S->device_queue.size());
   if (inflight) *inflight = (int64_t)S->inflight.size();
   if (free_bytes) {
     size_t f = 0;

@@ -230,3 +230,23 @@ def test_waiting_request_keeps_its_own_copy(B):
     for (P, b), r in zip(orig, (r1, r2)):
         assert r[0] == B.PCG_OK
         assert np.linalg.norm(b - oracle.apply(P, r[1])) <= 2e-10 * np.linalg.norm(b)
+
+
+def test_device_lane_requests(B):
+    """Requests of n >= 2^19 run on the whole GPU through the single-system solver while the
+    cluster lanes pause; small requests submitted around them still complete, and every
+    result solves its system."""
+    big3d = S.laplacian_3d(81)                                   # n = 531,441
+    big2d = S.varcoef_2d(800, 700, lo_exp=-1.0, hi_exp=1.0, seed=3)   # n = 560,000
+    small = [S.laplacian_2d(40, 30), random_sdd(2000, 7), S.laplacian_3d(15)]
+    reqs = [(big3d, S.normal(70, big3d.n), 0, B.PCG_FP64), (small[0], S.normal(71, small[0].n), 0, B.PCG_FP64),
+            (big2d, S.normal(72, big2d.n), B.PCG_JACOBI, B.PCG_MIXED_IR),
+            (small[1], S.normal(73, small[1].n), B.PCG_JACOBI, B.PCG_MIXED_IR),
+            (small[2], S.normal(74, small[2].n), 0, B.PCG_FP64)]
+    with B.Server(256 << 20, 8) as srv:
+        tickets = [srv.submit(P, b, tol=1e-8, flags=fl, precision=pr) for P, b, fl, pr in reqs]
+        out = [wait(srv, t, timeout=120.0) for t in tickets]
+    for (P, b, fl, pr), r in zip(reqs, out):
+        assert r[0] == B.PCG_OK, r[0]
+        tr = np.linalg.norm(b - oracle.apply(P, r[1])) / np.linalg.norm(b)
+        assert tr <= (1e-8 if pr == B.PCG_MIXED_IR else 3e-8) and abs(tr - r[3]) <= 1e-3 * tr + 1e-15, (tr, r[3])
