@@ -249,7 +249,11 @@ void pcg_batch_destroy(pcg_batch *batch);
  * two such kernels side by side on a fixed split of the GPU: requests with
  * n < 32,768 go to one with many clusters of 2 blocks, larger requests to one with
  * 16 clusters of 8 blocks (a large request on a small cluster would set the tail
- * latency).  Host data of an admitted request is packed into a pinned staging ring
+ * latency).  Requests with n >= 524,288 are solved one at a time on the whole GPU by
+ * pcg_create/pcg_solve from a host thread of the server, while both kernels pause
+ * (they finish what they hold, exit, and are relaunched afterwards); their device
+ * memory is allocated outside the arena.  Host data of an admitted request is packed
+ * into a pinned staging ring
  * and copied without blocking; a request is published to its kernel when its copies
  * are done.  A request's arithmetic is fixed by its own cluster, so its result does
  * not depend on what else runs.  With no work for 20 ms the kernel
