@@ -253,12 +253,12 @@ void pcg_batch_destroy(pcg_batch *batch);
  * pcg_create/pcg_solve from a host thread of the server, while both kernels pause
  * (they finish what they hold, exit, and are relaunched afterwards); their device
  * memory is allocated outside the arena.  Host data of an admitted request is packed
- * into a pinned staging ring
- * and copied without blocking; a request is published to its kernel when its copies
- * are done.  A request's arithmetic is fixed by its own cluster, so its result does
- * not depend on what else runs.  With no work for 20 ms the kernel
- * exits and is relaunched by the next submit or poll.  The server is internally
- * synchronised (calls may come from several host threads). */
+ * into a pinned staging ring and copied without blocking; a request is published to
+ * its kernel when its copies are done.  A request's arithmetic is fixed by its own
+ * cluster (or by the single-system solver), so its result does not depend on what
+ * else runs.  With no work for 20 ms a kernel exits and is relaunched by the next
+ * submit or poll.  The server is internally synchronised (calls may come from several
+ * host threads). */
 typedef struct pcg_server pcg_server;
 
 /* max_slots >= 1 requests in flight at once; hbm_budget_bytes >= 1 MiB.
