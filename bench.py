@@ -164,32 +164,35 @@ def cpu_oracle_rate(P, b, iters: int) -> tuple[float, float]:
     return iters / dt, dt
 
 
-def batch_measure(pkg, S, nsys: int, seed: int = 0) -> dict:
-    """Solves/s of nsys 2D FV systems (sides U{32..128}, kappa = 10^U[-2,2] per cell, b ~ N(0,1),
-    tol 1e-8) in one batched launch, in two forms: FP64 shifted p-CG (M = I, sigma = half the median
-    diagonal) and mixed precision with FP64 refinement and Jacobi M^-1 (sigma = 1); against plain FP64
-    solves one at a time through the single-system entry point (sampled), all through host buffers."""
+def batch_measure(pkg, S, nsys: int, side_hi: int, forms=("fp64_jacobi", "mixed_jacobi"), seed: int = 0) -> dict:
+    """Solves/s of nsys 2D FV systems (sides U{32..side_hi}, kappa = 10^U[-2,2] per cell, b ~ N(0,1),
+    tol 1e-8) in one batched launch, in the given forms: `fp64` (M = I, sigma = half the median
+    diagonal), `fp64_jacobi` and `mixed_jacobi` (Jacobi M^-1, sigma = 1; mixed precision with FP64
+    refinement); against plain FP64 solves one at a time through the single-system entry point
+    (a sample of 16 systems), all through host buffers."""
     import numpy as np
     import torch
     from paper_1706_05988_gb300 import pcg as C
     rng = np.random.default_rng(seed)
-    sides = rng.integers(32, 129, size=nsys)
+    sides = rng.integers(32, side_hi + 1, size=nsys)
     probs = [S.varcoef_2d(int(L), int(L), seed=seed + i) for i, L in enumerate(sides)]
     bs = [S.normal(1000 + i, P.n) for i, P in enumerate(probs)]
     sig_plain = [0.5 * float(np.median(P.diag)) for P in probs]
-    out = {"workload": f"{nsys} 2D variable-coefficient 5-point systems, sides U{{32..128}}, kappa 10^U[-2,2] "
+    out = {"workload": f"{nsys} 2D variable-coefficient 5-point systems, sides U{{32..{side_hi}}}, kappa 10^U[-2,2] "
                        "per cell, b ~ N(0,1), tol 1e-8"}
-    for name, flags, prec, sig in (("fp64", 0, C.PCG_FP64, sig_plain),
-                                   ("mixed_jacobi", pkg.PCG_JACOBI, C.PCG_MIXED_IR, [1.0] * nsys)):
+    kinds = {"fp64": (0, C.PCG_FP64, sig_plain), "fp64_jacobi": (pkg.PCG_JACOBI, C.PCG_FP64, [1.0] * nsys),
+             "mixed_jacobi": (pkg.PCG_JACOBI, C.PCG_MIXED_IR, [1.0] * nsys)}
+    for name in forms:
+        flags, prec, sig = kinds[name]
         with pkg.Batch(probs, flags=flags, precision=prec) as bt:
-            c, _ = bt.autotune(bs, sig, probe_iters=100)
+            c, _ = bt.autotune(bs, sig, probe_iters=50)
             bt.solve(bs, sig, tol=1e-8, maxit=100000)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             _, it, st, tr = bt.solve(bs, sig, tol=1e-8, maxit=100000)
             torch.cuda.synchronize()
             tb = time.perf_counter() - t0
-            out[name] = {"solves_per_s": nsys / tb, "kernel_ms": bt.last_kernel_ms(), "cluster_size": c,
+            out[name] = {"solves_per_s": nsys / tb, "kernel_ms": bt.last_kernel_ms(), "uniform_cluster_size": c,
                          "converged": int(np.sum(st == 0)), "max_true_relres": float(np.max(tr)),
                          "mean_iters": float(np.mean(it))}
     k = min(nsys, 16)
@@ -205,8 +208,8 @@ def batch_measure(pkg, S, nsys: int, seed: int = 0) -> dict:
             t1 += time.perf_counter() - t0
     one_rate = k / t1
     out["one_at_a_time_fp64"] = {"solves_per_s": one_rate, "sample": int(k)}
-    out["speedup_fp64"] = out["fp64"]["solves_per_s"] / one_rate
-    out["speedup_mixed_jacobi"] = out["mixed_jacobi"]["solves_per_s"] / one_rate
+    for name in forms:
+        out["speedup_" + name] = out[name]["solves_per_s"] / one_rate
     return out
 
 
@@ -476,7 +479,7 @@ def run_ours(args):
     # batch of independent 2D variable-coefficient systems in one persistent launch vs one at a time
     batch = None
     if not args.no_batch:
-        batch = batch_measure(pkg, S, args.batch_systems)
+        batch = batch_measure(pkg, S, args.batch_systems, args.batch_side_max)
 
     varcoef = None
     if not args.no_varcoef:
@@ -588,7 +591,8 @@ def main():
     ap.add_argument("--no-persistent", action="store_true", help="skip the persistent-kernel measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve measurement")
     ap.add_argument("--no-varcoef", action="store_true", help="skip the 128^3 variable-coefficient measurement")
-    ap.add_argument("--batch-systems", type=int, default=128, help="systems in the batched-solve measurement")
+    ap.add_argument("--batch-systems", type=int, default=512, help="systems in the batched-solve measurement")
+    ap.add_argument("--batch-side-max", type=int, default=512, help="batched systems have sides U{32..this}")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serving-requests", type=int, default=400)
     ap.add_argument("--serving-rate", type=float, default=2000.0, help="Poisson arrival rate, requests/s")
