@@ -42,9 +42,9 @@ __device__ __forceinline__ void solve_one(cg::cluster_group& cl, double (*part)[
   if constexpr (MODE == BM_FP64) cluster_solve<F>(cl, part, slot, d, V, prm.tol, prm.maxit, res);
   if constexpr (MODE == BM_JAC) cluster_solve_jac<F>(cl, part, slot, d, V, prm.tol, prm.maxit, res);
   if constexpr (MODE == BM_MX)
-    cluster_solve_mx<F, false>(cl, part, slot, d, V, prm.tol, prm.maxit, prm.eta, prm.max_restarts, res);
+    cluster_solve_mx_auto<F, false>(cl, part, slot, d, V, prm.tol, prm.maxit, prm.eta, prm.max_restarts, res);
   if constexpr (MODE == BM_MXJ)
-    cluster_solve_mx<F, true>(cl, part, slot, d, V, prm.tol, prm.maxit, prm.eta, prm.max_restarts, res);
+    cluster_solve_mx_auto<F, true>(cl, part, slot, d, V, prm.tol, prm.maxit, prm.eta, prm.max_restarts, res);
 }
 
 template <int F, int MODE>

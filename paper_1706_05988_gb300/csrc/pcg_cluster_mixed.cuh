@@ -11,32 +11,19 @@
 
 namespace pcgk {
 
-template <int F>
-struct FamilyOp32;
-template <>
-struct FamilyOp32<0> {
-  using T = StencilOp32<2, false, 1>;
+// The binary32 operator with V unknowns per thread (stencils; CSR rows stay one per thread).
+template <int F, int V>
+struct FamilyOp32V {
+  using T = StencilOp32<(F >= 2 ? 3 : 2), (F == 1 || F == 3), V>;
 };
-template <>
-struct FamilyOp32<1> {
-  using T = StencilOp32<2, true, 1>;
-};
-template <>
-struct FamilyOp32<2> {
-  using T = StencilOp32<3, false, 1>;
-};
-template <>
-struct FamilyOp32<3> {
-  using T = StencilOp32<3, true, 1>;
-};
-template <>
-struct FamilyOp32<4> {
+template <int V>
+struct FamilyOp32V<4, V> {
   using T = CsrOp32;
 };
 
-template <int F>
-__device__ __forceinline__ typename FamilyOp32<F>::T make_op32(const BatchSys& d) {
-  typename FamilyOp32<F>::T o;
+template <int F, int V = 1>
+__device__ __forceinline__ typename FamilyOp32V<F, V>::T make_op32(const BatchSys& d) {
+  typename FamilyOp32V<F, V>::T o;
   if constexpr (F == 4) {
     o.n = d.n;
     o.row_ptr = d.row_ptr;
@@ -213,15 +200,16 @@ __device__ __forceinline__ void cluster_solve_jac(cg::cluster_group& cl, double 
 // binary64 and restarts Algorithm 3 from x once the inner residual ||r_i|| reaches
 // max(eta * true residual, tol ||b|| / 2); the solve ends when the true residual reaches
 // tol ||b||, when a restart does not lower it (reported as maxit), or at maxit.
-template <int F, bool JAC>
+// VW: unknowns per thread in the binary32 sweeps (1, 2 or 4; a stencil's nx must be a multiple).
+template <int F, bool JAC, int VW = 1>
 __device__ __forceinline__ void cluster_solve_mx(cg::cluster_group& cl, double (*part)[4], int& slot,
                                                  const BatchSys& d, const BatchVecs& V, double tol, int maxit,
                                                  double eta, int max_restarts, BatchOut& res) {
   using Op = typename FamilyOp<F>::T;
-  using Op32 = typename FamilyOp32<F>::T;
+  using Op32 = typename FamilyOp32V<F, VW>::T;
   const unsigned rank = cl.block_rank(), C = cl.num_blocks();
   const Op op = make_op<F>(d);
-  const Op32 op32 = make_op32<F>(d);
+  const Op32 op32 = make_op32<F, VW>(d);
   const double sigma = d.sigma;
   const long long off = d.off;
   const double* b = V.b + off;
@@ -336,46 +324,69 @@ __device__ __forceinline__ void cluster_solve_mx(cg::cluster_group& cl, double (
       double ru = 0.0, wu = 0.0, rn2 = 0.0;
       for (auto q = op32.cursor(first); q.c0 < nc; op32.advance(q, stp32)) {
         const unsigned c = q.c0;
-        float mc[1], nv[1];
+        float mc[VW], nv[VW], wc[VW], zz[VW], ss[VW], pp[VW], w1[VW];
+        double rc[VW], xv[VW];
         op32.apply(JAC ? m : w, q, mc, nv);
-        const float wc = JAC ? w[c] : mc[0];
-        const double rc = r[c];
-        const float zz = fmaf(beta32, zf[c], nv[0]);
-        const float ss = fmaf(beta32, sf[c], wc);
-        zf[c] = zz;
-        sf[c] = ss;
-        const float w1 = fmaf(-alpha32, zz, wc);
-        wn[c] = w1;
         if constexpr (JAC) {
-          const float uc = uf[c];
-          const float tt = fmaf(beta32, tf[c], f32_of(rc));
-          const float pp = fmaf(beta32, pf[c], uc);
-          const float qq = fmaf(beta32, qf[c], mc[0]);
-          x[c] = fma(alpha, f64_of(pp), x[c]);
-          const double rn = fma(-alpha, f64_of(ss), fma(-asg, f64_of(tt), rc));
-          const float un = fmaf(-alpha32, qq, fmaf(-asg32, pp, uc));
-          tf[c] = tt;
-          pf[c] = pp;
-          qf[c] = qq;
-          uf[c] = un;
-          r[c] = rn;
-          mn[c] = d32[c] * w1;
-          const double ud = f64_of(un);
-          ru = fma(rn, ud, ru);
-          wu = fma(f64_of(w1), ud, wu);
-          rn2 = fma(rn, rn, rn2);
+          ldf<VW>(w + c, wc);
         } else {
-          const float pp = fmaf(beta32, pf[c], f32_of(rc));
-          pf[c] = pp;
-          const double pd = f64_of(pp);
-          x[c] = fma(alpha, pd, x[c]);
-          const double rn = fma(-alpha, f64_of(ss), fma(-asg, pd, rc));
-          r[c] = rn;
-          ru = fma(rn, rn, ru);
-          wu = fma(f64_of(w1), rn, wu);
-          rn2 = ru;
+#pragma unroll
+          for (int e = 0; e < VW; ++e) wc[e] = mc[e];
+        }
+        ldf<VW>(zf + c, zz);
+        ldf<VW>(sf + c, ss);
+        ldf<VW>(pf + c, pp);
+        ldd<VW>(r + c, rc);
+        ldd<VW>(x + c, xv);
+        float uu[VW], tt[VW], qq[VW], dd[VW], m1[VW];
+        if constexpr (JAC) {
+          ldf<VW>(uf + c, uu);
+          ldf<VW>(tf + c, tt);
+          ldf<VW>(qf + c, qq);
+          ldf<VW>(d32 + c, dd);
+        }
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+          zz[e] = fmaf(beta32, zz[e], nv[e]);
+          ss[e] = fmaf(beta32, ss[e], wc[e]);
+          w1[e] = fmaf(-alpha32, zz[e], wc[e]);
+          if constexpr (JAC) {
+            tt[e] = fmaf(beta32, tt[e], f32_of(rc[e]));
+            pp[e] = fmaf(beta32, pp[e], uu[e]);
+            qq[e] = fmaf(beta32, qq[e], mc[e]);
+            xv[e] = fma(alpha, f64_of(pp[e]), xv[e]);
+            const double rn = fma(-alpha, f64_of(ss[e]), fma(-asg, f64_of(tt[e]), rc[e]));
+            uu[e] = fmaf(-alpha32, qq[e], fmaf(-asg32, pp[e], uu[e]));
+            rc[e] = rn;
+            m1[e] = dd[e] * w1[e];
+            const double ud = f64_of(uu[e]);
+            ru = fma(rn, ud, ru);
+            wu = fma(f64_of(w1[e]), ud, wu);
+            rn2 = fma(rn, rn, rn2);
+          } else {
+            pp[e] = fmaf(beta32, pp[e], f32_of(rc[e]));
+            const double pd = f64_of(pp[e]);
+            xv[e] = fma(alpha, pd, xv[e]);
+            const double rn = fma(-alpha, f64_of(ss[e]), fma(-asg, pd, rc[e]));
+            rc[e] = rn;
+            ru = fma(rn, rn, ru);
+            wu = fma(f64_of(w1[e]), rn, wu);
+          }
+        }
+        stf<VW>(zf + c, zz);
+        stf<VW>(sf + c, ss);
+        stf<VW>(pf + c, pp);
+        std_<VW>(r + c, rc);
+        std_<VW>(x + c, xv);
+        stf<VW>(wn + c, w1, false);
+        if constexpr (JAC) {
+          stf<VW>(uf + c, uu);
+          stf<VW>(tf + c, tt);
+          stf<VW>(qf + c, qq);
+          stf<VW>(mn + c, m1, false);
         }
       }
+      if constexpr (!JAC) rn2 = ru;
       double t4[3] = {ru, wu, rn2}, o4[3];
       cluster_sum<3>(cl, t4, part, slot, o4);
       slot ^= 1;
@@ -401,6 +412,24 @@ __device__ __forceinline__ void cluster_solve_mx(cg::cluster_group& cl, double (
   res.status = status;
   res.bnorm = bnorm;
   res.true_res = true_res;
+}
+
+// Mixed precision with several unknowns per thread in the binary32 sweeps when the system's
+// row length allows: four with M = I, two with Jacobi (twice the vectors; four would spill
+// under the 128-register cap of two resident blocks).  The batched launch uses this; the
+// serving kernel keeps one per thread, which bounds its size.
+template <int F, bool JAC>
+__device__ __forceinline__ void cluster_solve_mx_auto(cg::cluster_group& cl, double (*part)[4], int& slot,
+                                                      const BatchSys& d, const BatchVecs& V, double tol, int maxit,
+                                                      double eta, int max_restarts, BatchOut& res) {
+  constexpr int W = JAC ? 2 : 4;
+  if constexpr (F != 4) {
+    if (d.nx % W == 0) {
+      cluster_solve_mx<F, JAC, W>(cl, part, slot, d, V, tol, maxit, eta, max_restarts, res);
+      return;
+    }
+  }
+  cluster_solve_mx<F, JAC, 1>(cl, part, slot, d, V, tol, maxit, eta, max_restarts, res);
 }
 
 }  // namespace pcgk

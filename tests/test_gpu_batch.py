@@ -180,3 +180,18 @@ def test_batch_size_classes_after_autotune(B):
             r = one.solve(b, method="spcg", sigma=4.0, tol=1e-9, maxit=20000)
         assert abs(int(i) - r.iters) <= 0.02 * r.iters + 2
         assert np.linalg.norm(b - oracle.apply(P, x)) <= 3e-9 * np.linalg.norm(b)
+
+
+def test_batch_mixed_wide_sweeps(B):
+    """Row lengths that are multiples of 4 and of 2 (the binary32 sweeps then take four or two
+    unknowns per thread) and odd ones in one mixed-precision batch, M = I and Jacobi."""
+    dims = [(64, 40), (66, 31), (45, 45), (128, 17), (30, 30)]
+    probs = [S.varcoef_2d(a, b, seed=60 + i) for i, (a, b) in enumerate(dims)]
+    bs = [S.normal(400 + i, P.n) for i, P in enumerate(probs)]
+    for jac in (False, True):
+        sig = [1.0] * len(probs) if jac else [0.5 * float(np.median(P.diag)) for P in probs]
+        with B.Batch(probs, flags=B.PCG_JACOBI if jac else 0, precision=B.PCG_MIXED_IR) as bt:
+            xs, it, st, tr = bt.solve(bs, sig, tol=1e-8, maxit=50000)
+        for P, b, x, code in zip(probs, bs, xs, st):
+            assert code == B.PCG_OK
+            assert np.linalg.norm(b - oracle.apply(P, x)) <= 1e-8 * np.linalg.norm(b)

@@ -171,7 +171,8 @@ def test_mixed_jacobi_alone_and_in_the_mix(B):
 
 
 def test_served_modes_match_batch(B):
-    """A served request and the same system in a batch run the same per-cluster solver."""
+    """A served request and the same system in a batch run the same per-cluster solver (an odd
+    row length: the batched mixed sweep then also takes one unknown per thread)."""
     P = S.varcoef_2d(45, 38, seed=11)
     b = S.normal(12, P.n)
     for jac, prec in MODES:
