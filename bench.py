@@ -597,7 +597,7 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=400)
     ap.add_argument("--serving-rate", type=float, default=2000.0, help="Poisson arrival rate, requests/s")
     ap.add_argument("--serving-n-max-exp", type=float, default=5.0,
-                    help="serving requests have n log-uniform in [1e3, 10^this] (config 5 goes to 7)")
+                    help="serving requests have n log-uniform in [1e3, 10^this] (the full serving workload goes to 7)")
     ap.add_argument("--size", type=int, default=N_SIDE, help="grid side (default: the 256^3 workload)")
     args = ap.parse_args()
     if args.profile_case:
