@@ -185,6 +185,16 @@ pcg_status pcg_select_sigma(pcg_ctx *ctx, const double *b, int32_t iters, const 
 pcg_status pcg_psi(pcg_ctx *ctx, const double *alpha, const double *beta, int32_t i, const double *grid,
                    int32_t ngrid, double *psi_out);
 
+/* psi_i for variable shifts (Section 4.1): the product of the propagation matrices
+ * P_j(sigma_{j-1}, sigma_j) of Eq. (propmat_varshifted), j = i .. 1, with psi_i the
+ * largest spectral norm of its partial products.  schedules (host) holds nsched
+ * schedules, schedule g at schedules[g * stride ..] with the indexing of
+ * pcg_set_shifts (entry 0 = sigma_{-1}, entry k + 1 = sigma_k); stride >= i + 2.
+ * alpha[0..i], beta[0..i] host; psi_out[nsched] host.  A constant schedule gives
+ * pcg_psi's value.  Errors: PCG_EINVAL for bad sizes or NULL arrays. */
+pcg_status pcg_psi_varsh(pcg_ctx *ctx, const double *alpha, const double *beta, int32_t i,
+                         const double *schedules, int32_t stride, int32_t nsched, double *psi_out);
+
 /* ---- Batches of independent systems (one persistent launch) ------------------
  * Many systems A_k x_k = b_k, each solved by Algorithm 3 (M = I, binary64) with its
  * own shift, advance in one launch: every thread-block cluster takes systems from a

@@ -6,7 +6,8 @@ Section 3.2 of arXiv 1706.05988:
   P_k(sigma)       the 4x4 local error propagation matrix, Eq. (propmat_shifted),
                    built from iteration k's alpha_k, beta_k;
   P_{j,i}(sigma)   = P_i P_{i-1} ... P_j, Eq. (matrix_product);
-  psi_i(sigma)     = max_{1<=j<=i} ||P_{j,i}(sigma)||_2, Eq. (functionpsi).
+  psi_i(sigma)     = max_{1<=j<=i} ||P_{j,i}(sigma)||_2, Eq. (functionpsi);
+  P_k(sigma_{k-1}, sigma_k)  the variable-shift matrix of Section 4.1, Eq. (propmat_varshifted).
 Section 5.1: the shift is chosen a posteriori, minimising psi_i over sigma,
 from the alpha/beta history of the unshifted pipelined CG run.
 
@@ -32,6 +33,28 @@ def psi(alpha, beta, i: int, sigma: float) -> float:
     best = 0.0
     for j in range(i, 0, -1):                 # Q = P_i ... P_j, extended on the right
         Q = Q @ prop_matrix(alpha[j], beta[j], sigma)
+        best = max(best, float(np.linalg.norm(Q, 2)))
+    return best
+
+
+def prop_matrix_var(alpha: float, beta: float, s_prev: float, s_cur: float) -> np.ndarray:
+    """P_k(sigma_{k-1}, sigma_k) of Eq. (propmat_varshifted), Section 4.1: the variable-shift
+    propagation matrix.  Its last row couples the j-gap to g and h through the change of
+    shift; with s_prev == s_cur it is P_k(sigma) of Eq. (propmat_shifted)."""
+    a, b, d = alpha, beta, s_cur - s_prev
+    return np.array([[1.0, -a * b, -a, 0.0],
+                     [0.0, b, 1.0, 0.0],
+                     [0.0, -a * b * s_prev, 1.0 - a * s_prev, -a * b],
+                     [0.0, -b * d, -d, b]])
+
+
+def psi_varsh(alpha, beta, i: int, shifts) -> float:
+    """psi_i for a shift schedule: shifts[0] = sigma_{-1}, shifts[k + 1] = sigma_k, so that
+    P_j = P_j(sigma_{j-1}, sigma_j) = P(alpha_j, beta_j, shifts[j], shifts[j + 1])."""
+    Q = np.eye(4)
+    best = 0.0
+    for j in range(i, 0, -1):
+        Q = Q @ prop_matrix_var(alpha[j], beta[j], shifts[j], shifts[j + 1])
         best = max(best, float(np.linalg.norm(Q, 2)))
     return best
 

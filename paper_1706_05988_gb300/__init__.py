@@ -9,4 +9,4 @@ from .pcg import (METHODS, Batch, Server, PCG_CG, PCG_CSR32, PCG_DEVICE_PTRS, PC
                   PCG_STENCIL_FP64_SUM, Matrix, pcg_apply,
                   PcgError, Solver, SolveResult, lib, pcg_create, pcg_destroy, pcg_kernel_stats,
                   pcg_kernel_stats_reset, pcg_last_error, pcg_psi, pcg_select_sigma, pcg_set_stream, pcg_solve,
-                  pcg_set_param, pcg_set_shifts, pcg_solve_device, pcg_version)
+                  pcg_set_param, pcg_set_shifts, pcg_psi_varsh, pcg_solve_device, pcg_version)

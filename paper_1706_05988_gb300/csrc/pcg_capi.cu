@@ -862,6 +862,42 @@ pcg_status pcg_psi(pcg_ctx* c, const double* alpha, const double* beta, int32_t 
   return PCG_OK;
 }
 
+pcg_status pcg_psi_varsh(pcg_ctx* c, const double* alpha, const double* beta, int32_t i, const double* schedules,
+                         int32_t stride, int32_t nsched, double* psi_out) {
+  if (!c) return PCG_EINVAL;
+  c->err.clear();
+  if (!alpha || !beta || !schedules || !psi_out || i < 1 || nsched < 1 || stride < i + 2)
+    return fail(c, PCG_EINVAL, "bad psi_varsh arguments");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  const long long need = 2LL * (i + 1) + (long long)stride * nsched + nsched;
+  if (need > INT32_MAX) return fail(c, PCG_EINVAL, "psi_varsh arguments too large");
+  if (c->small_cap < need) {
+    if (c->d_small) {
+      cudaFree(c->d_small);
+      c->owned.erase(std::find(c->owned.begin(), c->owned.end(), (void*)c->d_small));
+      c->d_small = nullptr;
+    }
+    void* p;
+    pcg_status s = dev_alloc(c, &p, (size_t)need * sizeof(double));
+    if (s != PCG_OK) return s;
+    c->d_small = (double*)p;
+    c->small_cap = (int)need;
+  }
+  double* da = c->d_small;
+  double* db = da + (i + 1);
+  double* ds = db + (i + 1);
+  double* dp = ds + (size_t)stride * nsched;
+  CUDA_TRY(c, cudaMemcpyAsync(da, alpha, (i + 1) * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(db, beta, (i + 1) * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(ds, schedules, (size_t)stride * nsched * sizeof(double), cudaMemcpyHostToDevice,
+                              c->stream));
+  CUDA_TRY(c, launch_psi_var(da, db, i, ds, stride, nsched, dp, c->stream));
+  ++c->launches;
+  CUDA_TRY(c, cudaMemcpyAsync(psi_out, dp, nsched * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return PCG_OK;
+}
+
 pcg_status pcg_select_sigma(pcg_ctx* c, const double* b, int32_t iters, const double* grid, int32_t ngrid,
                             double* sigma_out, double* psi_out) {
   if (!c) return PCG_EINVAL;

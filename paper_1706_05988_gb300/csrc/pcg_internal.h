@@ -114,6 +114,8 @@ cudaError_t launch_mxj_iter(const OpDesc& op, const Launch& L, const GenVecs& v,
                            double* partials);
 
 // psi_i(sigma) for every shift of sig[ngrid]; alpha/beta device arrays (>= i+1 entries).
+cudaError_t launch_psi_var(const double* alpha, const double* beta, int i, const double* sched, int stride,
+                           int nsched, double* psi, cudaStream_t stream);
 cudaError_t launch_psi(const double* alpha, const double* beta, int i, const double* sig, int ngrid, double* psi,
                        cudaStream_t stream);
 

@@ -99,7 +99,45 @@ __global__ void k_psi(const double* __restrict__ alpha, const double* __restrict
   psi[g] = best;
 }
 
+// Variable shift (Section 4.1): one thread per schedule, P_j(sigma_{j-1}, sigma_j) of
+// Eq. (propmat_varshifted); schedule g holds sigma_{-1}, sigma_0, ... at sched[g * stride + 0, 1, ...].
+__global__ void k_psi_var(const double* __restrict__ alpha, const double* __restrict__ beta, int i,
+                          const double* __restrict__ sched, int stride, int nsched, double* __restrict__ psi) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nsched) return;
+  const double* sh = sched + (long long)g * stride;
+  double Q[4][4];
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) Q[a][b] = a == b ? 1.0 : 0.0;
+  double best = 0.0;
+  for (int j = i; j >= 1; --j) {
+    const double al = alpha[j], be = beta[j], sp = sh[j], ds = sh[j + 1] - sh[j];
+    const double P[4][4] = {{1.0, -al * be, -al, 0.0},
+                            {0.0, be, 1.0, 0.0},
+                            {0.0, -al * be * sp, 1.0 - al * sp, -al * be},
+                            {0.0, -be * ds, -ds, be}};
+    double R[4][4];
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) {
+        double acc = 0.0;
+        for (int k = 0; k < 4; ++k) acc += Q[a][k] * P[k][b];
+        R[a][b] = acc;
+      }
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) Q[a][b] = R[a][b];
+    best = fmax(best, norm2_4x4(Q));
+  }
+  psi[g] = best;
+}
+
 }  // namespace
+
+cudaError_t launch_psi_var(const double* alpha, const double* beta, int i, const double* sched, int stride,
+                           int nsched, double* psi, cudaStream_t stream) {
+  const int block = 64;
+  k_psi_var<<<(nsched + block - 1) / block, block, 0, stream>>>(alpha, beta, i, sched, stride, nsched, psi);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_psi(const double* alpha, const double* beta, int i, const double* sig, int ngrid, double* psi,
                        cudaStream_t stream) {

@@ -82,6 +82,7 @@ def lib() -> ctypes.CDLL:
         L.pcg_apply.argtypes = [vp, vp, vp]
         L.pcg_set_param.argtypes = [vp, i32, f64]
         L.pcg_set_shifts.argtypes = [vp, vp, i32]
+        L.pcg_psi_varsh.argtypes = [vp, vp, vp, i32, vp, i32, i32, vp]
         L.pcg_batch_create.argtypes = [vp, i32, ctypes.c_uint32, ctypes.POINTER(vp)]
         L.pcg_batch_solve.argtypes = [vp, vp, vp, i32, vp, f64, i32, vp, vp, vp]
         L.pcg_batch_autotune.argtypes = [vp, vp, vp, i32, vp, vp]
@@ -106,7 +107,7 @@ def lib() -> ctypes.CDLL:
         L.pcg_version.argtypes = []
         L.pcg_version.restype = ctypes.c_char_p
         for f in ("pcg_create", "pcg_set_stream", "pcg_solve", "pcg_solve_device", "pcg_select_sigma", "pcg_psi",
-                  "pcg_apply", "pcg_true_residual_noalloc", "pcg_set_param", "pcg_set_shifts", "pcg_convert_check",
+                  "pcg_apply", "pcg_true_residual_noalloc", "pcg_set_param", "pcg_set_shifts", "pcg_convert_check", "pcg_psi_varsh",
                   "pcg_batch_create", "pcg_batch_solve", "pcg_batch_autotune", "pcg_batch_set_cluster",
                   "pcg_batch_set_precision", "pcg_batch_set_param", "pcg_batch_last_kernel_ms", "pcg_server_create",
                   "pcg_submit", "pcg_submit_ex", "pcg_poll", "pcg_server_stats",
@@ -167,6 +168,19 @@ def pcg_solve_device(ctx, b, x0, method, sigma, tol, maxit, precision, x_out, re
 
 def pcg_set_param(ctx, param: int, value: float) -> int:
     return lib().pcg_set_param(ctx, param, value)
+
+
+def pcg_psi_varsh(ctx, alpha, beta, i: int, schedules) -> np.ndarray:
+    """psi_i for each row of `schedules` (2D, one shift schedule per row, >= i + 2 columns)."""
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    sch = np.ascontiguousarray(np.atleast_2d(schedules), dtype=np.float64)
+    out = np.zeros(sch.shape[0])
+    s = lib().pcg_psi_varsh(ctx, a.ctypes.data, b.ctypes.data, i, sch.ctypes.data, sch.shape[1], sch.shape[0],
+                            out.ctypes.data)
+    if s != PCG_OK:
+        raise PcgError(s, "pcg_psi_varsh")
+    return out
 
 
 def pcg_set_shifts(ctx, shifts) -> int:

@@ -198,3 +198,26 @@ def test_general_errors(B):
         assert r.status == B.PCG_EINVAL
         r = s.solve(b, method="spcg", maxit=4)
         assert r.status in (B.PCG_OK, B.PCG_ENOTCONV) and r.iters == 4
+
+
+def test_psi_varsh_matches_oracle(B):
+    """psi_i of Section 4.1 (variable shift) on the device against the oracle, for constant,
+    ramped, decaying and jittered schedules over lapl200's history; a constant schedule also
+    equals pcg_psi's constant-shift value."""
+    from oracle import psi as PS
+    from paper_1706_05988_gb300 import pcg as C
+    P, b = S.lapl200()
+    o = oracle.pcg_sh(P, b, sigma=4.0, maxit=301, log_every=0)
+    i = 300
+    k = np.arange(i + 2)
+    scheds = np.stack([np.full(i + 2, 4.0), 4.0 * k / (i + 1), 2.0 + 4.0 * np.exp(-k / 50.0),
+                       4.0 + 0.5 * (S.uniform01(5, i + 2) - 0.5)])
+    with B.Solver(P) as s:
+        g = C.pcg_psi_varsh(s.ctx, o.alpha, o.beta, i, scheds)
+        g4 = C.pcg_psi(s.ctx, o.alpha, o.beta, i, np.array([4.0]))
+    ref = np.array([PS.psi_varsh(o.alpha, o.beta, i, sc) for sc in scheds])
+    assert rel(g, ref) < 1e-9, (g, ref)
+    assert rel(g[:1], g4) < 1e-12
+    with B.Solver(P) as s:
+        with pytest.raises(C.PcgError):
+            C.pcg_psi_varsh(s.ctx, o.alpha, o.beta, i, scheds[:, :i + 1])   # too short a schedule

@@ -295,6 +295,29 @@ def test_psi_closed_form_one_step():
     assert abs(PS.psi(al, be, 1, sigma) - np.sqrt((e + np.sqrt(e * e - 4)) / 2)) < 1e-14
 
 
+def test_psi_varsh_closed_form_one_step():
+    """Variable shift, one step, beta = 0, alpha*sigma_0 = 1 (sigma_0 = sigma_{i-1}): the nonzero part of
+    P is [[1, -c], [0, 1], [0, -d]] in rows 0, 1, 3 and columns 0, 2 (d = sigma_1 - sigma_0), whose
+    largest singular value is sqrt((t + sqrt(t^2 - 4 det)) / 2), t = 2 + c^2 + d^2, det = 1 + d^2."""
+    c, s0, d = 0.3, 1 / 0.3, 0.7
+    al, be = np.array([0.0, c]), np.array([0.0, 0.0])
+    t, det = 2 + c * c + d * d, 1 + d * d
+    want = np.sqrt((t + np.sqrt(t * t - 4 * det)) / 2)
+    assert abs(PS.psi_varsh(al, be, 1, [0.0, s0, s0 + d]) - want) < 1e-14
+    # the change of shift is what couples the j-gap in: with d = 0 it is the constant-shift value
+    e = 2 + c * c
+    assert abs(PS.psi_varsh(al, be, 1, [0.0, s0, s0]) - np.sqrt((e + np.sqrt(e * e - 4)) / 2)) < 1e-14
+
+
+def test_psi_varsh_constant_schedule_is_psi(lapl200_runs):
+    """A constant schedule gives psi_i(sigma) of Eq. (functionpsi) on a real alpha/beta history
+    (lapl200's unshifted pilot run, pinned to the paper's 3.46e2 at sigma = 4 above)."""
+    pcg = lapl200_runs["pcg"]
+    for sigma in (0.0, 2.5, 4.0):
+        sh = np.full(202, sigma)
+        assert abs(PS.psi_varsh(pcg.alpha, pcg.beta, 200, sh) / PS.psi(pcg.alpha, pcg.beta, 200, sigma) - 1) < 1e-12
+
+
 def test_psi_product_order_matters():
     """psi uses P_i ... P_j (newest on the left); the reversed product gives another value,
     so the lapl200 pin above also fixes the order."""
