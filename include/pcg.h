@@ -196,8 +196,8 @@ pcg_status pcg_psi_varsh(pcg_ctx *ctx, const double *alpha, const double *beta, 
                          const double *schedules, int32_t stride, int32_t nsched, double *psi_out);
 
 /* ---- Batches of independent systems (one persistent launch) ------------------
- * Many systems A_k x_k = b_k, each solved by Algorithm 3 (M = I, binary64) with its
- * own shift, advance in one launch: every thread-block cluster takes systems from a
+ * Many systems A_k x_k = b_k, each solved by Algorithm 3 with its own shift (binary64
+ * or mixed precision, M = I or Jacobi), advance in one launch: every thread-block cluster takes systems from a
  * device queue (largest first) and runs all iterations of one system, its blocks
  * sharing the unknowns; the dot products reduce through distributed shared memory
  * and one cluster barrier per iteration replaces the paper's global reduction.
