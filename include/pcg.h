@@ -197,10 +197,11 @@ pcg_status pcg_psi_varsh(pcg_ctx *ctx, const double *alpha, const double *beta, 
 
 /* ---- Batches of independent systems (one persistent launch) ------------------
  * Many systems A_k x_k = b_k, each solved by Algorithm 3 with its own shift (binary64
- * or mixed precision, M = I or Jacobi), advance in one launch: every thread-block cluster takes systems from a
- * device queue (largest first) and runs all iterations of one system, its blocks
- * sharing the unknowns; the dot products reduce through distributed shared memory
- * and one cluster barrier per iteration replaces the paper's global reduction.
+ * or mixed precision, M = I or Jacobi), advance together: every thread-block cluster
+ * takes systems from a device queue (largest first) and runs all iterations of one
+ * system, its blocks sharing the unknowns; the dot products reduce through
+ * distributed shared memory and one cluster barrier per iteration replaces the
+ * paper's global reduction.
  * All systems of a batch share one operator family (2D or 3D stencil, constant or
  * variable coefficients, or CSR) but not their sizes.  Systems are grouped into
  * three size classes (n < 8,192; < 65,536; larger), each with its own queue and
