@@ -29,9 +29,9 @@ StencilOp<DIM, MODE, VEC> make_stencil(const OpDesc& d) {
 }
 
 template <int DIM, class F>
-cudaError_t with_stencil(const OpDesc& d, F&& f) {
+cudaError_t with_stencil(const OpDesc& d, F&& f, int vec) {
   const bool var = d.diag != nullptr;
-  if (op_vec(d) == 2) {
+  if (vec == 2) {
     if (var) return f(make_stencil<DIM, ST_VAR, 2>(d));
     if (d.fixed_sum) return f(make_stencil<DIM, ST_LAP_FIXED, 2>(d));
     return f(make_stencil<DIM, ST_LAP_FP64, 2>(d));
@@ -41,11 +41,13 @@ cudaError_t with_stencil(const OpDesc& d, F&& f) {
   return f(make_stencil<DIM, ST_LAP_FP64, 1>(d));
 }
 
+// vec: unknowns per thread of a stencil operator (default: op_vec)
 template <class F>
-cudaError_t with_op(const OpDesc& d, F&& f) {
+cudaError_t with_op(const OpDesc& d, F&& f, int vec = 0) {
+  if (vec <= 0) vec = op_vec(d);
   switch (d.layout) {
-    case 0: return with_stencil<2>(d, std::forward<F>(f));
-    case 1: return with_stencil<3>(d, std::forward<F>(f));
+    case 0: return with_stencil<2>(d, std::forward<F>(f), vec);
+    case 1: return with_stencil<3>(d, std::forward<F>(f), vec);
     case 2: {
       CsrOp o;
       o.n = d.n;
@@ -126,19 +128,28 @@ cudaError_t with_general(bool jac, bool var, F&& f) {
   return cudaErrorInvalidValue;
 }
 
+// The Jacobi sweeps carry nine vectors: at most PCG_GEN_JAC_MAX_VEC unknowns per thread.
+int gen_vec(const OpDesc& d, bool jac) {
+  const int v = op_vec(d);
+  return jac && v > PCG_GEN_JAC_MAX_VEC ? PCG_GEN_JAC_MAX_VEC : v;
+}
+
 int grid_for_general(const OpDesc& d, bool jac, bool var) {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   int per_sm = 0;
-  with_op(d, [&](auto op) {
-    return with_general<std::decay_t<decltype(op)>>(jac, var, [&](auto K) {
-      per_sm = decltype(K)::blocks_per_sm();
-      return cudaSuccess;
-    });
-  });
+  with_op(
+      d,
+      [&](auto op) {
+        return with_general<std::decay_t<decltype(op)>>(jac, var, [&](auto K) {
+          per_sm = decltype(K)::blocks_per_sm();
+          return cudaSuccess;
+        });
+      },
+      gen_vec(d, jac));
   if (per_sm <= 0) return 0;
-  const long long units = d.n / op_vec(d);
+  const long long units = d.n / gen_vec(d, jac);
   long long g = (long long)sms * per_sm;
   const long long need = (units + kBlock - 1) / kBlock;
   if (need < g) g = need;
@@ -149,17 +160,23 @@ int grid_for_general(const OpDesc& d, bool jac, bool var) {
 
 cudaError_t launch_gen_w0(const OpDesc& d, const Launch& L, const GenVecs& v, State* st, Hist h, double* partials,
                           bool jac, bool var) {
-  return with_op(d, [&](auto op) {
-    return with_general<std::decay_t<decltype(op)>>(jac, var,
-                                                    [&](auto K) { return K.w0(op, L, v, st, h, partials); });
-  });
+  return with_op(
+      d,
+      [&](auto op) {
+        return with_general<std::decay_t<decltype(op)>>(jac, var,
+                                                        [&](auto K) { return K.w0(op, L, v, st, h, partials); });
+      },
+      gen_vec(d, jac));
 }
 cudaError_t launch_gen_iter(const OpDesc& d, const Launch& L, const GenVecs& v, State* st, Hist h, double* partials,
                             bool jac, bool var) {
-  return with_op(d, [&](auto op) {
-    return with_general<std::decay_t<decltype(op)>>(jac, var,
-                                                    [&](auto K) { return K.iter(op, L, v, st, h, partials); });
-  });
+  return with_op(
+      d,
+      [&](auto op) {
+        return with_general<std::decay_t<decltype(op)>>(jac, var,
+                                                        [&](auto K) { return K.iter(op, L, v, st, h, partials); });
+      },
+      gen_vec(d, jac));
 }
 
 int grid_for_persistent(const OpDesc& d) {

@@ -17,6 +17,15 @@
 #pragma once
 #include "pcg_kernels.cuh"
 
+// Resident blocks per SM the general sweep is compiled for (register cap 65536 / (256 * this)).
+#ifndef PCG_GEN_MIN_BLOCKS
+#define PCG_GEN_MIN_BLOCKS 2
+#endif
+// Most unknowns per thread of the Jacobi sweeps (nine vectors per unknown).
+#ifndef PCG_GEN_JAC_MAX_VEC
+#define PCG_GEN_JAC_MAX_VEC 2
+#endif
+
 namespace pcgk {
 
 struct GenVecs {
@@ -137,7 +146,8 @@ __global__ void __launch_bounds__(kBlock) k_gen_w0(Op op, GenVecs v, State* st, 
 
 // One iteration of Algorithm 4 (order of its statement), n = A m fused.
 template <class Op, bool JAC, bool VAR>
-__global__ void __launch_bounds__(kBlock) k_gen_iter(Op op, GenVecs v, State* st, Hist h, double* partials) {
+__global__ void __launch_bounds__(kBlock, PCG_GEN_MIN_BLOCKS) k_gen_iter(Op op, GenVecs v, State* st, Hist h,
+                                                                        double* partials) {
   constexpr int VEC = Op::VEC;
   if (st->status != ST_RUNNING) return;
   const int it = st->iter;
