@@ -76,3 +76,28 @@ def test_argument_errors_without_gpu(libpath):
     assert L.pcg_kernel_stats(None, None, None, None) == B.PCG_EINVAL
     L.pcg_destroy(None)
     assert B.pcg_last_error(None) == "null context"
+
+
+def test_argument_errors_of_the_extensions_without_gpu(libpath):
+    """Jacobi / variable shift / batch / serving / self-check entry points reject bad arguments
+    before touching the device."""
+    from paper_1706_05988_gb300 import pcg as B
+    L = B.lib()
+    vp = ctypes.c_void_p
+    assert L.pcg_set_shifts(None, None, 0) == B.PCG_EINVAL
+    assert L.pcg_psi_varsh(None, None, None, 10, None, 12, 1, None) == B.PCG_EINVAL
+    assert L.pcg_batch_set_precision(None, B.PCG_MIXED_IR) == B.PCG_EINVAL
+    assert L.pcg_batch_set_param(None, B.PCG_PARAM_MIXED_ETA, 0.5) == B.PCG_EINVAL
+    out = vp(1)
+    assert L.pcg_batch_create(None, 1, 0, ctypes.byref(out)) == B.PCG_EINVAL
+    m = B.pcg_matrix()
+    m.layout = B.PCG_STENCIL5_2D
+    m.nx, m.ny, m.nz = 8, 8, 1
+    arr = (B.pcg_matrix * 1)(m)
+    assert L.pcg_batch_create(ctypes.cast(arr, vp), 1, 0x4000, ctypes.byref(out)) == B.PCG_EINVAL
+    t = ctypes.c_uint64()
+    assert L.pcg_submit_ex(None, ctypes.byref(m), None, 1e-8, B.PCG_SPCG, 1.0, 10, 0, B.PCG_FP64,
+                           ctypes.byref(t)) == B.PCG_EINVAL
+    assert L.pcg_server_create(1024, 4, ctypes.byref(out)) == B.PCG_EINVAL       # budget below 1 MiB
+    assert L.pcg_convert_check(None, None, None, None, -1) == B.PCG_EINVAL
+    assert L.pcg_convert_check(None, None, None, None, 0) == B.PCG_OK
