@@ -352,6 +352,10 @@ pcg_status pcg_set_shifts(pcg_ctx *ctx, const double *shifts, int32_t count);
 /* Solver parameters (not part of the paper's method statement).
  *   PCG_PARAM_MIXED_ETA      inner tolerance of PCG_MIXED_IR, in (0, 1); default 2^-10
  *   PCG_PARAM_MAX_RESTARTS   most restarts of one PCG_MIXED_IR solve, >= 1; default 200
+ *   PCG_PARAM_TRUE_TOL       PCG_FP64 solves with res->true_every > 0: also stop once a
+ *                            logged true residual satisfies ||b - A x_i|| <= value ||b||
+ *                            (the true residual is checked every true_every iterations);
+ *                            0 (the default) turns it off
  *   PCG_PARAM_BARRIER_TIMEOUT_MS, PCG_PARAM_TEST_BARRIER_PHANTOMS: see below
  * Errors: PCG_EINVAL for an unknown parameter or a value out of range. */
 #define PCG_PARAM_MIXED_ETA 1
@@ -361,6 +365,7 @@ pcg_status pcg_set_shifts(pcg_ctx *ctx, const double *shifts, int32_t count);
 #define PCG_PARAM_TEST_BARRIER_PHANTOMS 4 /* PCG_PERSISTENT, for tests of the time limit: the
                                             barrier waits for this many arrivals that never
                                             come (0 = off, the default) */
+#define PCG_PARAM_TRUE_TOL 5
 pcg_status pcg_set_param(pcg_ctx *ctx, int32_t param, double value);
 
 /* Kernel accounting of the context since creation (or the last reset):

@@ -43,6 +43,7 @@ struct pcg_ctx {
   int grid_mx[KM_NKINDS] = {0};
   double mx_eta = 0.0009765625;        // 2^-10
   int mx_max_restarts = 200;
+  double true_tol = 0.0;                // PCG_PARAM_TRUE_TOL
   // general iteration (Jacobi M^-1 and/or variable shift)
   double* gen_base = nullptr;           // u, q, p, m (two buffers); t is v.p
   const float* dinv32 = nullptr;        // mixed precision with PCG_JACOBI
@@ -348,6 +349,10 @@ pcg_status pcg_set_param(pcg_ctx* c, int32_t param, double value) {
       if (!(value >= 1.0 && value <= 1e6)) return fail(c, PCG_EINVAL, "max restarts must lie in [1, 1e6]");
       c->mx_max_restarts = (int)value;
       return PCG_OK;
+    case PCG_PARAM_TRUE_TOL:
+      if (!(value >= 0.0) || !isfinite(value)) return fail(c, PCG_EINVAL, "true tolerance must be finite and >= 0");
+      c->true_tol = value;
+      return PCG_OK;
     default:
       return fail(c, PCG_EINVAL, "unknown parameter");
   }
@@ -383,6 +388,7 @@ pcg_status run_solve(pcg_ctx* c, bool has_x0, int method, double sigma, double t
   st.maxit = maxit;
   st.sigma = method == PCG_SPCG ? sigma : 0.0;
   st.tol_abs = tol;   // relative until the residual kernel scales it by ||b||
+  st.tol_true = c->true_tol;
   *c->h_state = st;
   CUDA_TRY(c, cudaMemcpyAsync(c->d_state, c->h_state, sizeof(State), cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(c->d_hist, 0xff, 7 * (size_t)c->hist_cap * sizeof(double), c->stream));  // NaN
@@ -430,7 +436,8 @@ pcg_status run_solve(pcg_ctx* c, bool has_x0, int method, double sigma, double t
   int prof_pairs = 0;
   int chunk = 16;
   while (done < maxit) {
-    const int todo = tol > 0.0 ? std::min(chunk, maxit - done) : maxit - done;
+    const bool poll = tol > 0.0 || (c->true_tol > 0.0 && true_every > 0);   // the solve may stop early
+    const int todo = poll ? std::min(chunk, maxit - done) : maxit - done;
     for (int k = 0; k < todo; ++k) {
       if (cg) {
         CUDA_TRY(c, launch_cg_spmv(c->op, L(K_CG_SPMV), c->v, c->d_state, c->h, c->d_partials));
@@ -451,7 +458,7 @@ pcg_status run_solve(pcg_ctx* c, bool has_x0, int method, double sigma, double t
         ++c->launches;
       }
     }
-    if (tol > 0.0 && done < maxit) {
+    if (poll && done < maxit) {
       CUDA_TRY(c, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(State), cudaMemcpyDeviceToHost, c->stream));
       CUDA_TRY(c, cudaStreamSynchronize(c->stream));
       if (c->h_state->status != ST_RUNNING) break;
@@ -673,6 +680,7 @@ pcg_status run_solve_general(pcg_ctx* c, bool has_x0, const std::vector<double>&
   st.maxit = maxit;
   st.sigma = sh[0];
   st.tol_abs = tol;   // relative until the residual kernel scales it by ||b||
+  st.tol_true = c->true_tol;
   *c->h_state = st;
   CUDA_TRY(c, cudaMemcpyAsync(c->d_state, c->h_state, sizeof(State), cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(c->d_hist, 0xff, 7 * (size_t)c->hist_cap * sizeof(double), c->stream));  // NaN
@@ -693,7 +701,8 @@ pcg_status run_solve_general(pcg_ctx* c, bool has_x0, const std::vector<double>&
   }
   int done = 0, chunk = 16;
   while (done < maxit) {
-    const int todo = tol > 0.0 ? std::min(chunk, maxit - done) : maxit - done;
+    const bool poll = tol > 0.0 || (c->true_tol > 0.0 && true_every > 0);   // the solve may stop early
+    const int todo = poll ? std::min(chunk, maxit - done) : maxit - done;
     for (int k = 0; k < todo; ++k) {
       CUDA_TRY(c, launch_gen_iter(c->op, Lg, g, c->d_state, c->h, c->d_partials, jac, var));
       ++c->launches;
@@ -703,7 +712,7 @@ pcg_status run_solve_general(pcg_ctx* c, bool has_x0, const std::vector<double>&
         ++c->launches;
       }
     }
-    if (tol > 0.0 && done < maxit) {
+    if (poll && done < maxit) {
       CUDA_TRY(c, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(State), cudaMemcpyDeviceToHost, c->stream));
       CUDA_TRY(c, cudaStreamSynchronize(c->stream));
       if (c->h_state->status != ST_RUNNING) break;

@@ -33,6 +33,8 @@ struct State {
   // grid barrier of the persistent kernel
   unsigned int bar_count;
   unsigned int bar_gen;
+  // stop once the logged true residual ||b - A x_i|| <= tol_true ||b|| (0: never)
+  double tol_true;
 };
 
 // Per-iteration histories (device arrays of maxit + 1 entries).

@@ -568,8 +568,11 @@ __global__ void __launch_bounds__(kBlock) k_true_res(Op op, Vecs v, State* st, H
   if (!reduce_last_block<2>(vals, partials, &st->ticket, tot)) return;
   if (threadIdx.x == 0) {
     const int i = st->iter;
-    h.tru[i] = sqrt(tot[0]);
+    const double tr = sqrt(tot[0]);
+    h.tru[i] = tr;
     h.gap[i] = sqrt(tot[1]);
+    // the true-residual stop (checked wherever the true residual is logged)
+    if (st->status == ST_RUNNING && st->tol_true > 0.0 && tr <= st->tol_true * st->bnorm) st->status = ST_CONVERGED;
     st->ticket = 0;
   }
 }

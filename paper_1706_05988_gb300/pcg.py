@@ -30,6 +30,7 @@ PCG_PROFILE = 0x2
 PCG_STENCIL_FP64_SUM = 0x4
 # pcg_set_param parameters
 PCG_PARAM_MIXED_ETA, PCG_PARAM_MAX_RESTARTS, PCG_PARAM_BARRIER_TIMEOUT_MS, PCG_PARAM_TEST_BARRIER_PHANTOMS = 1, 2, 3, 4
+PCG_PARAM_TRUE_TOL = 5
 PCG_PERSISTENT = 0x8
 PCG_JACOBI = 0x10
 

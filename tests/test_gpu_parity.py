@@ -376,3 +376,24 @@ def test_full_size_1000_iterations_properties(B, big):
     bn = np.linalg.norm(b)
     assert np.nanmax(g.gap) / bn < 1e-12
     assert abs(g.final_true_relres - g.final_rec_relres) < 1e-10
+
+
+@pytest.mark.parametrize("method,sigma", [("cg", 0.0), ("spcg", 4.0)])
+def test_true_residual_stop(B, method, sigma):
+    """The 100x100 Poisson run of the accuracy study: at most 2,000 iterations or a true relative
+    residual of 1e-14, checked every iteration (PCG_PARAM_TRUE_TOL); the stop iteration and the
+    final residual follow the oracle's true-residual stop."""
+    from paper_1706_05988_gb300 import pcg as C
+    P, b, _ = S.poisson2d_manufactured(100)
+    with B.Solver(P) as s:
+        assert C.pcg_set_param(s.ctx, C.PCG_PARAM_TRUE_TOL, 1e-14) == C.PCG_OK
+        g = s.solve(b, method=method, sigma=sigma, maxit=2000, true_every=1)
+        assert C.pcg_set_param(s.ctx, C.PCG_PARAM_TRUE_TOL, -1.0) == C.PCG_EINVAL
+    if method == "cg":
+        o = oracle.cg(P, b, maxit=2000, ttol=1e-14, log_every=1)
+    else:
+        o = oracle.pcg_sh(P, b, sigma=sigma, maxit=2000, ttol=1e-14, log_every=1)
+    bn = np.linalg.norm(b)
+    assert o.status == 1 and g.status == B.PCG_OK, (o.status, g.status)
+    assert abs(g.iters - o.iters) <= 2, (g.iters, o.iters)
+    assert g.final_true_relres <= 1e-14 and o.true[-1] / bn <= 1e-14
