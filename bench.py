@@ -454,7 +454,7 @@ def run_ours(args):
 
     # the same step with the persistent cooperative kernel (one launch for all iterations)
     persistent = None
-    if not args.no_persistent:
+    if not args.no_persistent and world == 1:   # side measurements: single-GPU runs only
         with pkg.Solver(P, flags=C.PCG_PROFILE | C.PCG_PERSISTENT) as sp:
             C.pcg_set_stream(sp.ctx, stream.cuda_stream)
             for _ in range(2):
@@ -478,22 +478,22 @@ def run_ours(args):
 
     # batch of independent 2D variable-coefficient systems in one persistent launch vs one at a time
     batch = None
-    if not args.no_batch:
+    if not args.no_batch and world == 1:   # side measurements: single-GPU runs only
         batch = batch_measure(pkg, S, args.batch_systems, args.batch_side_max)
 
     varcoef = None
-    if not args.no_varcoef:
+    if not args.no_varcoef and world == 1:   # side measurements: single-GPU runs only
         varcoef = varcoef_measure(pkg, S)
 
     serving = serving_1e8 = None
-    if not args.no_serving:
+    if not args.no_serving and world == 1:   # side measurements: single-GPU runs only
         serving = serving_measure(pkg, args.serving_requests, args.serving_rate, n_max_exp=args.serving_n_max_exp)
         serving_1e8 = serving_measure(pkg, args.serving_requests, args.serving_rate, tol=1e-8,
                                       n_max_exp=args.serving_n_max_exp)
 
     # the same workload as CSR (int32 indices): config's second form, one timed step
     csr = None
-    if not args.no_csr:
+    if not args.no_csr and world == 1:   # side measurements: single-GPU runs only
         Pc = S.to_csr(P)
         bytes_csr = BYTES_PER_DOF * n + 12 * Pc.nnz + 4 * (n + 1)
         with pkg.Solver(Pc, flags=C.PCG_PROFILE) as sc:
