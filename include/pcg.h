@@ -66,8 +66,10 @@ typedef enum { PCG_FP64 = 0, PCG_MIXED_IR = 1 } pcg_precision;
                                   PCG_JACOBI or a variable shift launch per iteration */
 #define PCG_JACOBI 0x10u      /* preconditioner M^{-1} = diag(A)^{-1} (the paper's JAC, Table 1):
                                   Algorithm 3 with its separate preconditioned recurrences for
-                                  u, q, p (PCG_PCG / PCG_SPCG, in FP64 or PCG_MIXED_IR; host
-                                  arrays only: with PCG_DEVICE_PTRS, PCG_EINVAL) */
+                                  u, q, p (PCG_PCG / PCG_SPCG, in FP64 or PCG_MIXED_IR).
+                                  D^{-1} is formed at creation: on the host from host
+                                  arrays, on the device from PCG_DEVICE_PTRS arrays; a
+                                  non-positive diagonal entry gives PCG_EINVAL */
 #define PCG_STENCIL_FP64_SUM 0x4u  /* constant-coefficient stencils: sum each row with FP64
                                   additions instead of the default fixed-point row sum.
                                   Default: the row C*w_c - sum(neighbours) is summed exactly

@@ -179,7 +179,6 @@ pcg_status pcg_create(const pcg_matrix* A, uint32_t flags, pcg_ctx** out) {
   *out = nullptr;
   if (!A) return PCG_EINVAL;
   if (flags & ~(PCG_DEVICE_PTRS | PCG_PROFILE | PCG_STENCIL_FP64_SUM | PCG_PERSISTENT | PCG_JACOBI)) return PCG_EINVAL;
-  if ((flags & PCG_JACOBI) && (flags & PCG_DEVICE_PTRS)) return PCG_EINVAL;   // the diagonal is read on the host
   OpDesc op{};
   op.layout = A->layout;
   op.fixed_sum = (flags & PCG_STENCIL_FP64_SUM) ? 0 : 1;
@@ -253,7 +252,22 @@ pcg_status pcg_create(const pcg_matrix* A, uint32_t flags, pcg_ctx** out) {
     return bail(PCG_ENOMEM);
   }
   c->h_state = (State*)p;
-  if (flags & PCG_JACOBI) {
+  if ((flags & PCG_JACOBI) && (flags & PCG_DEVICE_PTRS)) {
+    // M^{-1} = diag(A)^{-1}, formed on the device from the caller's device arrays
+    void* p;
+    if ((s = dev_alloc(c, &p, (size_t)n * sizeof(double) + 256)) != PCG_OK) return bail(s);
+    c->d_dinv = (double*)p;
+    int* d_bad = (int*)((char*)p + (size_t)n * sizeof(double));
+    int bad = 0;
+    if (cudaMemsetAsync(d_bad, 0, sizeof(int), c->stream) != cudaSuccess ||
+        launch_jacobi_dinv(c->op, c->d_dinv, d_bad, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+      cudaGetLastError();
+      return bail(fail(c, PCG_ECUDA, "could not form the Jacobi diagonal"));
+    }
+    if (bad) return bail(fail(c, PCG_EINVAL, "PCG_JACOBI needs a positive diagonal"));
+  } else if (flags & PCG_JACOBI) {
     // M^{-1} = diag(A)^{-1}, formed on the host from the operator's description
     std::vector<double> dinv(n);
     bool ok = true;

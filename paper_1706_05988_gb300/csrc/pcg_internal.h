@@ -88,6 +88,8 @@ cudaError_t launch_apply(const OpDesc& op, const Launch& L, const double* x, dou
 
 // General iteration: Jacobi preconditioner and/or variable shift (pcg_general.cuh).
 struct GenVecs;
+// D^{-1} of a matrix whose arrays are on the device; *bad (device) is set for a non-positive diagonal.
+cudaError_t launch_jacobi_dinv(const OpDesc& op, double* dinv, int* bad, cudaStream_t stream);
 // jac: D^{-1} recurrences; var: variable-shift correction terms (at least one is set)
 int grid_for_general(const OpDesc& op, bool jac, bool var);
 cudaError_t launch_gen_w0(const OpDesc& op, const Launch& L, const GenVecs& v, State* st, Hist h, double* partials,
