@@ -66,7 +66,8 @@ typedef enum { PCG_FP64 = 0, PCG_MIXED_IR = 1 } pcg_precision;
                                   PCG_JACOBI or a variable shift launch per iteration */
 #define PCG_JACOBI 0x10u      /* preconditioner M^{-1} = diag(A)^{-1} (the paper's JAC, Table 1):
                                   Algorithm 3 with its separate preconditioned recurrences for
-                                  u, q, p (PCG_PCG / PCG_SPCG, in FP64 or PCG_MIXED_IR).
+                                  u, q, p (PCG_PCG / PCG_SPCG, in FP64 or PCG_MIXED_IR),
+                                  and Algorithm 1 with u = D^{-1} r (PCG_CG, FP64).
                                   D^{-1} is formed at creation: on the host from host
                                   arrays, on the device from PCG_DEVICE_PTRS arrays; a
                                   non-positive diagonal entry gives PCG_EINVAL */

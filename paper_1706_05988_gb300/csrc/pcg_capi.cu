@@ -765,8 +765,9 @@ pcg_status solve_common(pcg_ctx* c, const double* b, const double* x0, int32_t m
     for (int k = 1; k <= maxit; ++k) var = var || sh[k] != sh[0];
     sigma = sh[0];
   }
-  const bool general = c->d_dinv != nullptr || var;
-  if (general && method == PCG_CG) return fail(c, PCG_ENOTIMPL, "PCG_JACOBI is implemented for Algorithms 2 and 3");
+  // Algorithm 1 takes M^{-1} in its own kernels; Algorithms 2-4 with M^{-1} or a variable shift
+  // run the general sweeps
+  const bool general = method != PCG_CG && (c->d_dinv != nullptr || var);
   if (var && precision == PCG_MIXED_IR)
     return fail(c, PCG_ENOTIMPL, "PCG_MIXED_IR with a variable shift is not implemented");
   CUDA_TRY(c, cudaSetDevice(c->device));
@@ -774,6 +775,7 @@ pcg_status solve_common(pcg_ctx* c, const double* b, const double* x0, int32_t m
   if ((s = ensure_vectors(c)) != PCG_OK) return s;
   if (precision == PCG_MIXED_IR && (s = ensure_mixed(c)) != PCG_OK) return s;
   if ((s = ensure_hist(c, maxit + 1)) != PCG_OK) return s;
+  c->v.dinv = method == PCG_CG ? c->d_dinv : nullptr;
   const size_t bytes = (size_t)c->n * sizeof(double);
   const cudaMemcpyKind in = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   const cudaMemcpyKind outk = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;

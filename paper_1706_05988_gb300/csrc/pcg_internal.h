@@ -59,6 +59,7 @@ struct OpDesc {
 struct Vecs {
   const double* b;
   double *x, *r, *w0, *w1, *z, *s, *p;
+  const double* dinv = nullptr;   // Algorithm 1 with M^{-1} = D^{-1} (nullptr: M = I)
 };
 
 struct Launch {

@@ -394,10 +394,10 @@ __device__ __forceinline__ void finish_spcg(State* st, Hist h, double gamma, dou
   st->ticket = 0;
 }
 
-// Algorithm 1 after (r_i, r_i): stop tests, beta_i = gamma_i / gamma_{i-1}.
-__device__ __forceinline__ void finish_cg_gamma(State* st, Hist h, double gamma, bool init) {
+// Algorithm 1 after gamma_i = (r_i, u_i) and (r_i, r_i): stop tests, beta_i = gamma_i / gamma_{i-1}.
+__device__ __forceinline__ void finish_cg_gamma(State* st, Hist h, double gamma, double rr, bool init) {
   const int i = init ? 0 : st->iter + 1;
-  const double rn = sqrt(gamma);
+  const double rn = sqrt(rr);
   h.gamma[i] = gamma;
   h.rec[i] = rn;
   int status = ST_RUNNING;
@@ -577,23 +577,41 @@ __global__ void __launch_bounds__(kBlock) k_true_res(Op op, Vecs v, State* st, H
   }
 }
 
-// Algorithm 1, line 1: p_0 = r_0 (M = I), gamma_0 = (r_0, r_0).
+// u = M^{-1} r for Algorithm 1: D^{-1} r, or r itself for M = I (never stored).
+template <int VEC>
+__device__ __forceinline__ void cg_precond(const double* dinv, int c0, const double (&r)[VEC], double (&u)[VEC]) {
+  if (dinv) {
+    double d[VEC];
+    ld_stream<VEC>(dinv + c0, d);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) u[e] = d[e] * r[e];
+  } else {
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) u[e] = r[e];
+  }
+}
+
+// Algorithm 1, line 1: u_0 = M^{-1} r_0, p_0 = u_0, gamma_0 = (r_0, u_0), ||r_0||.
 template <int VEC>
 __global__ void __launch_bounds__(kBlock) k_cg_p0(int n, Vecs v, State* st, Hist h, double* partials) {
   if (st->status != ST_RUNNING) return;
-  double g = 0.0;
+  double g = 0.0, rr = 0.0;
   const int nu = n / VEC;
   for (int u = blockIdx.x * kBlock + threadIdx.x; u < nu; u += gridDim.x * kBlock) {
     const int c0 = u * VEC;
-    double r[VEC];
+    double r[VEC], uu[VEC];
     ld_stream<VEC>(v.r + c0, r);
-    st_plain<VEC>(v.p + c0, r);
+    cg_precond<VEC>(v.dinv, c0, r, uu);
+    st_plain<VEC>(v.p + c0, uu);
 #pragma unroll
-    for (int e = 0; e < VEC; ++e) g = fma(r[e], r[e], g);
+    for (int e = 0; e < VEC; ++e) {
+      g = fma(r[e], uu[e], g);
+      rr = fma(r[e], r[e], rr);
+    }
   }
-  double vals[1] = {g}, tot[1];
-  if (!reduce_last_block<1>(vals, partials, &st->ticket, tot)) return;
-  if (threadIdx.x == 0) finish_cg_gamma(st, h, tot[0], true);
+  double vals[2] = {g, rr}, tot[2];
+  if (!reduce_last_block<2>(vals, partials, &st->ticket, tot)) return;
+  if (threadIdx.x == 0) finish_cg_gamma(st, h, tot[0], tot[1], true);
 }
 
 // Algorithm 1: s_i = A p_i and (s_i, p_i) -> alpha_i = gamma_i / (s_i, p_i).
@@ -630,7 +648,7 @@ template <int VEC>
 __global__ void __launch_bounds__(kBlock) k_cg_update(int n, Vecs v, State* st, Hist h, double* partials) {
   if (st->status != ST_RUNNING) return;
   const double alpha = h.alpha[st->iter];
-  double g = 0.0;
+  double g = 0.0, rr = 0.0;
   const int nu = n / VEC;
   for (int u = blockIdx.x * kBlock + threadIdx.x; u < nu; u += gridDim.x * kBlock) {
     const int c0 = u * VEC;
@@ -643,17 +661,23 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(int n, Vecs v, State* st, 
     for (int e = 0; e < VEC; ++e) {
       x[e] = fma(alpha, p[e], x[e]);
       r[e] = fma(-alpha, s[e], r[e]);
-      g = fma(r[e], r[e], g);
+    }
+    double uu[VEC];
+    cg_precond<VEC>(v.dinv, c0, r, uu);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) {
+      g = fma(r[e], uu[e], g);
+      rr = fma(r[e], r[e], rr);
     }
     st_stream<VEC>(v.x + c0, x);
     st_stream<VEC>(v.r + c0, r);
   }
-  double vals[1] = {g}, tot[1];
-  if (!reduce_last_block<1>(vals, partials, &st->ticket, tot)) return;
-  if (threadIdx.x == 0) finish_cg_gamma(st, h, tot[0], false);
+  double vals[2] = {g, rr}, tot[2];
+  if (!reduce_last_block<2>(vals, partials, &st->ticket, tot)) return;
+  if (threadIdx.x == 0) finish_cg_gamma(st, h, tot[0], tot[1], false);
 }
 
-// Algorithm 1: p_{i+1} = u_{i+1} + beta_{i+1} p_i (u = r).
+// Algorithm 1: p_{i+1} = u_{i+1} + beta_{i+1} p_i, u_{i+1} = M^{-1} r_{i+1}.
 template <int VEC>
 __global__ void __launch_bounds__(kBlock) k_cg_p(int n, Vecs v, State* st, Hist h) {
   if (st->status != ST_RUNNING) return;
@@ -661,11 +685,12 @@ __global__ void __launch_bounds__(kBlock) k_cg_p(int n, Vecs v, State* st, Hist 
   const int nu = n / VEC;
   for (int u = blockIdx.x * kBlock + threadIdx.x; u < nu; u += gridDim.x * kBlock) {
     const int c0 = u * VEC;
-    double r[VEC], p[VEC];
+    double r[VEC], uu[VEC], p[VEC];
     ld_stream<VEC>(v.r + c0, r);
     ld_stream<VEC>(v.p + c0, p);
+    cg_precond<VEC>(v.dinv, c0, r, uu);
 #pragma unroll
-    for (int e = 0; e < VEC; ++e) p[e] = fma(beta, p[e], r[e]);
+    for (int e = 0; e < VEC; ++e) p[e] = fma(beta, p[e], uu[e]);
     st_plain<VEC>(v.p + c0, p);
   }
 }

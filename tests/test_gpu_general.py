@@ -189,7 +189,7 @@ def test_general_errors(B):
     P = S.laplacian_2d(32)
     b = rhs(P)
     with B.Solver(P, flags=B.PCG_JACOBI) as s:
-        r = s.solve(b, method="cg", maxit=10, raise_on_error=False)
+        r = s.solve(b, method="cg", maxit=10, precision=B.PCG_MIXED_IR, raise_on_error=False)
         assert r.status == B.PCG_ENOTIMPL
         assert B.pcg_set_shifts(s.ctx, np.array([1.0, -0.5])) == B.PCG_EINVAL
         assert B.pcg_set_shifts(s.ctx, np.array([1.0, np.nan])) == B.PCG_EINVAL
@@ -249,3 +249,18 @@ def test_jacobi_with_device_matrix_arrays(B):
     bad["diag"][7] = 0.0
     with pytest.raises(C.PcgError):
         B.Solver(P, flags=B.PCG_JACOBI, device_arrays=bad)
+
+
+@pytest.mark.parametrize("name", ["varcoef3d_24", "varcoef2d_77x53", "csr_sdd_5003"])
+def test_jacobi_cg_vs_oracle(B, name):
+    """Algorithm 1 with M^-1 = D^-1 (the paper's JAC rows of Table 1) against the oracle's CG."""
+    P = PROBLEMS[name]()
+    b = rhs(P)
+    minv = 1.0 / diag_of(P)
+    with B.Solver(P, flags=B.PCG_JACOBI) as s:
+        g = s.solve(b, method="cg", maxit=150, true_every=1)
+        t = s.solve(b, method="cg", tol=1e-9, maxit=5000)
+    o = oracle.cg(P, b, maxit=150, minv=minv, log_every=1)
+    ot = oracle.cg(P, b, maxit=5000, rtol=1e-9, minv=minv, log_every=0)
+    check(g, o, np.linalg.norm(b), rec_floor=1e-6)
+    assert t.status == B.PCG_OK and ot.status == 1 and abs(t.iters - ot.iters) <= 1, (t.iters, ot.iters)
