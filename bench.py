@@ -372,7 +372,12 @@ def run_ours(args):
     from paper_1706_05988_gb300 import pcg as C
     import synthetic as S
 
-    pkg.build.build()
+    # one rank builds the in-tree library (a no-op when it is current); the others wait for it
+    if local == 0:
+        pkg.build.build()
+    barrier(world)
+    if local != 0:
+        pkg.build.build()
     P, b_host, _ = S.poisson3d_manufactured(N_SIDE)
     n = P.n
     solver = pkg.Solver(P, flags=C.PCG_PROFILE)
