@@ -453,7 +453,7 @@ def run_ours(args):
         rate, dt = cpu_oracle_rate(P, b_host, args.ref_iters)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{args.ref_iters} iterations of the same {N_SIDE}^3 shifted p-CG solve, single-threaded "
-                         f"FP64 oracle ({dt:.1f} s)"}
+                         f"FP64 oracle ({dt:.1f} s; the host has {os.cpu_count()} cores)"}
 
     solver.close()
 
