@@ -590,7 +590,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--ref-iters", type=int, default=10, help="oracle iterations per sample")
+    ap.add_argument("--ref-iters", type=int, default=50, help="oracle iterations per sample (about 11 s on one core)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timing")
     ap.add_argument("--no-csr", action="store_true", help="skip the CSR form of the workload")
     ap.add_argument("--no-persistent", action="store_true", help="skip the persistent-kernel measurement")
