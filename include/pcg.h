@@ -242,6 +242,12 @@ pcg_status pcg_batch_autotune(pcg_batch *batch, const double *const *b, const do
                               int32_t *cluster_out, double *ms_out);
 pcg_status pcg_batch_set_cluster(pcg_batch *batch, int32_t cluster_size);
 
+/* The three size classes: systems per class and current cluster size (arrays of 3,
+ * either may be NULL); pcg_batch_set_class_cluster sets one class's cluster size
+ * (1, 2, 4, 8 or 16).  Errors: PCG_EINVAL. */
+pcg_status pcg_batch_classes(const pcg_batch *batch, int32_t *nsys, int32_t *cluster);
+pcg_status pcg_batch_set_class_cluster(pcg_batch *batch, int32_t size_class, int32_t cluster_size);
+
 /* Precision of later pcg_batch_solve calls: PCG_FP64 (default) or PCG_MIXED_IR.
  * pcg_batch_set_param takes PCG_PARAM_MIXED_ETA and PCG_PARAM_MAX_RESTARTS with the
  * meaning and defaults they have for pcg_set_param.  Errors: PCG_EINVAL. */

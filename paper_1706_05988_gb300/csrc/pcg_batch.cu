@@ -656,6 +656,23 @@ pcg_status pcg_batch_set_param(pcg_batch* B, int32_t param, double value) {
   return PCG_EINVAL;
 }
 
+pcg_status pcg_batch_classes(const pcg_batch* B, int32_t* nsys, int32_t* cluster) {
+  if (!B) return PCG_EINVAL;
+  for (int k = 0; k < kNumClasses; ++k) {
+    if (nsys) nsys[k] = B->cls[k].nsys;
+    if (cluster) cluster[k] = B->cls[k].csize;
+  }
+  return PCG_OK;
+}
+
+pcg_status pcg_batch_set_class_cluster(pcg_batch* B, int32_t size_class, int32_t cluster_size) {
+  if (!B || size_class < 0 || size_class >= kNumClasses) return PCG_EINVAL;
+  if (cluster_size != 1 && cluster_size != 2 && cluster_size != 4 && cluster_size != 8 && cluster_size != 16)
+    return PCG_EINVAL;
+  B->cls[size_class].csize = cluster_size;
+  return PCG_OK;
+}
+
 pcg_status pcg_batch_set_cluster(pcg_batch* B, int32_t cluster_size) {
   if (!B) return PCG_EINVAL;
   if (cluster_size != 1 && cluster_size != 2 && cluster_size != 4 && cluster_size != 8 && cluster_size != 16)
