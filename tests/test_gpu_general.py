@@ -264,3 +264,25 @@ def test_jacobi_cg_vs_oracle(B, name):
     ot = oracle.cg(P, b, maxit=5000, rtol=1e-9, minv=minv, log_every=0)
     check(g, o, np.linalg.norm(b), rec_floor=1e-6)
     assert t.status == B.PCG_OK and ot.status == 1 and abs(t.iters - ot.iters) <= 1, (t.iters, ot.iters)
+
+
+def test_varcoef_128_jacobi_full_size_vs_oracle(B):
+    """The 128^3 high-contrast FV system (kappa = 10^U[-3,3] on 8^3 blocks, b ~ N(0,1)) at full size:
+    Jacobi shifted p-CG's first 20 iterations against the oracle, and the mixed-precision form with
+    binary64 refinement reaching a true relative residual of 1e-10, checked by the oracle's operator."""
+    P = S.varcoef_3d(128, block=8, seed=0)
+    b = S.normal(1, P.n)
+    minv = 1.0 / diag_of(P)
+    with B.Solver(P, flags=B.PCG_JACOBI) as s:
+        g = s.solve(b, method="spcg", sigma=1.0, maxit=20, true_every=0)
+        m = s.solve(b, method="spcg", sigma=1.0, tol=1e-10, maxit=40000, precision=B.PCG_MIXED_IR)
+    o = oracle.pcg_sh(P, b, sigma=1.0, maxit=20, minv=minv, log_every=0)
+    assert g.iters == o.iters == 20
+    assert rel(g.alpha[:20], o.alpha[:20]) <= TOL_SCALARS
+    assert rel(g.beta[1:20], o.beta[1:20]) <= TOL_SCALARS
+    idx = np.random.default_rng(2).integers(0, P.n, 20000)
+    np.testing.assert_allclose(g.x[idx], o.x[idx], rtol=1e-9, atol=1e-11 * np.abs(o.x).max())
+    assert m.status == B.PCG_OK
+    bn = np.linalg.norm(b)
+    assert np.linalg.norm(b - oracle.apply(P, m.x)) <= 1.05e-10 * bn
+

@@ -378,6 +378,20 @@ def test_full_size_1000_iterations_properties(B, big):
     assert abs(g.final_true_relres - g.final_rec_relres) < 1e-10
 
 
+def test_full_size_csr_first_iterations_vs_oracle(B, big):
+    """The same 256^3 Laplacian assembled as CSR with int32 indices (117,047,296 entries, the
+    benchmark's CSR form): the first 4 iterations against the oracle on the same CSR arrays."""
+    P, b = big
+    Pc = S.to_csr(P)
+    assert Pc.nnz == 117_047_296
+    with B.Solver(Pc) as s:
+        g = s.solve(b, method="spcg", sigma=6.0, maxit=4, true_every=0)
+    o = oracle.pcg_sh(Pc, b, sigma=6.0, maxit=4, log_every=0)
+    check_scalars(g, o, k=4)
+    idx = np.random.default_rng(1).integers(0, P.n, 20000)
+    np.testing.assert_allclose(g.x[idx], o.x[idx], rtol=1e-11, atol=1e-13 * np.abs(o.x).max())
+
+
 @pytest.mark.parametrize("method,sigma", [("cg", 0.0), ("spcg", 4.0)])
 def test_true_residual_stop(B, method, sigma):
     """The 100x100 Poisson run of the accuracy study: at most 2,000 iterations or a true relative
