@@ -194,7 +194,8 @@ def batch_measure(pkg, S, nsys: int, side_hi: int, forms=("fp64_jacobi", "mixed_
             tb = time.perf_counter() - t0
             out[name] = {"solves_per_s": nsys / tb, "kernel_ms": bt.last_kernel_ms(), "uniform_cluster_size": c,
                          "converged": int(np.sum(st == 0)), "max_true_relres": float(np.max(tr)),
-                         "mean_iters": float(np.mean(it))}
+                         "mean_iters": float(np.mean(it)),
+                         "unknown_iterations": float(np.sum(it.astype(np.float64) * np.array([P.n for P in probs])))}
     k = min(nsys, 16)
     idx = np.linspace(0, nsys - 1, k).astype(int)
     t1 = 0.0
@@ -245,17 +246,18 @@ def varcoef_measure(pkg, S) -> dict:
     return out
 
 
-def serving_trace(nreq: int, rate: float, seed: int = 0, n_max_exp: float = 5.0):
+def serving_trace(nreq: int, rate: float, seed: int = 0, n_max_exp: float = 5.0, first: int = None):
     """Seeded request stream: Poisson arrivals at `rate` per second; n log-uniform in
     [1e3, 10^n_max_exp]; half stencils (2D/3D unscaled Laplacians), half random SDD CSR (7-27
-    entries per row, off-diagonals U[-1,0]); tolerance log-uniform in [1e-10, 1e-6]; b ~ N(0,1)."""
+    entries per row, off-diagonals U[-1,0]); tolerance log-uniform in [1e-10, 1e-6]; b ~ N(0,1).
+    first: build only the first requests of the same stream."""
     import numpy as np
     import synthetic as S
     u = S.uniform01(seed, 4 * nreq).reshape(nreq, 4)
     gaps = -np.log(1.0 - u[:, 0]) / rate
     arrive = np.cumsum(gaps)
     reqs = []
-    for i in range(nreq):
+    for i in range(nreq if first is None else min(first, nreq)):
         n = int(10 ** (3 + (n_max_exp - 3) * u[i, 1]))
         if u[i, 2] < 0.25:
             side = max(int(round(n ** 0.5)), 4)
@@ -326,11 +328,72 @@ def serving_measure(pkg, nreq: int, rate: float, tol=None, n_max_exp: float = 5.
         if now < arr:
             time.sleep(arr - now)
         with pkg.Solver(P) as one:
-            diag = 4.0 if P.layout == 0 else 6.0 if P.layout == 1 else float(np.mean(P.val[P.col == np.repeat(
-                np.arange(P.n), np.diff(P.row_ptr))]))
-            one.solve(b, method="spcg", sigma=diag, tol=tol, maxit=100000)
+            one.solve(b, method="spcg", sigma=request_sigma(P), tol=tol, maxit=100000)
         lat1[k] = time.perf_counter() - t0 - arr
     out["one_at_a_time_fp64"] = summary(lat1, time.perf_counter() - t0)
+    return out
+
+
+def request_sigma(P) -> float:
+    """The one-at-a-time shift rule: the constant stencil's diagonal, the mean CSR diagonal."""
+    import numpy as np
+    if P.layout == 0:
+        return 4.0
+    if P.layout == 1:
+        return 6.0
+    return float(np.mean(P.val[P.col == np.repeat(np.arange(P.n), np.diff(P.row_ptr))]))
+
+
+def cpu_side_baselines(S, args, batch, varcoef) -> dict:
+    """The oracle (single-threaded FP64, as it stands) beside the side measurements, each on a
+    bounded sample scaled to that measurement's unit."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    out = {}
+    if batch is not None and "fp64_jacobi" in batch:
+        # seconds per unknown-iteration of Jacobi shifted p-CG on 4 systems of the batch, times the
+        # unknown-iterations the batched FP64 Jacobi solve ran (sum over systems of n x iterations)
+        rng = np.random.default_rng(0)
+        sides = rng.integers(32, args.batch_side_max + 1, size=args.batch_systems)
+        idx = np.linspace(0, args.batch_systems - 1, 4).astype(int)
+        k, work, t = 200, 0.0, 0.0
+        for i in idx:
+            P = S.varcoef_2d(int(sides[i]), int(sides[i]), seed=int(i))
+            b = S.normal(1000 + int(i), P.n)
+            minv = 1.0 / np.asarray(P.diag)
+            t0 = time.perf_counter()
+            oracle.pcg_sh(P, b, sigma=1.0, maxit=k, minv=minv, log_every=0)
+            t += time.perf_counter() - t0
+            work += k * P.n
+        est = batch["fp64_jacobi"]["unknown_iterations"] * t / work
+        out["batch_fp64_jacobi"] = {
+            "solves_per_s": args.batch_systems / est, "est_batch_s": est,
+            "sample": f"{k} iterations of 4 of the batch's systems ({t:.1f} s), scaled by the unknown-iterations "
+                      "of the batched FP64 Jacobi solve"}
+    if varcoef is not None:
+        P = S.varcoef_3d(128, block=8, seed=0)
+        b = S.normal(1, P.n)
+        minv = 1.0 / np.asarray(P.diag)
+        k = 30
+        t0 = time.perf_counter()
+        oracle.pcg_sh(P, b, sigma=varcoef["sigma"], maxit=k, minv=minv, log_every=0)
+        t = time.perf_counter() - t0
+        out["varcoef_128_fp64_jacobi"] = {
+            "iters_per_s": k / t, "est_solve_ms": 1e3 * varcoef["fp64"]["iters"] * t / k,
+            "sample": f"{k} iterations of the FP64 Jacobi solve ({t:.1f} s)"}
+    if not args.no_serving:
+        budget, cnt, t0 = 5.0, 0, time.perf_counter()
+        for _, P, b, tol in serving_trace(args.serving_requests, args.serving_rate, n_max_exp=args.serving_n_max_exp,
+                                          first=64):
+            oracle.pcg_sh(P, b, sigma=request_sigma(P), rtol=tol, maxit=100000, log_every=0)
+            cnt += 1
+            if time.perf_counter() - t0 > budget:
+                break
+        t = time.perf_counter() - t0
+        out["serving_fp64"] = {"solves_per_s": cnt / t,
+                               "sample": f"the trace's first {cnt} requests back to back ({t:.1f} s), FP64, "
+                                         "the one-at-a-time shift rule and tolerances"}
     return out
 
 
@@ -520,6 +583,9 @@ def run_ours(args):
                    "kernel_avg_ms": k_s * 1e3, "algorithmic_bytes_per_launch": bytes_csr,
                    "achieved_gbs": bytes_csr / k_s / 1e9, "frac": bytes_csr / k_s / 1e9 / peak}
         del Pc
+
+    if cpu is not None:
+        cpu["side"] = cpu_side_baselines(S, args, batch, varcoef)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
