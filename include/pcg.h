@@ -250,7 +250,9 @@ pcg_status pcg_batch_set_class_cluster(pcg_batch *batch, int32_t size_class, int
 
 /* Precision of later pcg_batch_solve calls: PCG_FP64 (default) or PCG_MIXED_IR.
  * pcg_batch_set_param takes PCG_PARAM_MIXED_ETA and PCG_PARAM_MAX_RESTARTS with the
- * meaning and defaults they have for pcg_set_param.  Errors: PCG_EINVAL. */
+ * meaning they have for pcg_set_param; the batch's default eta is 2^-14 (the per-cluster
+ * solves restart less often than the single-system solver, default 2^-10), and
+ * max_restarts defaults to 200 as there.  Errors: PCG_EINVAL. */
 pcg_status pcg_batch_set_precision(pcg_batch *batch, int32_t precision);
 pcg_status pcg_batch_set_param(pcg_batch *batch, int32_t param, double value);
 
@@ -296,7 +298,7 @@ pcg_status pcg_submit(pcg_server *server, const pcg_matrix *A, const double *b, 
 /* pcg_submit with a preconditioner and a precision for this request: flags 0 or
  * PCG_JACOBI (M^{-1} = diag(A)^{-1}, as for pcg_create); precision PCG_FP64 or
  * PCG_MIXED_IR (binary32 auxiliary vectors with binary64 restarts as in pcg_solve,
- * eta = 2^-10, at most 200 restarts; tol then applies to the true residual).  The
+ * eta = 2^-14, at most 200 restarts; tol then applies to the true residual).  The
  * request's arena block also holds its Jacobi vectors and binary32 coefficients.
  * With PCG_JACOBI, sigma < 0 selects 1, the mean diagonal entry of M^{-1} A.
  * pcg_submit(...) is pcg_submit_ex(..., 0, PCG_FP64, ticket).  Errors as pcg_submit,

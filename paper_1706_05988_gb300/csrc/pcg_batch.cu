@@ -187,7 +187,7 @@ struct pcg_batch {
   double* d_vec = nullptr;        // b, x, r, w0, w1, z, s, p (+ u, q, t, m0, m1, u64, dinv, dinv32)
   bool jacobi = false;
   int precision = PCG_FP64;
-  double eta = 1.0 / 1024.0;      // inner tolerance factor of the mixed-precision restarts
+  double eta = kClusterMixedEta;  // inner tolerance factor of the mixed-precision restarts
   int max_restarts = 200;
   double* h_stage = nullptr;      // pinned staging of b / x (total doubles)
   cudaStream_t stream = nullptr;

@@ -11,6 +11,16 @@
 
 namespace pcgk {
 
+// Default inner tolerance factor eta of the per-cluster mixed-precision solves (batch and
+// serving): a restart comes once the recursive residual has fallen by eta.  2^-14 (the
+// single-system solver uses 2^-10): on 512 high-contrast 2D systems solved to 1e-8 with
+// Jacobi, 2^-10 / 2^-12 / 2^-14 / 2^-16 took 3,215 / 3,022 / 2,978 / 2,982 iterations on
+// average, since fewer restarts leave the Krylov space fewer times.
+#ifndef PCG_CLUSTER_MIXED_ETA_LOG2
+#define PCG_CLUSTER_MIXED_ETA_LOG2 14
+#endif
+constexpr double kClusterMixedEta = 1.0 / (double)(1ll << PCG_CLUSTER_MIXED_ETA_LOG2);
+
 // The binary32 operator with V unknowns per thread (stencils; CSR rows stay one per thread).
 template <int F, int V>
 struct FamilyOp32V {

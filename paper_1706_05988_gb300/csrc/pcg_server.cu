@@ -335,7 +335,7 @@ pcg_status upload(pcg_server* S, Request* R, bool staged) {
   w->maxit = R->maxit;
   w->mode = R->mode;
   w->max_restarts = 200;
-  w->eta = 1.0 / 1024.0;
+  w->eta = pcgk::kClusterMixedEta;
   w->tol = R->tol;
   w->sys = d;
   w->vec.b = v;
