@@ -612,11 +612,26 @@ def run_ours(args):
 def profile_case(kind: str, n: int) -> int:
     """A short solve for an ncu capture (no timing, no JSON): `spcg` runs 8 iterations of the
     main kernel on the n^3 Laplacian; `jacobi-fp64` and `jacobi-mixed` run 12 iterations of the
-    Jacobi sweeps (sigma = 1; the mixed one with eta = 1e-30, so no restart interrupts)."""
+    Jacobi sweeps (sigma = 1; the mixed one with eta = 1e-30, so no restart interrupts);
+    `batch-*` run batched launches (see below)."""
     import synthetic as S
     import paper_1706_05988_gb300 as pkg
     from paper_1706_05988_gb300 import pcg as C
     pkg.build.build()
+    if kind.startswith("batch-large"):
+        # one batched launch of the large systems of the 512-system batch: 64 2D FV systems with
+        # sides U{256..512} (9.6M unknowns), 500 iterations each, Jacobi, cluster size 2
+        import numpy as np
+        rng = np.random.default_rng(0)
+        probs = [S.varcoef_2d(int(L), int(L), seed=i) for i, L in enumerate(rng.integers(256, 513, size=64))]
+        bs = [S.normal(1000 + i, P.n) for i, P in enumerate(probs)]
+        prec = C.PCG_MIXED_IR if kind == "batch-large-mixed-jacobi" else C.PCG_FP64
+        with pkg.Batch(probs, flags=pkg.PCG_JACOBI, precision=prec) as bt:
+            bt.set_cluster(2)
+            for _ in range(2):
+                _, it, st, _ = bt.solve(bs, [1.0] * len(probs), tol=1e-8, maxit=500)
+            print(kind, "kernel ms", bt.last_kernel_ms(), "unknowns", sum(P.n for P in probs), "iterations", int(it.max()))
+        return 0
     if kind.startswith("batch"):
         # one batched launch: 128 2D FV systems (sides U{32..128}) to 1e-8, cluster size 4
         import numpy as np
@@ -650,7 +665,8 @@ def profile_case(kind: str, n: int) -> int:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--profile-case", choices=["spcg", "jacobi-fp64", "jacobi-mixed", "batch-fp64",
-                                               "batch-mixed-jacobi"], default=None,
+                                               "batch-mixed-jacobi", "batch-large-fp64-jacobi",
+                                               "batch-large-mixed-jacobi"], default=None,
                     help="run one short solve of --size^3 for an ncu capture, then exit")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)

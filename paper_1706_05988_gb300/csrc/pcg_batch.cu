@@ -47,8 +47,17 @@ __device__ __forceinline__ void solve_one(cg::cluster_group& cl, double (*part)[
     cluster_solve_mx_auto<F, true>(cl, part, slot, d, V, prm.tol, prm.maxit, prm.eta, prm.max_restarts, res);
 }
 
+// Resident blocks per SM k_batch is compiled for (register cap 65536 / (256 x this)).
+// The per-cluster sweeps wait on global loads (ncu: long-scoreboard stalls, 25 % of the
+// DRAM peak), so warps per SM count more than the spills a 64-register cap costs: on 512
+// high-contrast 2D systems, 4 blocks per SM gave 79.4 / 109.2 solves/s (FP64 / mixed,
+// Jacobi) against 72.3 / 101.4 with 2 blocks and 128 registers.
+#ifndef PCG_BATCH_MIN_BLOCKS
+#define PCG_BATCH_MIN_BLOCKS 4
+#endif
+
 template <int F, int MODE>
-__global__ void __launch_bounds__(kBlock, 2) k_batch(const BatchSys* __restrict__ sys, const int* __restrict__ order,
+__global__ void __launch_bounds__(kBlock, PCG_BATCH_MIN_BLOCKS) k_batch(const BatchSys* __restrict__ sys, const int* __restrict__ order,
                                                   int nsys, int* next, BatchVecs V, BatchOut* out, BatchParams prm) {
   cg::cluster_group cl = cg::this_cluster();
   const unsigned rank = cl.block_rank();

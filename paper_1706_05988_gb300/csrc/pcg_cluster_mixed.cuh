@@ -425,15 +425,22 @@ __device__ __forceinline__ void cluster_solve_mx(cg::cluster_group& cl, double (
 }
 
 // Mixed precision with several unknowns per thread in the binary32 sweeps when the system's
-// row length allows: four with M = I, two with Jacobi (twice the vectors; four would spill
-// under the 128-register cap of two resident blocks).  The batched launch uses this; the
-// serving kernel keeps one per thread, which bounds its size.
+// row length allows: four with M = I, two with Jacobi (twice the vectors).  On 512 2D systems
+// with Jacobi and 4 resident blocks per SM, two unknowns per thread gave 109.2 solves/s and
+// one gave 103.  The batched launch and the serving kernel's large lane use this; its small
+// lane keeps one per thread.
 template <int F, bool JAC>
 __device__ __forceinline__ void cluster_solve_mx_auto(cg::cluster_group& cl, double (*part)[4], int& slot,
                                                       const BatchSys& d, const BatchVecs& V, double tol, int maxit,
                                                       double eta, int max_restarts, BatchOut& res) {
-  constexpr int W = JAC ? 2 : 4;
-  if constexpr (F != 4) {
+#ifndef PCG_CLUSTER_MX_JAC_VW
+#define PCG_CLUSTER_MX_JAC_VW 2
+#endif
+#ifndef PCG_CLUSTER_MX_VW
+#define PCG_CLUSTER_MX_VW 4
+#endif
+  constexpr int W = JAC ? PCG_CLUSTER_MX_JAC_VW : PCG_CLUSTER_MX_VW;
+  if constexpr (F != 4 && W > 1) {
     if (d.nx % W == 0) {
       cluster_solve_mx<F, JAC, W>(cl, part, slot, d, V, tol, maxit, eta, max_restarts, res);
       return;

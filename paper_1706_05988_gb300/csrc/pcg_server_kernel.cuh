@@ -113,8 +113,13 @@ __device__ __forceinline__ void load_item(const WorkItem* src, WorkItem* dst) {
   for (unsigned i = 0; i < sizeof(WorkItem) / 8; ++i) b[i] = __ldcv(a + i);
 }
 
+// Resident blocks per SM k_server is compiled for (register cap 65536 / (256 x this)).
+#ifndef PCG_SERVER_MIN_BLOCKS
+#define PCG_SERVER_MIN_BLOCKS 2
+#endif
+
 template <bool WIDE>
-__global__ void __launch_bounds__(kBlock, 2) k_server(ServerShared* sh, const WorkItem* items, BatchOut* results,
+__global__ void __launch_bounds__(kBlock, PCG_SERVER_MIN_BLOCKS) k_server(ServerShared* sh, const WorkItem* items, BatchOut* results,
                                                    unsigned int* done, unsigned int cap, unsigned int* claim,
                                                    unsigned int* left) {
   cg::cluster_group cl = cg::this_cluster();
