@@ -298,7 +298,9 @@ pcg_status pcg_submit(pcg_server *server, const pcg_matrix *A, const double *b, 
 /* pcg_submit with a preconditioner and a precision for this request: flags 0 or
  * PCG_JACOBI (M^{-1} = diag(A)^{-1}, as for pcg_create); precision PCG_FP64 or
  * PCG_MIXED_IR (binary32 auxiliary vectors with binary64 restarts as in pcg_solve,
- * eta = 2^-14, at most 200 restarts; tol then applies to the true residual).  The
+ * at most 200 restarts, eta = 2^-14 in the cluster lanes and pcg_solve's default 2^-10
+ * for requests of n >= 2^19, which the single-system solver takes on the whole GPU;
+ * tol then applies to the true residual).  The
  * request's arena block also holds its Jacobi vectors and binary32 coefficients.
  * With PCG_JACOBI, sigma < 0 selects 1, the mean diagonal entry of M^{-1} A.
  * pcg_submit(...) is pcg_submit_ex(..., 0, PCG_FP64, ticket).  Errors as pcg_submit,

@@ -138,11 +138,15 @@ def test_batch_mixed_reaches_tolerance(B, name, maker, jac, sigma):
 
 
 def test_batch_mixed_matches_single_mixed(B):
+    """The batch's mixed-precision solves (inner tolerance eta = 2^-14 by default) take the
+    iterations of the single-system solver run with the same eta."""
+    from paper_1706_05988_gb300 import pcg as C
     probs, bs = var2d_batch(k=5, seed=9)
     with B.Batch(probs, flags=B.PCG_JACOBI, precision=B.PCG_MIXED_IR) as bt:
         xs, it, st, tr = bt.solve(bs, [1.0] * len(probs), tol=1e-9, maxit=20000)
     for P, b, x, i, code in zip(probs, bs, xs, it, st):
         with B.Solver(P, flags=B.PCG_JACOBI) as one:
+            assert C.pcg_set_param(one.ctx, C.PCG_PARAM_MIXED_ETA, 2.0 ** -14) == B.PCG_OK
             r = one.solve(b, method="spcg", sigma=1.0, tol=1e-9, maxit=20000, precision=B.PCG_MIXED_IR)
         assert code == B.PCG_OK and r.status == B.PCG_OK
         assert abs(int(i) - r.iters) <= 0.05 * r.iters + 10, (int(i), r.iters)
