@@ -625,9 +625,11 @@ def profile_case(kind: str, n: int) -> int:
         rng = np.random.default_rng(0)
         probs = [S.varcoef_2d(int(L), int(L), seed=i) for i, L in enumerate(rng.integers(256, 513, size=64))]
         bs = [S.normal(1000 + i, P.n) for i, P in enumerate(probs)]
-        prec = C.PCG_MIXED_IR if kind == "batch-large-mixed-jacobi" else C.PCG_FP64
+        prec = C.PCG_MIXED_IR if kind.startswith("batch-large-mixed-jacobi") else C.PCG_FP64
         with pkg.Batch(probs, flags=pkg.PCG_JACOBI, precision=prec) as bt:
             bt.set_cluster(2)
+            if kind.endswith("-occ4"):
+                bt.set_class_occupancy(2, 4)      # the 64-register kernel variant, forced
             for _ in range(2):
                 _, it, st, _ = bt.solve(bs, [1.0] * len(probs), tol=1e-8, maxit=500)
             print(kind, "kernel ms", bt.last_kernel_ms(), "unknowns", sum(P.n for P in probs), "iterations", int(it.max()))
@@ -666,7 +668,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--profile-case", choices=["spcg", "jacobi-fp64", "jacobi-mixed", "batch-fp64",
                                                "batch-mixed-jacobi", "batch-large-fp64-jacobi",
-                                               "batch-large-mixed-jacobi"], default=None,
+                                               "batch-large-mixed-jacobi", "batch-large-mixed-jacobi-occ4"],
+                    default=None,
                     help="run one short solve of --size^3 for an ncu capture, then exit")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)

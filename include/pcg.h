@@ -242,11 +242,17 @@ pcg_status pcg_batch_autotune(pcg_batch *batch, const double *const *b, const do
                               int32_t *cluster_out, double *ms_out);
 pcg_status pcg_batch_set_cluster(pcg_batch *batch, int32_t cluster_size);
 
-/* The three size classes: systems per class and current cluster size (arrays of 3,
- * either may be NULL); pcg_batch_set_class_cluster sets one class's cluster size
- * (1, 2, 4, 8 or 16).  Errors: PCG_EINVAL. */
-pcg_status pcg_batch_classes(const pcg_batch *batch, int32_t *nsys, int32_t *cluster);
+/* The three size classes: systems per class, current cluster size and the resident
+ * blocks per SM of the class's kernel variant (arrays of 3, any may be NULL; blocks per SM
+ * is 0 for a class not launched yet).  Each class's kernel exists compiled for 2 resident
+ * blocks per SM (128 registers) and for 4 (64 registers, with spills): by default a class
+ * takes 4 when it has more systems than a 2-block grid holds clusters, else 2; the
+ * autotuner times both.  pcg_batch_set_class_cluster sets one class's cluster size (1, 2,
+ * 4, 8 or 16), pcg_batch_set_class_occupancy its variant (2, 4, or 0 for the default
+ * rule).  Errors: PCG_EINVAL. */
+pcg_status pcg_batch_classes(const pcg_batch *batch, int32_t *nsys, int32_t *cluster, int32_t *blocks_per_sm);
 pcg_status pcg_batch_set_class_cluster(pcg_batch *batch, int32_t size_class, int32_t cluster_size);
+pcg_status pcg_batch_set_class_occupancy(pcg_batch *batch, int32_t size_class, int32_t blocks_per_sm);
 
 /* Precision of later pcg_batch_solve calls: PCG_FP64 (default) or PCG_MIXED_IR.
  * pcg_batch_set_param takes PCG_PARAM_MIXED_ETA and PCG_PARAM_MAX_RESTARTS with the

@@ -1,13 +1,14 @@
-// Batched shifted pipelined CG: many independent systems in one persistent launch.
+// Batched shifted pipelined CG: many independent systems in one persistent launch (host
+// side; the kernel is in pcg_batch_kernel.cuh).
 //
 // Each thread-block cluster takes systems from a device work queue (largest first)
-// and runs every iteration of Algorithm 3 (M = I, binary64) for that system itself:
-// the blocks of the cluster split the system's unknowns, the dot products reduce
-// warp -> block -> cluster through distributed shared memory, and one cluster
-// barrier per iteration stands in for the global reduction.  Every block sums
-// the cluster's partials in rank order, so all blocks hold identical scalars and
-// take the same stop decision.  Blocks of different clusters never wait on each
-// other; the only barrier is the hardware cluster barrier.
+// and runs every iteration of Algorithm 3 for that system itself: the blocks of the
+// cluster split the system's unknowns, the dot products reduce warp -> block ->
+// cluster through distributed shared memory, and one cluster barrier per iteration
+// stands in for the global reduction.  Every block sums the cluster's partials in rank
+// order, so all blocks hold identical scalars and take the same stop decision.  Blocks
+// of different clusters never wait on each other; the only barrier is the hardware
+// cluster barrier.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -23,124 +24,7 @@
 
 #define PCG_KERNELS_IMPL
 #include "../../include/pcg.h"
-#include "pcg_cluster_mixed.cuh"
-
-namespace pcgk {
-namespace {
-
-// Solver per cluster: binary64 M = I, binary64 Jacobi, mixed M = I, mixed Jacobi.
-enum { BM_FP64 = 0, BM_JAC, BM_MX, BM_MXJ, BM_NMODES };
-
-struct BatchParams {
-  double tol, eta;
-  int maxit, max_restarts;
-};
-
-template <int F, int MODE>
-__device__ __forceinline__ void solve_one(cg::cluster_group& cl, double (*part)[4], int& slot, const BatchSys& d,
-                                          const BatchVecs& V, const BatchParams& prm, BatchOut& res) {
-  if constexpr (MODE == BM_FP64) cluster_solve<F>(cl, part, slot, d, V, prm.tol, prm.maxit, res);
-  if constexpr (MODE == BM_JAC) cluster_solve_jac<F>(cl, part, slot, d, V, prm.tol, prm.maxit, res);
-  if constexpr (MODE == BM_MX)
-    cluster_solve_mx_auto<F, false>(cl, part, slot, d, V, prm.tol, prm.maxit, prm.eta, prm.max_restarts, res);
-  if constexpr (MODE == BM_MXJ)
-    cluster_solve_mx_auto<F, true>(cl, part, slot, d, V, prm.tol, prm.maxit, prm.eta, prm.max_restarts, res);
-}
-
-// Resident blocks per SM k_batch is compiled for (register cap 65536 / (256 x this)).
-// The per-cluster sweeps wait on global loads (ncu: long-scoreboard stalls, 25 % of the
-// DRAM peak), so warps per SM count more than the spills a 64-register cap costs: on 512
-// high-contrast 2D systems, 4 blocks per SM gave 79.4 / 109.2 solves/s (FP64 / mixed,
-// Jacobi) against 72.3 / 101.4 with 2 blocks and 128 registers.
-#ifndef PCG_BATCH_MIN_BLOCKS
-#define PCG_BATCH_MIN_BLOCKS 4
-#endif
-
-template <int F, int MODE>
-__global__ void __launch_bounds__(kBlock, PCG_BATCH_MIN_BLOCKS) k_batch(const BatchSys* __restrict__ sys, const int* __restrict__ order,
-                                                  int nsys, int* next, BatchVecs V, BatchOut* out, BatchParams prm) {
-  cg::cluster_group cl = cg::this_cluster();
-  const unsigned rank = cl.block_rank();
-  __shared__ double part[2][4];
-  __shared__ int s_task;
-  int slot = 0;
-  for (;;) {
-    if (rank == 0 && threadIdx.x == 0) s_task = atomicAdd(next, 1);
-    cl.sync();
-    const int task = *cl.map_shared_rank(&s_task, 0);
-    cl.sync();                       // every block has read the task before rank 0 overwrites it
-    if (task >= nsys) return;
-    const int k = order[task];
-    const BatchSys d = sys[k];
-    BatchOut res;
-    solve_one<F, MODE>(cl, part, slot, d, V, prm, res);
-    if (rank == 0 && threadIdx.x == 0) out[k] = res;
-  }
-}
-
-template <int F, int MODE>
-cudaError_t launch_batch(int clusters, int csize, cudaStream_t stream, const BatchSys* sys, const int* order,
-                         int nsys, int* next, BatchVecs V, BatchOut* out, BatchParams prm) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(clusters * csize);
-  cfg.blockDim = dim3(kBlock);
-  cfg.stream = stream;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = csize;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_batch<F, MODE>, sys, order, nsys, next, V, out, prm);
-}
-
-template <int F, int MODE>
-int max_clusters(int csize) {
-  if (csize > 8) {
-    if (cudaFuncSetAttribute(k_batch<F, MODE>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
-      return 0;
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(csize);
-  cfg.blockDim = dim3(kBlock);
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = csize;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  int n = 0;
-  return cudaOccupancyMaxActiveClusters(&n, k_batch<F, MODE>, &cfg) == cudaSuccess ? n : 0;
-}
-
-template <int F, class Fn>
-cudaError_t with_mode(int mode, Fn&& fn) {
-  switch (mode) {
-    case BM_FP64: return fn(std::integral_constant<int, F>{}, std::integral_constant<int, BM_FP64>{});
-    case BM_JAC: return fn(std::integral_constant<int, F>{}, std::integral_constant<int, BM_JAC>{});
-    case BM_MX: return fn(std::integral_constant<int, F>{}, std::integral_constant<int, BM_MX>{});
-    case BM_MXJ: return fn(std::integral_constant<int, F>{}, std::integral_constant<int, BM_MXJ>{});
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-// fn(family, mode) with both as compile-time constants
-template <class Fn>
-cudaError_t with_family(int fam, int mode, Fn&& fn) {
-  switch (fam) {
-    case 0: return with_mode<0>(mode, fn);
-    case 1: return with_mode<1>(mode, fn);
-    case 2: return with_mode<2>(mode, fn);
-    case 3: return with_mode<3>(mode, fn);
-    case 4: return with_mode<4>(mode, fn);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-}  // namespace
-}  // namespace pcgk
+#include "pcg_batch_kernel.cuh"
 
 using namespace pcgk;
 
@@ -156,6 +40,8 @@ constexpr long long kClassBound[kNumClasses] = {8192, 65536, 1LL << 40};   // n 
 struct SizeClass {
   int nsys = 0;
   int csize = 4;
+  int occ = 0;                  // resident blocks per SM of its kernel: 2, 4, or 0 = chosen per launch
+  int occ_used = 0;             // the value the last graph was built with
   int* d_order = nullptr;       // the class's systems, largest first (device)
   int* d_next = nullptr;        // queue head (device)
   cudaStream_t stream = nullptr;
@@ -166,11 +52,12 @@ struct SizeClass {
 struct GraphKey {
   int mode = -1, mask = 0;
   int csize[kNumClasses] = {0, 0, 0};
+  int occ[kNumClasses] = {0, 0, 0};
   double tol = 0.0, eta = 0.0;
   int maxit = 0, max_restarts = 0;
   bool operator==(const GraphKey& o) const {
     for (int k = 0; k < kNumClasses; ++k)
-      if (csize[k] != o.csize[k]) return false;
+      if (csize[k] != o.csize[k] || occ[k] != o.occ[k]) return false;
     return mode == o.mode && mask == o.mask && tol == o.tol && eta == o.eta && maxit == o.maxit &&
            max_restarts == o.max_restarts;
   }
@@ -252,13 +139,17 @@ BatchVecs vecs_of(pcg_batch* B) {
 
 int mode_of(const pcg_batch* B) { return (B->precision == PCG_MIXED_IR ? BM_MX : BM_FP64) + (B->jacobi ? 1 : 0); }
 
-int max_clusters_of(int fam, int mode, int csize) {
-  int n = 0;
-  with_family(fam, mode, [&](auto F, auto M) {
-    n = max_clusters<decltype(F)::value, decltype(M)::value>(csize);
-    return cudaSuccess;
-  });
-  return n;
+int max_clusters_of(int fam, int mode, int csize, int occ) {
+  return occ == 4 ? batch_max_clusters_occ4(fam, mode, csize) : batch_max_clusters_occ2(fam, mode, csize);
+}
+
+// The kernel variant of a size class: as set, or 4 resident blocks per SM when the class
+// has more systems than a 2-block grid holds clusters (more warps then pay for the spills
+// of the 64-register cap), else 2.
+int occ_for(const pcg_batch* B, int mode, const SizeClass& c) {
+  if (c.occ == 2 || c.occ == 4) return c.occ;
+  const int m2 = max_clusters_of(B->family, mode, c.csize, 2);
+  return c.nsys > m2 && max_clusters_of(B->family, mode, c.csize, 4) > 0 ? 4 : 2;
 }
 
 // Builds (or reuses) the graph that launches every class in `mask` on its own stream, then
@@ -268,7 +159,10 @@ pcg_status run_batch(pcg_batch* B, int mask, double tol, int maxit) {
   GraphKey key;
   key.mode = mode;
   key.mask = mask;
-  for (int k = 0; k < kNumClasses; ++k) key.csize[k] = B->cls[k].csize;
+  for (int k = 0; k < kNumClasses; ++k) {
+    key.csize[k] = B->cls[k].csize;
+    key.occ[k] = B->cls[k].nsys > 0 && ((mask >> k) & 1) ? occ_for(B, mode, B->cls[k]) : 0;
+  }
   key.tol = tol;
   key.maxit = maxit;
   key.eta = B->eta;
@@ -285,7 +179,7 @@ pcg_status run_batch(pcg_batch* B, int mask, double tol, int maxit) {
     for (int k = 0; k < kNumClasses; ++k) {
       const SizeClass& c = B->cls[k];
       if (!((mask >> k) & 1) || c.nsys == 0) continue;
-      const int maxc = max_clusters_of(B->family, mode, c.csize);
+      const int maxc = max_clusters_of(B->family, mode, c.csize, key.occ[k]);
       if (maxc <= 0) {
         cudaGetLastError();
         return PCG_ECUDA;
@@ -308,10 +202,9 @@ pcg_status run_batch(pcg_batch* B, int mask, double tol, int maxit) {
       e = cudaStreamWaitEvent(c.stream, B->fork, 0);
       if (e == cudaSuccess) e = cudaMemsetAsync(c.d_next, 0, sizeof(int), c.stream);
       if (e == cudaSuccess)
-        e = with_family(B->family, mode, [&](auto F, auto M) {
-          return launch_batch<decltype(F)::value, decltype(M)::value>(clusters[k], c.csize, c.stream, B->d_sys,
-                                                                      c.d_order, c.nsys, c.d_next, V, B->d_out, prm);
-        });
+        e = (key.occ[k] == 4 ? batch_launch_occ4 : batch_launch_occ2)(B->family, mode, clusters[k], c.csize,
+                                                                       c.stream, B->d_sys, c.d_order, c.nsys,
+                                                                       c.d_next, V, B->d_out, prm);
       if (e == cudaSuccess) e = cudaEventRecord(c.done, c.stream);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(B->stream, c.done, 0);
     }
@@ -329,6 +222,8 @@ pcg_status run_batch(pcg_batch* B, int mask, double tol, int maxit) {
       return PCG_ECUDA;
     }
     B->graph_key = key;
+    for (int k = 0; k < kNumClasses; ++k)
+      if (key.occ[k]) B->cls[k].occ_used = key.occ[k];
   }
   if (cudaEventRecord(B->e0, B->stream) != cudaSuccess) return PCG_ECUDA;
   if (cudaGraphLaunch(B->graph, B->stream) != cudaSuccess) {
@@ -613,31 +508,38 @@ pcg_status pcg_batch_autotune(pcg_batch* B, const double* const* b, const double
     for (int k = 0; k < kNumClasses; ++k) B->cls[k].csize = saved[k];
     return PCG_ECUDA;
   }
-  // 2. each size class alone: its fastest cluster size (the per-class shape cache)
+  // 2. each size class alone: its fastest cluster size and kernel variant (2 or 4 resident
+  //    blocks per SM) -- the per-class shape cache
   for (SizeClass& sc : B->cls) sc.csize = best_c;
   for (int k = 0; k < kNumClasses; ++k) {
     SizeClass& sc = B->cls[k];
     if (sc.nsys == 0) continue;
+    const int saved_occ = sc.occ;
     double bk = INFINITY;
-    int ck = best_c;
+    int ck = best_c, ok = saved_occ;
     for (int ci = 0; ci < 5; ++ci) {
-      sc.csize = cand[ci];
-      pcg_status s = PCG_OK;
-      for (int j = 0; j < B->nsys; ++j) B->host_sys[j].sigma = sigma[j];
-      if (cudaMemcpyAsync(B->d_sys, B->host_sys.data(), B->nsys * sizeof(BatchSys), cudaMemcpyHostToDevice,
-                          B->stream) != cudaSuccess)
-        return PCG_ECUDA;
-      s = run_batch(B, 1 << k, 0.0, probe_iters);
-      if (s != PCG_OK) {
-        cudaGetLastError();
-        continue;
-      }
-      if (B->last_kernel_ms < bk) {
-        bk = B->last_kernel_ms;
-        ck = cand[ci];
+      for (int occ : {2, 4}) {
+        sc.csize = cand[ci];
+        sc.occ = occ;
+        pcg_status s = PCG_OK;
+        for (int j = 0; j < B->nsys; ++j) B->host_sys[j].sigma = sigma[j];
+        if (cudaMemcpyAsync(B->d_sys, B->host_sys.data(), B->nsys * sizeof(BatchSys), cudaMemcpyHostToDevice,
+                            B->stream) != cudaSuccess)
+          return PCG_ECUDA;
+        s = run_batch(B, 1 << k, 0.0, probe_iters);
+        if (s != PCG_OK) {
+          cudaGetLastError();
+          continue;
+        }
+        if (B->last_kernel_ms < bk) {
+          bk = B->last_kernel_ms;
+          ck = cand[ci];
+          ok = occ;
+        }
       }
     }
     sc.csize = ck;
+    sc.occ = ok;
   }
   B->tuned = 1;
   if (cluster_out) *cluster_out = best_c;
@@ -665,12 +567,20 @@ pcg_status pcg_batch_set_param(pcg_batch* B, int32_t param, double value) {
   return PCG_EINVAL;
 }
 
-pcg_status pcg_batch_classes(const pcg_batch* B, int32_t* nsys, int32_t* cluster) {
+pcg_status pcg_batch_classes(const pcg_batch* B, int32_t* nsys, int32_t* cluster, int32_t* blocks_per_sm) {
   if (!B) return PCG_EINVAL;
   for (int k = 0; k < kNumClasses; ++k) {
     if (nsys) nsys[k] = B->cls[k].nsys;
     if (cluster) cluster[k] = B->cls[k].csize;
+    if (blocks_per_sm) blocks_per_sm[k] = B->cls[k].occ ? B->cls[k].occ : B->cls[k].occ_used;
   }
+  return PCG_OK;
+}
+
+pcg_status pcg_batch_set_class_occupancy(pcg_batch* B, int32_t size_class, int32_t blocks_per_sm) {
+  if (!B || size_class < 0 || size_class >= kNumClasses) return PCG_EINVAL;
+  if (blocks_per_sm != 0 && blocks_per_sm != 2 && blocks_per_sm != 4) return PCG_EINVAL;
+  B->cls[size_class].occ = blocks_per_sm;
   return PCG_OK;
 }
 

@@ -89,8 +89,9 @@ def lib() -> ctypes.CDLL:
         L.pcg_batch_autotune.argtypes = [vp, vp, vp, i32, vp, vp]
         L.pcg_batch_set_cluster.argtypes = [vp, i32]
         L.pcg_batch_set_precision.argtypes = [vp, i32]
-        L.pcg_batch_classes.argtypes = [vp, vp, vp]
+        L.pcg_batch_classes.argtypes = [vp, vp, vp, vp]
         L.pcg_batch_set_class_cluster.argtypes = [vp, i32, i32]
+        L.pcg_batch_set_class_occupancy.argtypes = [vp, i32, i32]
         L.pcg_batch_set_param.argtypes = [vp, i32, f64]
         L.pcg_batch_last_kernel_ms.argtypes = [vp, ctypes.POINTER(f64)]
         L.pcg_batch_destroy.argtypes = [vp]
@@ -113,7 +114,7 @@ def lib() -> ctypes.CDLL:
                   "pcg_apply", "pcg_true_residual_noalloc", "pcg_set_param", "pcg_set_shifts", "pcg_convert_check", "pcg_psi_varsh",
                   "pcg_batch_create", "pcg_batch_solve", "pcg_batch_autotune", "pcg_batch_set_cluster",
                   "pcg_batch_set_precision", "pcg_batch_set_param", "pcg_batch_last_kernel_ms", "pcg_server_create",
-                  "pcg_batch_classes", "pcg_batch_set_class_cluster",
+                  "pcg_batch_classes", "pcg_batch_set_class_cluster", "pcg_batch_set_class_occupancy",
                   "pcg_submit", "pcg_submit_ex", "pcg_poll", "pcg_server_stats",
                   "pcg_kernel_stats", "pcg_kernel_stats_reset"):
             getattr(L, f).restype = st
@@ -412,14 +413,18 @@ class Batch:
         return lib().pcg_batch_set_cluster(self.h, c)
 
     def classes(self):
-        """(systems per size class, cluster size per class)."""
+        """(systems per size class, cluster size per class, resident blocks per SM per class)."""
         n = np.zeros(3, dtype=np.int32)
         c = np.zeros(3, dtype=np.int32)
-        lib().pcg_batch_classes(self.h, n.ctypes.data, c.ctypes.data)
-        return n, c
+        o = np.zeros(3, dtype=np.int32)
+        lib().pcg_batch_classes(self.h, n.ctypes.data, c.ctypes.data, o.ctypes.data)
+        return n, c, o
 
     def set_class_cluster(self, size_class: int, c: int) -> int:
         return lib().pcg_batch_set_class_cluster(self.h, size_class, c)
+
+    def set_class_occupancy(self, size_class: int, blocks_per_sm: int) -> int:
+        return lib().pcg_batch_set_class_occupancy(self.h, size_class, blocks_per_sm)
 
     def last_kernel_ms(self):
         v = ctypes.c_double()

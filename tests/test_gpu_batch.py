@@ -168,7 +168,8 @@ def test_batch_jacobi_rejects_zero_diagonal(B):
 def test_batch_size_classes_after_autotune(B):
     """Systems in all three size classes (n from 400 to 90,000) run concurrently, each class with
     the cluster size the autotuner picked for it; every result matches the single-system solver.
-    Cluster sizes set per class by hand give a new graph whose results also converge."""
+    Cluster sizes and kernel variants set per class by hand give new graphs whose results
+    also converge, bit-identical between the two variants."""
     sides = [20, 33, 47, 64, 90, 120, 181, 256, 300]
     probs = [S.laplacian_2d(L, L + 3) for L in sides]
     bs = [S.normal(300 + i, P.n) for i, P in enumerate(probs)]
@@ -176,20 +177,33 @@ def test_batch_size_classes_after_autotune(B):
     with B.Batch(probs) as bt:
         c, ms = bt.autotune(bs, sig, probe_iters=30)
         assert c in (1, 2, 4, 8, 16) and np.isfinite(ms).any()
-        nsys, csz = bt.classes()
+        nsys, csz, occ = bt.classes()
         assert nsys.tolist() == [4, 3, 2]                # n < 8192, < 65536, larger
         assert all(int(k) in (1, 2, 4, 8, 16) for k in csz)
+        assert all(int(k) in (2, 4) for k in occ)       # the autotuner's kernel variant per class
         xs, it, st, tr = bt.solve(bs, sig, tol=1e-9, maxit=20000)
         xs2, it2, _, _ = bt.solve(bs, sig, tol=1e-9, maxit=20000)      # the graph replayed
         assert bt.set_class_cluster(3, 2) == B.PCG_EINVAL
         assert bt.set_class_cluster(0, 3) == B.PCG_EINVAL
+        assert bt.set_class_occupancy(0, 3) == B.PCG_EINVAL
+        assert bt.set_class_occupancy(3, 2) == B.PCG_EINVAL
         for k, cs in enumerate((1, 4, 16)):
             assert bt.set_class_cluster(k, cs) == B.PCG_OK
         assert bt.classes()[1].tolist() == [1, 4, 16]
-        xs3, _, st3, _ = bt.solve(bs, sig, tol=1e-9, maxit=20000)      # a new graph
-    assert np.all(st3 == B.PCG_OK)
-    for P, b, x in zip(probs, bs, xs3):
-        assert np.linalg.norm(b - oracle.apply(P, x)) <= 3e-9 * np.linalg.norm(b)
+        runs = []
+        for occ in ((2, 4, 2), (4, 2, 4)):               # both kernel variants in every class
+            for k, o in enumerate(occ):
+                assert bt.set_class_occupancy(k, o) == B.PCG_OK
+            assert bt.classes()[2].tolist() == list(occ)
+            runs.append(bt.solve(bs, sig, tol=1e-9, maxit=20000))      # a new graph each
+    for xs3, it3, st3, _ in runs:
+        assert np.all(st3 == B.PCG_OK)
+        for P, b, x in zip(probs, bs, xs3):
+            assert np.linalg.norm(b - oracle.apply(P, x)) <= 3e-9 * np.linalg.norm(b)
+    # the variant changes registers, not arithmetic: the same iterates
+    assert np.array_equal(runs[0][1], runs[1][1])
+    for x0, x1 in zip(runs[0][0], runs[1][0]):
+        assert np.array_equal(x0, x1)
     assert np.all(st == B.PCG_OK)
     for P, b, x, x2, i, i2 in zip(probs, bs, xs, xs2, it, it2):
         assert i == i2 and np.array_equal(x, x2)
