@@ -114,6 +114,7 @@ BatchVecs vecs_of(pcg_batch* B) {
   const long long t = B->total;
   double* base = B->d_vec;
   BatchVecs V;
+  V.stride = t;
   V.b = base;
   V.x = base + t;
   V.r = base + 2 * t;

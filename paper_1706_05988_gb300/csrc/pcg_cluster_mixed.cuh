@@ -81,11 +81,11 @@ __device__ __forceinline__ void cluster_solve_jac(cg::cluster_group& cl, double 
   const unsigned rank = cl.block_rank(), C = cl.num_blocks();
   const Op op = make_op<F>(d);
   const double sigma = d.sigma;
-  const long long off = d.off;
-  const double* b = V.b + off;
-  const double* dinv = V.dinv + off;
-  double *x = V.x + off, *r = V.r + off, *w0 = V.w0 + off, *w1 = V.w1 + off, *z = V.z + off, *s = V.s + off,
-         *p = V.p + off, *u = V.u + off, *qv = V.q + off, *t = V.t + off, *m0 = V.m0 + off, *m1 = V.m1 + off;
+  // vector k at b + k * stride (see cluster_solve_mx); addresses formed where used
+  double* const vb = const_cast<double*>(V.b) + d.off;
+  long long stride = V.stride;
+  auto dv = [&](int k) { return vb + (long long)k * stride; };
+  const double* b = vb;
   const unsigned nc = (unsigned)d.n;
   const auto stp = op.step(C * kBlock);
   const int first = (int)(rank * kBlock + threadIdx.x);
@@ -94,9 +94,9 @@ __device__ __forceinline__ void cluster_solve_jac(cg::cluster_group& cl, double 
   double bb = 0.0;
   for (unsigned i = first; i < nc; i += C * kBlock) {
     const double bv = b[i];
-    r[i] = bv;
-    u[i] = dinv[i] * bv;
-    x[i] = 0.0;
+    dv(2)[i] = bv;
+    dv(8)[i] = dv(14)[i] * bv;
+    dv(1)[i] = 0.0;
     bb = fma(bv, bv, bb);
   }
   double t1[1] = {bb}, o1[1];
@@ -108,18 +108,19 @@ __device__ __forceinline__ void cluster_solve_jac(cg::cluster_group& cl, double 
   // w_0 = A u_0 - sigma r_0, m_0 = D^{-1} w_0; z = q = s = t = p = 0
   double ru = 0.0, wu = 0.0, rr = 0.0;
   for (auto q = op.cursor(first); q.c0 < nc; op.advance(q, stp)) {
+    asm volatile("" : "+l"(stride));
     const unsigned c = q.c0;
     double uc[1], au[1];
-    op.apply(u, q, uc, au);
-    const double rc = r[c];
+    op.apply(dv(8), q, uc, au);
+    const double rc = dv(2)[c];
     const double wv = fma(-sigma, rc, au[0]);
-    w0[c] = wv;
-    m0[c] = dinv[c] * wv;
-    z[c] = 0.0;
-    qv[c] = 0.0;
-    s[c] = 0.0;
-    t[c] = 0.0;
-    p[c] = 0.0;
+    dv(3)[c] = wv;
+    dv(11)[c] = dv(14)[c] * wv;
+    dv(5)[c] = 0.0;
+    dv(9)[c] = 0.0;
+    dv(6)[c] = 0.0;
+    dv(10)[c] = 0.0;
+    dv(7)[c] = 0.0;
     ru = fma(rc, uc[0], ru);
     wu = fma(wv, uc[0], wu);
     rr = fma(rc, rc, rr);
@@ -143,12 +144,23 @@ __device__ __forceinline__ void cluster_solve_jac(cg::cluster_group& cl, double 
   }
   while (status == ST_RUNNING) {
     const double asg = alpha * sigma;
-    const double* __restrict__ w = (it & 1) ? w1 : w0;
-    double* __restrict__ wn = (it & 1) ? w0 : w1;
-    const double* __restrict__ m = (it & 1) ? m1 : m0;
-    double* __restrict__ mn = (it & 1) ? m0 : m1;
+    const int odd = it & 1;
     ru = wu = rr = 0.0;
     for (auto q = op.cursor(first); q.c0 < nc; op.advance(q, stp)) {
+      asm volatile("" : "+l"(stride));
+      const double* __restrict__ w = dv(odd ? 4 : 3);
+      double* __restrict__ wn = dv(odd ? 3 : 4);
+      const double* __restrict__ m = dv(odd ? 12 : 11);
+      double* __restrict__ mn = dv(odd ? 11 : 12);
+      double* __restrict__ x = dv(1);
+      double* __restrict__ r = dv(2);
+      double* __restrict__ z = dv(5);
+      double* __restrict__ s = dv(6);
+      double* __restrict__ p = dv(7);
+      double* __restrict__ u = dv(8);
+      double* __restrict__ qv = dv(9);
+      double* __restrict__ t = dv(10);
+      const double* __restrict__ dinv = dv(14);
       const unsigned c = q.c0;
       double mc[1], nv[1];
       op.apply(m, q, mc, nv);
@@ -201,7 +213,7 @@ __device__ __forceinline__ void cluster_solve_jac(cg::cluster_group& cl, double 
   res.iters = it;
   res.status = status;
   res.bnorm = bnorm;
-  res.true_res = cluster_true_res<F>(cl, part, slot, op, b, x, nc, first, stp);
+  res.true_res = cluster_true_res<F>(cl, part, slot, op, b, dv(1), nc, first, stp);
 }
 
 // Mixed precision with restarts (M = I, or M^{-1} = D^{-1} when JAC), x_0 = 0.
@@ -221,37 +233,26 @@ __device__ __forceinline__ void cluster_solve_mx(cg::cluster_group& cl, double (
   const Op op = make_op<F>(d);
   const Op32 op32 = make_op32<F, VW>(d);
   const double sigma = d.sigma;
-  const long long off = d.off;
-  const double* b = V.b + off;
-  double *x = V.x + off, *r = V.r + off;
-  float* const wb0 = reinterpret_cast<float*>(V.w0 + off);
-  float* const wb1 = reinterpret_cast<float*>(V.w1 + off);
-  float* const zf = reinterpret_cast<float*>(V.z + off);
-  float* const sf = reinterpret_cast<float*>(V.s + off);
-  float* const pf = reinterpret_cast<float*>(V.p + off);
-  float *uf = nullptr, *qf = nullptr, *tf = nullptr, *mb0 = nullptr, *mb1 = nullptr;
-  const double* dinv = nullptr;
-  const float* d32 = nullptr;
-  double* u64 = nullptr;
-  if constexpr (JAC) {
-    uf = reinterpret_cast<float*>(V.u + off);
-    qf = reinterpret_cast<float*>(V.q + off);
-    tf = reinterpret_cast<float*>(V.t + off);
-    mb0 = reinterpret_cast<float*>(V.m0 + off);
-    mb1 = reinterpret_cast<float*>(V.m1 + off);
-    dinv = V.dinv + off;
-    d32 = reinterpret_cast<const float*>(V.dinv32 + off);
-    u64 = V.u64 + off;
-  }
+  // Every vector of the layout lies at b + k * stride (k: b 0, x 1, r 2, w0 3, w1 4, z 5, s 6,
+  // p 7, u 8, q 9, t 10, m0 11, m1 12, u64 13, dinv 14, dinv32 15).  The addresses are formed
+  // from that base and stride where they are used: `stride` is re-declared opaque at the top
+  // of every sweep (an empty asm), so no per-vector address stays live across the solve and
+  // the registers go to the unknowns in flight instead.
+  double* const vb = const_cast<double*>(V.b) + d.off;
+  long long stride = V.stride;
+  auto dv = [&](int k) { return vb + (long long)k * stride; };
+  auto fv = [&](int k) { return reinterpret_cast<float*>(vb + (long long)k * stride); };
+  const double* b = vb;
   const unsigned nc = (unsigned)d.n;
   const auto stp = op.step(C * kBlock);
   const auto stp32 = op32.step(C * kBlock);
   const int first = (int)(rank * kBlock + threadIdx.x);
 
   double bb = 0.0;
+  double* const x0 = dv(1);
   for (unsigned i = first; i < nc; i += C * kBlock) {
     const double bv = b[i];
-    x[i] = 0.0;
+    x0[i] = 0.0;
     bb = fma(bv, bv, bb);
   }
   double t1[1] = {bb}, o1[1];
@@ -265,16 +266,17 @@ __device__ __forceinline__ void cluster_solve_mx(cg::cluster_group& cl, double (
     // restart, part 1: r = b - A x (binary64); JAC: u = D^{-1} r rounded to binary32
     double rr = 0.0;
     for (auto q = op.cursor(first); q.c0 < nc; op.advance(q, stp)) {
+      asm volatile("" : "+l"(stride));
       const unsigned c = q.c0;
       double xc[1], ax[1];
-      op.apply(x, q, xc, ax);
+      op.apply(dv(1), q, xc, ax);
       const double rv = b[c] - ax[0];
-      r[c] = rv;
+      dv(2)[c] = rv;
       rr = fma(rv, rv, rr);
       if constexpr (JAC) {
-        const float u32 = f32_of(dinv[c] * rv);
-        uf[c] = u32;
-        u64[c] = f64_of(u32);
+        const float u32 = f32_of(dv(14)[c] * rv);
+        fv(8)[c] = u32;
+        dv(13)[c] = f64_of(u32);
       }
     }
     double t2[1] = {rr}, o2[1];
@@ -296,19 +298,20 @@ __device__ __forceinline__ void cluster_solve_mx(cg::cluster_group& cl, double (
     // restart, part 2: w_0 = A u_0 - sigma r (binary64 operator), auxiliary vectors zero
     double g = 0.0, o = 0.0, rr0 = 0.0;
     for (auto q = op.cursor(first); q.c0 < nc; op.advance(q, stp)) {
+      asm volatile("" : "+l"(stride));
       const unsigned c = q.c0;
       double uc[1], au[1];
-      op.apply(JAC ? u64 : r, q, uc, au);
-      const double rv = r[c];
+      op.apply(dv(JAC ? 13 : 2), q, uc, au);
+      const double rv = dv(2)[c];
       const float w32 = f32_of(fma(-sigma, rv, au[0]));
-      (par ? wb1 : wb0)[c] = w32;
-      zf[c] = 0.f;
-      sf[c] = 0.f;
-      pf[c] = 0.f;
+      fv(par ? 4 : 3)[c] = w32;
+      fv(5)[c] = 0.f;
+      fv(6)[c] = 0.f;
+      fv(7)[c] = 0.f;
       if constexpr (JAC) {
-        (par ? mb1 : mb0)[c] = d32[c] * w32;
-        qf[c] = 0.f;
-        tf[c] = 0.f;
+        fv(par ? 12 : 11)[c] = fv(15)[c] * w32;
+        fv(9)[c] = 0.f;
+        fv(10)[c] = 0.f;
       }
       g = fma(rv, uc[0], g);
       o = fma(f64_of(w32), uc[0], o);
@@ -327,12 +330,22 @@ __device__ __forceinline__ void cluster_solve_mx(cg::cluster_group& cl, double (
     for (;;) {
       const double asg = alpha * sigma;
       const float alpha32 = f32_of(alpha), beta32 = f32_of(beta), asg32 = f32_of(asg);
-      const float* __restrict__ w = par ? wb1 : wb0;
-      float* __restrict__ wn = par ? wb0 : wb1;
-      const float* __restrict__ m = par ? mb1 : mb0;
-      float* __restrict__ mn = par ? mb0 : mb1;
       double ru = 0.0, wu = 0.0, rn2 = 0.0;
       for (auto q = op32.cursor(first); q.c0 < nc; op32.advance(q, stp32)) {
+        asm volatile("" : "+l"(stride));
+        const float* __restrict__ w = fv(par ? 4 : 3);
+        float* __restrict__ wn = fv(par ? 3 : 4);
+        const float* __restrict__ m = fv(par ? 12 : 11);
+        float* __restrict__ mn = fv(par ? 11 : 12);
+        float* __restrict__ zf = fv(5);
+        float* __restrict__ sf = fv(6);
+        float* __restrict__ pf = fv(7);
+        float* __restrict__ uf = fv(8);
+        float* __restrict__ qf = fv(9);
+        float* __restrict__ tf = fv(10);
+        const float* __restrict__ d32 = fv(15);
+        double* __restrict__ r = dv(2);
+        double* __restrict__ x = dv(1);
         const unsigned c = q.c0;
         float mc[VW], nv[VW], wc[VW], zz[VW], ss[VW], pp[VW], w1[VW];
         double rc[VW], xv[VW];
@@ -413,7 +426,7 @@ __device__ __forceinline__ void cluster_solve_mx(cg::cluster_group& cl, double (
       gamma = gn;
     }
     if (it >= maxit) {
-      true_res = cluster_true_res<F>(cl, part, slot, op, b, x, nc, first, stp);
+      true_res = cluster_true_res<F>(cl, part, slot, op, b, dv(1), nc, first, stp);
       status = true_res <= tol_abs ? ST_CONVERGED : ST_MAXIT;
       break;
     }

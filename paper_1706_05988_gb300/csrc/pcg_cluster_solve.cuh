@@ -44,6 +44,7 @@ struct BatchVecs {
   double *u, *q, *t, *m0, *m1, *u64;   // Jacobi only (u64: binary64 scratch of a mixed restart)
   const double* dinv;                  // Jacobi: D^{-1}
   const double* dinv32;                // Jacobi, mixed: D^{-1} rounded to binary32 (binary32 slot)
+  long long stride;                    // vector k of this list lies at b + k * stride
 };
 
 

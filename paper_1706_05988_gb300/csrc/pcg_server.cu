@@ -338,6 +338,7 @@ pcg_status upload(pcg_server* S, Request* R, bool staged) {
   w->eta = pcgk::kClusterMixedEta;
   w->tol = R->tol;
   w->sys = d;
+  w->vec.stride = npad;
   w->vec.b = v;
   w->vec.x = v + npad;
   w->vec.r = v + 2 * npad;
