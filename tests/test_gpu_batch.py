@@ -226,3 +226,39 @@ def test_batch_mixed_wide_sweeps(B):
         for P, b, x, code in zip(probs, bs, xs, st):
             assert code == B.PCG_OK
             assert np.linalg.norm(b - oracle.apply(P, x)) <= 1e-8 * np.linalg.norm(b)
+
+
+FAMILIES = {
+    "lapl2d": lambda: [S.laplacian_2d(40, 30), S.laplacian_2d(64, 20), S.laplacian_2d(17, 33)],
+    "var2d": lambda: [S.varcoef_2d(a, b, lo_exp=-1.0, hi_exp=1.0, seed=81 + i)
+                      for i, (a, b) in enumerate(((40, 30), (64, 20), (17, 33)))],
+    "lapl3d": lambda: [S.laplacian_3d(12), S.laplacian_3d(16), S.laplacian_3d(9)],
+    "var3d": lambda: [S.varcoef_3d(n, block=4, lo_exp=-1.0, hi_exp=1.0, seed=84 + n) for n in (12, 16)],
+    "csr": lambda: [S.random_sdd_csr(n, seed=n) for n in (700, 1500)],
+}
+
+
+@pytest.mark.parametrize("family", list(FAMILIES))
+def test_register_variants_agree(B, family):
+    """Every operator family and every form (binary64 or mixed, M = I or Jacobi) through the
+    batch kernel compiled for 2 and for 4 resident blocks per SM: bit-identical iterates,
+    each near its tolerance against the oracle's operator (coefficient contrast 10^[-1, 1],
+    at which the binary32 sweeps without Jacobi still converge)."""
+    from paper_1706_05988_gb300 import pcg as C
+    probs = FAMILIES[family]()
+    bs = [S.normal(500 + i, P.n) for i, P in enumerate(probs)]
+    for jac in (False, True):
+        for prec in (C.PCG_FP64, C.PCG_MIXED_IR):
+            sig = [1.0] * len(probs) if jac else [shift(P) for P in probs]
+            runs = []
+            with B.Batch(probs, flags=B.PCG_JACOBI if jac else 0, precision=prec) as bt:
+                for occ in (2, 4):
+                    for k in range(3):
+                        assert bt.set_class_occupancy(k, occ) == B.PCG_OK
+                    runs.append(bt.solve(bs, sig, tol=1e-8, maxit=20000))
+            (x2, i2, s2, _), (x4, i4, s4, _) = runs
+            assert np.all(s2 == B.PCG_OK) and np.array_equal(s2, s4), (jac, prec, s2, s4)
+            assert np.array_equal(i2, i4), (jac, prec)
+            for P, b, a, c in zip(probs, bs, x2, x4):
+                assert np.array_equal(a, c)
+                assert np.linalg.norm(b - oracle.apply(P, a)) <= 3e-8 * np.linalg.norm(b)
