@@ -441,17 +441,17 @@ __device__ __forceinline__ void cluster_solve_mx(cg::cluster_group& cl, double (
 // row length allows: four with M = I, two with Jacobi (twice the vectors).  On 512 2D systems
 // with Jacobi and 4 resident blocks per SM, two unknowns per thread gave 109.2 solves/s and
 // one gave 103.  The batched launch and the serving kernel's large lane use this; its small
-// lane keeps one per thread.
-template <int F, bool JAC>
-__device__ __forceinline__ void cluster_solve_mx_auto(cg::cluster_group& cl, double (*part)[4], int& slot,
-                                                      const BatchSys& d, const BatchVecs& V, double tol, int maxit,
-                                                      double eta, int max_restarts, BatchOut& res) {
+// lane keeps one per thread.  The widths can be set at build time (1, 2 or 4).
 #ifndef PCG_CLUSTER_MX_JAC_VW
 #define PCG_CLUSTER_MX_JAC_VW 2
 #endif
 #ifndef PCG_CLUSTER_MX_VW
 #define PCG_CLUSTER_MX_VW 4
 #endif
+template <int F, bool JAC>
+__device__ __forceinline__ void cluster_solve_mx_auto(cg::cluster_group& cl, double (*part)[4], int& slot,
+                                                      const BatchSys& d, const BatchVecs& V, double tol, int maxit,
+                                                      double eta, int max_restarts, BatchOut& res) {
   constexpr int W = JAC ? PCG_CLUSTER_MX_JAC_VW : PCG_CLUSTER_MX_VW;
   if constexpr (F != 4 && W > 1) {
     if (d.nx % W == 0) {
