@@ -88,6 +88,9 @@ def test_argument_errors_of_the_extensions_without_gpu(libpath):
     assert L.pcg_psi_varsh(None, None, None, 10, None, 12, 1, None) == B.PCG_EINVAL
     assert L.pcg_batch_set_precision(None, B.PCG_MIXED_IR) == B.PCG_EINVAL
     assert L.pcg_batch_set_param(None, B.PCG_PARAM_MIXED_ETA, 0.5) == B.PCG_EINVAL
+    assert L.pcg_batch_classes(None, None, None, None) == B.PCG_EINVAL
+    assert L.pcg_batch_set_class_cluster(None, 0, 2) == B.PCG_EINVAL
+    assert L.pcg_batch_set_class_occupancy(None, 0, 4) == B.PCG_EINVAL
     out = vp(1)
     assert L.pcg_batch_create(None, 1, 0, ctypes.byref(out)) == B.PCG_EINVAL
     m = B.pcg_matrix()
