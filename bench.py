@@ -164,7 +164,19 @@ def cpu_oracle_rate(P, b, iters: int) -> tuple[float, float]:
     return iters / dt, dt
 
 
-def batch_measure(pkg, S, nsys: int, side_hi: int, forms=("fp64_jacobi", "mixed_jacobi"), seed: int = 0) -> dict:
+# Algorithmic bytes per unknown and iteration of the per-cluster solvers on 2D variable-
+# coefficient systems (vectors and face coefficients read once and written once per sweep):
+#   fp64 (M = I): reads w, 3 coefficient arrays, z, s, p, r, x (72 B); writes z, s, p, x, r, w' (48 B)
+#   fp64_jacobi: reads m, 3 coefficients, w, r, u, t, s, z, p, q, x, D^-1 (112 B); writes t, s, z,
+#                p, q, x, r, u, w', m' (80 B)
+#   mixed_jacobi: binary32 m, 3 coefficients, w, z, s, p, u, t, q, D^-1 and binary64 r, x (64 B);
+#                 writes binary32 z, s, p, u, t, q, w', m' and binary64 r, x (48 B)
+# Small systems keep their vectors in L2, so these are algorithmic, not DRAM, bytes.
+BATCH_BYTES_PER_UNKNOWN_ITER = {"fp64": 120, "fp64_jacobi": 192, "mixed_jacobi": 112}
+
+
+def batch_measure(pkg, S, nsys: int, side_hi: int, forms=("fp64_jacobi", "mixed_jacobi"), seed: int = 0,
+                  peak_gbs: float = None) -> dict:
     """Solves/s of nsys 2D FV systems (sides U{32..side_hi}, kappa = 10^U[-2,2] per cell, b ~ N(0,1),
     tol 1e-8) in one batched launch, in the given forms: `fp64` (M = I, sigma = half the median
     diagonal), `fp64_jacobi` and `mixed_jacobi` (Jacobi M^-1, sigma = 1; mixed precision with FP64
@@ -196,6 +208,12 @@ def batch_measure(pkg, S, nsys: int, side_hi: int, forms=("fp64_jacobi", "mixed_
                          "converged": int(np.sum(st == 0)), "max_true_relres": float(np.max(tr)),
                          "mean_iters": float(np.mean(it)),
                          "unknown_iterations": float(np.sum(it.astype(np.float64) * np.array([P.n for P in probs])))}
+            ui_s = out[name]["unknown_iterations"] / tb
+            gbs = ui_s * BATCH_BYTES_PER_UNKNOWN_ITER[name] / 1e9
+            out[name].update({"unknown_iterations_per_s": ui_s, "algorithmic_gbs": gbs,
+                              "bytes_per_unknown_iteration": BATCH_BYTES_PER_UNKNOWN_ITER[name]})
+            if peak_gbs:
+                out[name]["frac_of_hbm"] = gbs / peak_gbs
     k = min(nsys, 16)
     idx = np.linspace(0, nsys - 1, k).astype(int)
     t1 = 0.0
@@ -547,7 +565,7 @@ def run_ours(args):
     # batch of independent 2D variable-coefficient systems in one persistent launch vs one at a time
     batch = None
     if not args.no_batch and world == 1:   # side measurements: single-GPU runs only
-        batch = batch_measure(pkg, S, args.batch_systems, args.batch_side_max)
+        batch = batch_measure(pkg, S, args.batch_systems, args.batch_side_max, peak_gbs=peak)
 
     varcoef = None
     if not args.no_varcoef and world == 1:   # side measurements: single-GPU runs only
