@@ -236,8 +236,9 @@ pcg_status pcg_batch_solve(pcg_batch *batch, const double *const *b, double *con
 /* Autotuner: times probe_iters iterations of the whole batch with one cluster size in
  * {1, 2, 4, 8, 16} for every class (ms_out[5], may be NULL: the time of each candidate,
  * NaN where a size cannot be launched; cluster_out, may be NULL: the fastest), then
- * times each size class alone for every candidate and keeps the fastest size per
- * class for later solves.  pcg_batch_set_cluster sets one size for every class. */
+ * times each size class alone for every candidate size and both register variants of
+ * its kernel (see pcg_batch_classes) and keeps the fastest pair per class for later
+ * solves.  pcg_batch_set_cluster sets one size for every class. */
 pcg_status pcg_batch_autotune(pcg_batch *batch, const double *const *b, const double *sigma, int32_t probe_iters,
                               int32_t *cluster_out, double *ms_out);
 pcg_status pcg_batch_set_cluster(pcg_batch *batch, int32_t cluster_size);
