@@ -60,6 +60,20 @@ struct pcg_ctx {
   int64_t launches = 0, iter_launches = 0;
   double iter_ms = 0.0;
   std::vector<cudaEvent_t> ev;          // PCG_PROFILE: pairs around iteration launches
+  // Launch-per-iteration path without profiling: kIterGraphLen launches of the fused
+  // iteration kernel captured once as a CUDA graph and replayed (the launches are
+  // identical: the iteration index lives in device memory).  Rebuilt when a launch
+  // argument changes.
+  cudaGraphExec_t iter_graph = nullptr;
+  struct IterGraphKey {
+    OpDesc op;
+    Vecs v;
+    Hist h;
+    State* st;
+    double* partials;
+    cudaStream_t stream;
+    int grid;
+  } iter_key;
   std::string err;
 };
 
@@ -317,6 +331,7 @@ void pcg_destroy(pcg_ctx* c) {
   cudaGetDevice(&prev);
   cudaSetDevice(c->device);
   if (c->own_stream) cudaStreamSynchronize(c->own_stream);
+  if (c->iter_graph) cudaGraphExecDestroy(c->iter_graph);
   for (void* p : c->owned) cudaFree(p);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   if (c->h_state) cudaFreeHost(c->h_state);
@@ -391,6 +406,51 @@ pcg_status pcg_kernel_stats_reset(pcg_ctx* c) {
 
 namespace {
 
+constexpr int kIterGraphLen = 32;
+
+// The graph of kIterGraphLen iteration launches for the current launch arguments (built
+// on first use).  PCG_ENOTIMPL when the stream cannot be captured (the legacy default
+// stream): the caller then launches directly.
+pcg_status ensure_iter_graph(pcg_ctx* c) {
+  pcg_ctx::IterGraphKey key;
+  memset(&key, 0, sizeof key);
+  key.op = c->op;
+  key.v = c->v;
+  key.h = c->h;
+  key.st = c->d_state;
+  key.partials = c->d_partials;
+  key.stream = c->stream;
+  key.grid = c->grid[K_SPCG_ITER];
+  if (c->iter_graph && memcmp(&key, &c->iter_key, sizeof key) == 0) return PCG_OK;
+  if (c->iter_graph) {
+    cudaGraphExecDestroy(c->iter_graph);
+    c->iter_graph = nullptr;
+  }
+  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return PCG_ENOTIMPL;
+  }
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < kIterGraphLen && e == cudaSuccess; ++k)
+    e = launch_spcg_iter(c->op, launch_of(c, K_SPCG_ITER), c->v, c->d_state, c->h, c->d_partials);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
+  if (e != cudaSuccess || ee != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return PCG_ENOTIMPL;
+  }
+  e = cudaGraphInstantiate(&c->iter_graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    c->iter_graph = nullptr;
+    cudaGetLastError();
+    return PCG_ENOTIMPL;
+  }
+  memcpy(&c->iter_key, &key, sizeof key);
+  return PCG_OK;
+}
+
 // The launch sequence of one solve.  b (device, 16-byte aligned or the
 // context's copy), x0 already placed in v.x when has_x0.
 pcg_status run_solve(pcg_ctx* c, bool has_x0, int method, double sigma, double tol, int maxit, int true_every,
@@ -452,7 +512,17 @@ pcg_status run_solve(pcg_ctx* c, bool has_x0, int method, double sigma, double t
   while (done < maxit) {
     const bool poll = tol > 0.0 || (c->true_tol > 0.0 && true_every > 0);   // the solve may stop early
     const int todo = poll ? std::min(chunk, maxit - done) : maxit - done;
-    for (int k = 0; k < todo; ++k) {
+    int k = 0;
+    if (!cg && !profile && true_every <= 0 && todo >= kIterGraphLen && ensure_iter_graph(c) == PCG_OK) {
+      // whole graphs of kIterGraphLen iterations; the remainder is launched directly below
+      for (; k + kIterGraphLen <= todo; k += kIterGraphLen) {
+        CUDA_TRY(c, cudaGraphLaunch(c->iter_graph, c->stream));
+        c->launches += kIterGraphLen;
+        c->iter_launches += kIterGraphLen;
+        done += kIterGraphLen;
+      }
+    }
+    for (; k < todo; ++k) {
       if (cg) {
         CUDA_TRY(c, launch_cg_spmv(c->op, L(K_CG_SPMV), c->v, c->d_state, c->h, c->d_partials));
         CUDA_TRY(c, launch_cg_update(c->op, L(K_CG_UPDATE), c->v, c->d_state, c->h, c->d_partials));

@@ -296,6 +296,28 @@ def test_deterministic_and_pcg_is_sigma0(B):
     assert np.array_equal(a.x, p.x) and np.array_equal(a.rec, p.rec)
 
 
+def test_graph_replay_matches_direct_launches(B):
+    """Without profiling and true-residual logging, the iteration launches are replayed from
+    a CUDA graph of 32; with logging (here never due) they are launched one by one.  The
+    kernel is the same, so iterates, histories and stop iteration are bit-identical, for a
+    fixed count (graphs plus a ragged remainder) and for a tolerance stop (polled chunks)."""
+    P, b, _ = S.poisson2d_manufactured(100)
+    with B.Solver(P) as s:
+        for tol, maxit in ((0.0, 203), (1e-9, 5000)):
+            g = s.solve(b, method="spcg", sigma=4.0, tol=tol, maxit=maxit, true_every=0)
+            d = s.solve(b, method="spcg", sigma=4.0, tol=tol, maxit=maxit, true_every=maxit + 1)
+            assert g.iters == d.iters and g.status == d.status
+            assert np.array_equal(g.x, d.x)
+            k = g.iters + 1
+            assert np.array_equal(g.alpha[:k], d.alpha[:k]) and np.array_equal(g.rec[:k], d.rec[:k])
+        assert g.iters < 5000
+        # a second context on the same problem rebuilds nothing of the first one's graph
+        with B.Solver(P) as s2:
+            g2 = s2.solve(b, method="spcg", sigma=4.0, tol=0.0, maxit=203, true_every=0)
+        g3 = s.solve(b, method="spcg", sigma=4.0, tol=0.0, maxit=203, true_every=0)
+        assert np.array_equal(g2.x, g3.x)
+
+
 def test_device_entry_point_matches_host(B):
     import torch
     P, b, _ = S.poisson3d_manufactured(24)
