@@ -15,6 +15,12 @@ Contents
   pcg_sh(...)      Algorithm 3, shifted pipelined CG
   psi / select_sigma   Section 3.2, Eq. (functionpsi)        -> oracle.psi
   exact rational CG / p-CG-sh for tiny systems               -> oracle.exact
+
+Every function above is pinned by tests/test_oracle.py (exact arithmetic, closed forms,
+library routines, the values Table 1 and Section 5.1 print).  Parity unpinned: the level
+at which unshifted p-CG (Algorithm 2) stalls on lapl200, which Table 1 prints as 3.1e-7.
+It depends on rounding after the iteration has lost its way; only its order relative to
+CG (at least 100 times higher) is tested.
 """
 from __future__ import annotations
 

@@ -28,6 +28,11 @@
  *     a non-finite or non-positive delta, or denominator of alpha, is a breakdown.
  *   - Dots and norms are plain left-to-right sums.
  *
+ * Pins: every routine is checked by tests/test_oracle.py.  Parity unpinned: the
+ * level at which oracle_pcg (unshifted) stalls on lapl200, printed as 3.1e-7 in
+ * Table 1; it depends on rounding after the iteration has lost its way, and only
+ * its order relative to CG is tested.
+ *
  * All history arrays are optional (NULL) and, when given, hold maxit+1 entries.
  * Index conventions (both methods): alpha[i], beta[i] are the scalars used in
  * iteration i (beta[0] = 0); rec[i] = ||r_i||_2 (recursive residual);
