@@ -637,7 +637,8 @@ def run_ours(args):
 
 def profile_case(kind: str, n: int) -> int:
     """A short solve for an ncu capture (no timing, no JSON): `spcg` runs 8 iterations of the
-    main kernel on the n^3 Laplacian; `jacobi-fp64` and `jacobi-mixed` run 12 iterations of the
+    main kernel on the n^3 Laplacian (`-split32`: with the dots on the FP32 pipe; `-staged`: the
+    TMA-staged sweep with a ring of 2 chunks); `jacobi-fp64` and `jacobi-mixed` run 12 iterations of the
     Jacobi sweeps (sigma = 1; the mixed one with eta = 1e-30, so no restart interrupts);
     `batch-*` run batched launches (see below)."""
     import synthetic as S
@@ -676,8 +677,10 @@ def profile_case(kind: str, n: int) -> int:
         print(kind, int(np.sum(st == 0)), float(np.mean(it)))
         return 0
     P, b = S.poisson3d_manufactured(n)[:2]
-    if kind == "spcg":
-        with pkg.Solver(P) as s:
+    if kind.startswith("spcg"):
+        with pkg.Solver(P, flags=pkg.PCG_DOTS_SPLIT32 if "split32" in kind else 0) as s:
+            if "staged" in kind:
+                C.pcg_set_param(s.ctx, C.PCG_PARAM_ITER_STAGES, 2.0)
             r = s.solve(b, method="spcg", sigma=6.0, maxit=8)
     else:
         with pkg.Solver(P, flags=pkg.PCG_JACOBI) as s:
@@ -692,7 +695,8 @@ def profile_case(kind: str, n: int) -> int:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile-case", choices=["spcg", "jacobi-fp64", "jacobi-mixed", "batch-fp64",
+    ap.add_argument("--profile-case", choices=["spcg", "spcg-split32", "spcg-staged", "spcg-staged-split32",
+                                               "jacobi-fp64", "jacobi-mixed", "batch-fp64",
                                                "batch-mixed-jacobi", "batch-large-fp64-jacobi",
                                                "batch-large-mixed-jacobi", "batch-large-mixed-jacobi-occ4"],
                     default=None,

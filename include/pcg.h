@@ -78,6 +78,18 @@ typedef enum { PCG_FP64 = 0, PCG_MIXED_IR = 1 } pcg_precision;
                                   term and rounded once to binary64; its error is at most
                                   0.5 ulp of the result plus 6 * 2^-6 ulp of the largest
                                   term, below the worst case of FP64 left-to-right summation */
+#define PCG_DOTS_SPLIT32 0x20u /* PCG_PCG / PCG_SPCG, FP64, M = I, constant shift, launch per
+                                  iteration: accumulate the merged dots (r,r) and (w,r) on the
+                                  FP32 pipe instead of with binary64 fused multiply-adds.  Each
+                                  value is split exactly (integer operations) into two binary32
+                                  parts after a power-of-two scale taken from the previous
+                                  iteration's norms, and the products are summed error-free
+                                  (TwoProd/TwoSum); about 2^-47 per term (1e-14 relative to the
+                                  sum on Laplacian runs, against 1e-15 for binary64).  Values
+                                  outside the scaled binary32 range are summed in binary64.
+                                  It frees 2 of the sweep's 9 FP64 operations per unknown but
+                                  adds about 50 integer/FP32 instructions; on GB300 the 256^3
+                                  sweep is then slower (0.34 against 0.29 ms), so it is opt-in */
 
 /*
  * The operator A.
@@ -327,7 +339,6 @@ pcg_status pcg_server_stats(pcg_server *server, int64_t *waiting, int64_t *infli
 /* Stops the kernel and releases everything (pending requests are dropped). */
 void pcg_server_destroy(pcg_server *server);
 
-/* Largest n accepted by pcg_true_residual_noalloc. */
 /* Self-check of the binary32 <-> binary64 conversions that the mixed-precision
  * kernels perform with integer operations (the paper has no counterpart):
  * f_out[i] = (float)d_in[i] (round to nearest even) and d_out[i] = (double)f_in[i],
@@ -335,6 +346,7 @@ void pcg_server_destroy(pcg_server *server);
  * Errors: PCG_EINVAL (n < 0 or a NULL array with n > 0), PCG_ECUDA. */
 pcg_status pcg_convert_check(const double *d_in, float *f_out, const float *f_in, double *d_out, int64_t n);
 
+/* Largest n accepted by pcg_true_residual_noalloc. */
 #define PCG_NOALLOC_MAX_N 16777216
 
 /* ||b - A x||_2 and ||(b - A x) - r||_2 without allocating anything.
@@ -351,13 +363,17 @@ pcg_status pcg_convert_check(const double *d_in, float *f_out, const float *f_in
  * The work is queued on `stream` (NULL = the default stream) and the call returns
  * without waiting; norms is valid once the stream reaches that point.
  * Scratch: one file-scope device array of 64 KiB (per-block partial sums and a
- * ticket), held by every GPU that loads this library until the process exits.  The
- * first call on a device looks up that array's address and caches it; make that
- * first call before any stream capture.  Every call shares the array: calls whose
+ * ticket), held by every GPU that loads this library until the process exits.  Every
+ * call made outside stream capture looks up that array's address in the current
+ * context (no device work) and keeps it for the device; a call on a capturing stream
+ * uses the address kept by the last call outside capture on that device.  So make
+ * one call outside capture before capturing, and again after anything that destroys
+ * and recreates the device's context (cudaDeviceReset).  Every call shares the array: calls whose
  * work overlaps on a GPU (other streams, other host threads) race and give wrong
  * norms; serialise them.  No cudaMalloc, cudaFree or other allocating call is made.
- * Errors: PCG_EINVAL for NULL pointers, an invalid description, misaligned vectors
- * or n > PCG_NOALLOC_MAX_N (16,777,216 unknowns); PCG_ECUDA if a CUDA call fails. */
+ * Errors: PCG_EINVAL for NULL pointers, an invalid description, a vector or norms
+ * not 8-byte aligned, b, x or r not 16-byte aligned where the operator reads two
+ * unknowns per thread (stencils with an even row length), or n > PCG_NOALLOC_MAX_N (16,777,216 unknowns); PCG_ECUDA if a CUDA call fails. */
 pcg_status pcg_true_residual_noalloc(const pcg_matrix *A, const double *b, const double *x, const double *r,
                                      double *norms, void *stream);
 
@@ -376,7 +392,7 @@ pcg_status pcg_set_shifts(pcg_ctx *ctx, const double *shifts, int32_t count);
  *                            logged true residual satisfies ||b - A x_i|| <= value ||b||
  *                            (the true residual is checked every true_every iterations);
  *                            0 (the default) turns it off
- *   PCG_PARAM_BARRIER_TIMEOUT_MS, PCG_PARAM_TEST_BARRIER_PHANTOMS: see below
+ *   PCG_PARAM_BARRIER_TIMEOUT_MS, PCG_PARAM_TEST_BARRIER_PHANTOMS, PCG_PARAM_ITER_STAGES: see below
  * Errors: PCG_EINVAL for an unknown parameter or a value out of range. */
 #define PCG_PARAM_MIXED_ETA 1
 #define PCG_PARAM_MAX_RESTARTS 2
@@ -386,7 +402,23 @@ pcg_status pcg_set_shifts(pcg_ctx *ctx, const double *shifts, int32_t count);
                                             barrier waits for this many arrivals that never
                                             come (0 = off, the default) */
 #define PCG_PARAM_TRUE_TOL 5
+#define PCG_PARAM_ITER_STAGES 6   /* the fused iteration of PCG_PCG / PCG_SPCG (FP64, M = I,
+                                     constant shift, launch per iteration) on a constant-
+                                     coefficient stencil with an even row length: 2 or 3 =
+                                     every operand of a block's chunk (z, s, p, x, r, and w's
+                                     rows with their neighbour rows and planes) is staged in
+                                     shared memory by TMA bulk copies, a ring of that many
+                                     chunks; 0 (default) = every thread loads its own
+                                     unknowns.  The staged ring takes 72 KB per block at
+                                     256^3, so 3 blocks fit on an SM instead of 4, and the
+                                     256^3 sweep is slower (0.33 against 0.29 ms) */
 pcg_status pcg_set_param(pcg_ctx *ctx, int32_t param, double value);
+
+/* The current value of a parameter of pcg_set_param.  For PCG_PARAM_ITER_STAGES this is the
+ * depth in use: 0 where the operator cannot be staged (CSR, variable coefficients, odd row
+ * length) or where two blocks' rings do not fit in one SM's shared memory.
+ * Errors: PCG_EINVAL for a NULL argument or an unknown parameter. */
+pcg_status pcg_get_param(const pcg_ctx *ctx, int32_t param, double *value);
 
 /* Kernel accounting of the context since creation (or the last reset):
  * total launches of every kernel of this library, and -- with PCG_PROFILE --

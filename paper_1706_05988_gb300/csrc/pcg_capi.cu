@@ -79,7 +79,11 @@ struct pcg_ctx {
 
 namespace {
 
-const char* kVersion = "libpcg 0.1 (sm_103a, FP64 shifted pipelined CG)";
+const char* kVersion = "libpcg 0.2 (sm_103a, FP64 shifted pipelined CG)";
+
+// Depth of the TMA-staged ring of the fused iteration (PCG_PARAM_ITER_STAGES); 0 = the
+// register sweep, which is the faster one on GB300 at every size measured.
+constexpr int kDefaultIterStages = 0;
 
 pcg_status fail(pcg_ctx* c, pcg_status s, const char* msg) {
   if (c) c->err = msg;
@@ -192,10 +196,13 @@ pcg_status pcg_create(const pcg_matrix* A, uint32_t flags, pcg_ctx** out) {
   if (!out) return PCG_EINVAL;
   *out = nullptr;
   if (!A) return PCG_EINVAL;
-  if (flags & ~(PCG_DEVICE_PTRS | PCG_PROFILE | PCG_STENCIL_FP64_SUM | PCG_PERSISTENT | PCG_JACOBI)) return PCG_EINVAL;
+  if (flags & ~(PCG_DEVICE_PTRS | PCG_PROFILE | PCG_STENCIL_FP64_SUM | PCG_PERSISTENT | PCG_JACOBI | PCG_DOTS_SPLIT32))
+    return PCG_EINVAL;
   OpDesc op{};
   op.layout = A->layout;
   op.fixed_sum = (flags & PCG_STENCIL_FP64_SUM) ? 0 : 1;
+  op.ff_dots = (flags & PCG_DOTS_SPLIT32) ? 1 : 0;
+  op.iter_stages = kDefaultIterStages;
   int64_t n = 0, nnz = 0;
   if (A->layout == PCG_STENCIL5_2D || A->layout == PCG_STENCIL7_3D) {
     const int64_t nz = A->layout == PCG_STENCIL7_3D ? A->nz : 1;
@@ -314,6 +321,7 @@ pcg_status pcg_create(const pcg_matrix* A, uint32_t flags, pcg_ctx** out) {
       return bail(fail(c, PCG_ECUDA, "could not size the persistent grid"));
     }
   }
+  c->op.iter_stages = resolve_iter_stages(c->op, c->op.iter_stages);
   for (int k = 0; k < K_NKINDS; ++k) {
     c->grid[k] = grid_for(c->op, k, kBlockThreads);
     if (c->grid[k] <= 0) {
@@ -378,12 +386,38 @@ pcg_status pcg_set_param(pcg_ctx* c, int32_t param, double value) {
       if (!(value >= 1.0 && value <= 1e6)) return fail(c, PCG_EINVAL, "max restarts must lie in [1, 1e6]");
       c->mx_max_restarts = (int)value;
       return PCG_OK;
+    case PCG_PARAM_ITER_STAGES: {
+      if (!(value == 0.0 || value == 2.0 || value == 3.0)) return fail(c, PCG_EINVAL, "stages must be 0, 2 or 3");
+      const int old_stages = c->op.iter_stages;
+      c->op.iter_stages = resolve_iter_stages(c->op, (int)value);
+      const int g = grid_for(c->op, K_SPCG_ITER, kBlockThreads);
+      if (g <= 0) {
+        cudaGetLastError();
+        c->op.iter_stages = old_stages;
+        return fail(c, PCG_ECUDA, "could not size the iteration grid");
+      }
+      c->grid[K_SPCG_ITER] = g;
+      return PCG_OK;
+    }
     case PCG_PARAM_TRUE_TOL:
       if (!(value >= 0.0) || !isfinite(value)) return fail(c, PCG_EINVAL, "true tolerance must be finite and >= 0");
       c->true_tol = value;
       return PCG_OK;
     default:
       return fail(c, PCG_EINVAL, "unknown parameter");
+  }
+}
+
+pcg_status pcg_get_param(const pcg_ctx* c, int32_t param, double* value) {
+  if (!c || !value) return PCG_EINVAL;
+  switch (param) {
+    case PCG_PARAM_MIXED_ETA: *value = c->mx_eta; return PCG_OK;
+    case PCG_PARAM_MAX_RESTARTS: *value = c->mx_max_restarts; return PCG_OK;
+    case PCG_PARAM_BARRIER_TIMEOUT_MS: *value = c->barrier_timeout_ms; return PCG_OK;
+    case PCG_PARAM_TEST_BARRIER_PHANTOMS: *value = c->barrier_phantoms; return PCG_OK;
+    case PCG_PARAM_TRUE_TOL: *value = c->true_tol; return PCG_OK;
+    case PCG_PARAM_ITER_STAGES: *value = c->op.iter_stages; return PCG_OK;
+    default: return PCG_EINVAL;
   }
 }
 
@@ -866,7 +900,8 @@ pcg_status solve_common(pcg_ctx* c, const double* b, const double* x0, int32_t m
   CUDA_TRY(c, cudaMemcpyAsync(x_out, c->v.x, bytes, outk, c->stream));
   pcg_status ret = st == ST_CONVERGED ? PCG_OK : st == ST_BREAKDOWN ? PCG_EBREAKDOWN
                    : st == ST_TIMEOUT ? PCG_ETIMEOUT : PCG_ENOTCONV;
-  if (st == ST_TIMEOUT) c->err = "a grid-barrier wait of the persistent kernel exceeded its time limit";
+  if (st == ST_TIMEOUT)
+    c->err = "a bounded device wait (the persistent kernel's grid barrier or a staged sweep's copy) exceeded its time limit";
   if (st == ST_STALLED) c->err = "iterative refinement stalled: a restart did not lower the true residual";
   if (res) {
     const size_t k = (size_t)iters + 1;

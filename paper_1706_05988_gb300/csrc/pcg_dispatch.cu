@@ -75,13 +75,22 @@ int op_vec(const OpDesc& d) {
   return 2;
 }
 
+int resolve_iter_stages(const OpDesc& d, int stages) {
+  int r = 0;
+  with_op(d, [&](auto op) {
+    r = K<decltype(op)>::iter_stages(op, stages);
+    return cudaSuccess;
+  });
+  return r;
+}
+
 int grid_for(const OpDesc& d, int kind, int block) {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   int per_sm = 0;
   with_op(d, [&](auto op) {
-    per_sm = K<decltype(op)>::blocks_per_sm(kind);
+    per_sm = K<decltype(op)>::blocks_per_sm(op, kind, d.iter_stages);
     return cudaSuccess;
   });
   if (per_sm <= 0) return 0;
@@ -102,7 +111,7 @@ cudaError_t launch_spcg_w0(const OpDesc& d, const Launch& L, Vecs v, State* st, 
   return with_op(d, [&](auto op) { return K<decltype(op)>::spcg_w0(op, L, v, st, h, partials); });
 }
 cudaError_t launch_spcg_iter(const OpDesc& d, const Launch& L, Vecs v, State* st, Hist h, double* partials) {
-  return with_op(d, [&](auto op) { return K<decltype(op)>::spcg_iter(op, L, v, st, h, partials); });
+  return with_op(d, [&](auto op) { return K<decltype(op)>::spcg_iter(op, L, v, st, h, partials, d.ff_dots != 0, d.iter_stages); });
 }
 cudaError_t launch_true_res(const OpDesc& d, const Launch& L, Vecs v, State* st, Hist h, double* partials) {
   return with_op(d, [&](auto op) { return K<decltype(op)>::true_res(op, L, v, st, h, partials); });

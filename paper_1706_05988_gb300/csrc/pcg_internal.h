@@ -35,6 +35,10 @@ struct State {
   unsigned int bar_gen;
   // stop once the logged true residual ||b - A x_i|| <= tol_true ||b|| (0: never)
   double tol_true;
+  // power-of-two scales of r and w for the next iteration's FP32-pipe dot products
+  // (pcg_ffdot.cuh), set by the finisher of Algorithm 3
+  int ff_sr;
+  int ff_sw;
 };
 
 // Per-iteration histories (device arrays of maxit + 1 entries).
@@ -47,6 +51,8 @@ struct Hist {
 struct OpDesc {
   int layout;            // 0 = 2D stencil, 1 = 3D stencil, 2 = CSR
   int fixed_sum;         // constant-coefficient stencil rows in fixed point (pcg_fixedsum.cuh)
+  int ff_dots;           // merged dots of the fused iteration on the FP32 pipe (pcg_ffdot.cuh)
+  int iter_stages;       // fused iteration: 0 = register sweep, 2 or 3 = TMA-staged ring of that depth
   int n, nx, ny, nz;
   const double *diag, *ax, *ay, *az;   // variable coefficients; diag == nullptr: Laplacian
   const int *row_ptr, *col;
@@ -70,6 +76,10 @@ struct Launch {
 // Number of vector lanes per thread the kernels use for this operator
 // (2 = 128-bit loads; needs an even row length for stencils).
 int op_vec(const OpDesc& op);
+
+// The staging depth the fused iteration uses for this operator when `stages` (0, 2 or 3)
+// is asked for: 0 where the operator cannot be staged or the ring does not fit twice per SM.
+int resolve_iter_stages(const OpDesc& op, int stages);
 
 // Resident-grid size of each kernel family for this operator (0 on error).
 int grid_for(const OpDesc& op, int kind, int block);

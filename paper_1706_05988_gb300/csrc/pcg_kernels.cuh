@@ -14,6 +14,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "pcg_ffdot.cuh"
+#include "pcg_tma.cuh"
 #include "pcg_fixedsum.cuh"
 #include "pcg_internal.h"
 
@@ -39,6 +41,9 @@ template <int DIM, int MODE, int VEC_>
 struct StencilOp {
   static constexpr int VEC = VEC_;
   static constexpr bool VAR = MODE == ST_VAR;
+  // the staged fused iteration (k_spcg_iter_tma) copies w's rows with 16-byte bulk copies
+  static constexpr bool STAGED = MODE != ST_VAR && VEC == 2;
+  static constexpr int DIMS = DIM;
   int n, nx, ny, nz, nxny;
   const double *diag, *ax, *ay, *az;
 
@@ -100,6 +105,35 @@ struct StencilOp {
     // x neighbours of the unit: left of the first, right of the last unknown
     const double xl = i0 > 0 ? __ldg(w + c0 - 1) : 0.0;
     const double xr = i0 + VEC < (unsigned)nx ? __ldg(w + c0 + VEC) : 0.0;
+    row(q, c, xl, xr, ym, yp, zm, zp, wc, aw);
+  }
+
+  // The same row from staged copies of w in shared memory (constant coefficients):
+  // `ctr` holds w from the unit's row minus nx (ctr[nx] = w[c0]), `zlo`/`zhi` w one
+  // plane below/above (zlo[0] = w[c0 - nxny], zhi[0] = w[c0 + nxny]).  Neighbours outside
+  // the grid read as 0, as in apply().
+  __device__ __forceinline__ void apply_staged(const double* ctr, const double* zlo, const double* zhi,
+                                               const Cursor& q, double (&wc)[VEC], double (&aw)[VEC]) const {
+    const unsigned i0 = q.i0, j = q.j, k = q.k;
+    const bool has_ym = j > 0, has_yp = j + 1 < (unsigned)ny;
+    const bool has_zm = DIM == 3 && k > 0, has_zp = DIM == 3 && k + 1 < (unsigned)nz;
+    double c[VEC], ym[VEC], yp[VEC], zm[VEC], zp[VEC];
+    lds<VEC>(ctr + nx, c);
+    lds_if<VEC>(has_ym, ctr, ym);
+    lds_if<VEC>(has_yp, ctr + 2 * nx, yp);
+    if (DIM == 3) {
+      lds_if<VEC>(has_zm, zlo, zm);
+      lds_if<VEC>(has_zp, zhi, zp);
+    }
+    const double xl = i0 > 0 ? ctr[nx - 1] : 0.0;
+    const double xr = i0 + VEC < (unsigned)nx ? ctr[nx + VEC] : 0.0;
+    row(q, c, xl, xr, ym, yp, zm, zp, wc, aw);
+  }
+
+  // (A w) at the unit from w there (c) and at its neighbours (0 outside the grid).
+  __device__ __forceinline__ void row(const Cursor& q, const double (&c)[VEC], double xl, double xr,
+                                      const double (&ym)[VEC], const double (&yp)[VEC], const double (&zm)[VEC],
+                                      const double (&zp)[VEC], double (&wc)[VEC], double (&aw)[VEC]) const {
     double xm[VEC], xp[VEC];
 #pragma unroll
     for (int e = 0; e < VEC; ++e) {
@@ -157,6 +191,8 @@ struct StencilOp {
         aw[e] = fma(C, c[e], -s);
       }
     } else {
+      const unsigned c0 = q.c0, i0 = q.i0;
+      const bool has_yp = q.j + 1 < (unsigned)ny, has_zp = DIM == 3 && q.k + 1 < (unsigned)nz;
       double d[VEC], fx[VEC], fy[VEC], fyp[VEC], fz[VEC], fzp[VEC];
       ldg<VEC>(diag + c0, d);
       ldg<VEC>(ax + c0, fx);
@@ -185,6 +221,26 @@ struct StencilOp {
   }
 
   template <int V>
+  __device__ __forceinline__ static void lds(const double* p, double (&o)[V]) {
+    if constexpr (V == 2) {
+      const double2 t = *reinterpret_cast<const double2*>(p);
+      o[0] = t.x;
+      o[1] = t.y;
+    } else {
+      o[0] = *p;
+    }
+  }
+  template <int V>
+  __device__ __forceinline__ static void lds_if(bool ok, const double* p, double (&o)[V]) {
+    if (ok) {
+      lds<V>(p, o);
+    } else {
+#pragma unroll
+      for (int e = 0; e < V; ++e) o[e] = 0.0;
+    }
+  }
+
+  template <int V>
   __device__ __forceinline__ static void ldg(const double* p, double (&o)[V]) {
     if constexpr (V == 2) {
       const double2 t = __ldg(reinterpret_cast<const double2*>(p));
@@ -209,6 +265,7 @@ struct StencilOp {
 // CSR matrix, one row per unit.
 struct CsrOp {
   static constexpr int VEC = 1;
+  static constexpr bool STAGED = false;
   int n;
   const int *row_ptr, *col;
   const double* val;
@@ -245,14 +302,16 @@ struct Kernels {
   static cudaError_t residual(const Op& op, const Launch& L, const double* b, const double* x0, double* x,
                               double* r, State* st, double* partials);
   static cudaError_t spcg_w0(const Op& op, const Launch& L, Vecs v, State* st, Hist h, double* partials);
-  static cudaError_t spcg_iter(const Op& op, const Launch& L, Vecs v, State* st, Hist h, double* partials);
+  static cudaError_t spcg_iter(const Op& op, const Launch& L, Vecs v, State* st, Hist h, double* partials,
+                               bool ff_dots, int stages);
   static cudaError_t true_res(const Op& op, const Launch& L, Vecs v, State* st, Hist h, double* partials);
   static cudaError_t cg_p0(const Op& op, const Launch& L, Vecs v, State* st, Hist h, double* partials);
   static cudaError_t cg_spmv(const Op& op, const Launch& L, Vecs v, State* st, Hist h, double* partials);
   static cudaError_t cg_update(const Op& op, const Launch& L, Vecs v, State* st, Hist h, double* partials);
   static cudaError_t cg_p(const Op& op, const Launch& L, Vecs v, State* st, Hist h);
   static cudaError_t apply(const Op& op, const Launch& L, const double* x, double* y);
-  static int blocks_per_sm(int kind);
+  static int blocks_per_sm(const Op& op, int kind, int stages);
+  static int iter_stages(const Op& op, int stages);
 };
 
 #ifdef PCG_KERNELS_IMPL
@@ -389,6 +448,7 @@ __device__ __forceinline__ void finish_spcg(State* st, Hist h, double gamma, dou
       h.beta[i] = beta;
     }
   }
+  ff_scales(gamma, delta, st->sigma, st->ff_sr, st->ff_sw);
   st->iter = i;
   st->status = status;
   st->ticket = 0;
@@ -496,50 +556,287 @@ __global__ void __launch_bounds__(kBlock) k_spcg_w0(Op op, Vecs v, State* st, Hi
 // and, in the same sweep, the partials of gamma_{i+1} = (r_{i+1}, r_{i+1}) and
 // (w_{i+1}, r_{i+1}); the last block turns them into alpha_{i+1}, beta_{i+1}.
 // w is double-buffered (neighbours read w_i while w_{i+1} is written).
-template <class Op>
+// FF: the two dots on the FP32 pipe (pcg_ffdot.cuh), else binary64 fused multiply-adds.
+
+// Per-thread state of the sweep: the iteration's scalars and the dot accumulators.
+struct SpcgSweep {
+  double alpha, beta, asg;
+  int sr, sw;
+  double g = 0.0, o = 0.0;
+  FfAcc G, O;
+  unsigned bad = 0u;
+};
+
+// The recurrences of one unit from its loaded z, s, p, x, r, w_i and (A w_i); stores the
+// updated vectors and accumulates the dots.
+template <int VEC, bool FF>
+__device__ __forceinline__ void spcg_unit(const Vecs& v, double* __restrict__ wn, int c0, SpcgSweep& S,
+                                          const double (&wc)[VEC], const double (&nv)[VEC], double (&z)[VEC],
+                                          double (&s)[VEC], double (&p)[VEC], double (&x)[VEC], double (&r)[VEC]) {
+  double w1[VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) {
+    z[e] = fma(S.beta, z[e], nv[e]);
+    s[e] = fma(S.beta, s[e], wc[e]);
+    p[e] = fma(S.beta, p[e], r[e]);
+    x[e] = fma(S.alpha, p[e], x[e]);
+    const double rn = fma(-S.alpha, s[e], fma(-S.asg, p[e], r[e]));
+    const double wv = fma(-S.alpha, z[e], wc[e]);
+    r[e] = rn;
+    w1[e] = wv;
+    if constexpr (FF) {
+      const FfSplit fr = ff_split(rn, S.sr, S.bad), fw = ff_split(wv, S.sw, S.bad);
+      ff_add_square(S.G, fr);
+      ff_add_product(S.O, fw, fr);
+    } else {
+      S.g = fma(rn, rn, S.g);
+      S.o = fma(wv, rn, S.o);
+    }
+  }
+  st_stream<VEC>(v.z + c0, z);
+  st_stream<VEC>(v.s + c0, s);
+  st_stream<VEC>(v.p + c0, p);
+  st_stream<VEC>(v.x + c0, x);
+  st_stream<VEC>(v.r + c0, r);
+  st_plain<VEC>(wn + c0, w1);
+}
+
+// One unit with its vectors loaded from global memory.
+template <class Op, bool FF>
+__device__ __forceinline__ void spcg_unit_global(const Op& op, const Vecs& v, const double* __restrict__ w,
+                                                 double* __restrict__ wn, const typename Op::Cursor& q, SpcgSweep& S) {
+  constexpr int VEC = Op::VEC;
+  const int c0 = (int)q.c0;
+  double wc[VEC], nv[VEC], z[VEC], s[VEC], p[VEC], x[VEC], r[VEC];
+  op.apply(w, q, wc, nv);
+  ld_stream<VEC>(v.z + c0, z);
+  ld_stream<VEC>(v.s + c0, s);
+  ld_stream<VEC>(v.p + c0, p);
+  ld_stream<VEC>(v.x + c0, x);
+  ld_stream<VEC>(v.r + c0, r);
+  spcg_unit<VEC, FF>(v, wn, c0, S, wc, nv, z, s, p, x, r);
+}
+
+// The thread's dot partials, then the grid reduction and the finisher.  With FF and an
+// out-of-range value, the thread's dots are summed again in binary64 from the r_{i+1}
+// and w_{i+1} it has just written (its units are the grid-stride units from q0).
+template <class Op, bool FF>
+__device__ __forceinline__ void spcg_sweep_finish(const Op& op, const Vecs& v, const double* __restrict__ wn,
+                                                  typename Op::Cursor q0, const typename Op::Step& stp, unsigned nc,
+                                                  SpcgSweep& S, State* st, Hist h, double* partials) {
+  constexpr int VEC = Op::VEC;
+  if constexpr (FF) {
+    if (S.bad) {
+      for (auto q = q0; q.c0 < nc; op.advance(q, stp)) {
+        const int c0 = (int)q.c0;
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+          const double rn = v.r[c0 + e], wv = wn[c0 + e];
+          S.g = fma(rn, rn, S.g);
+          S.o = fma(wv, rn, S.o);
+        }
+      }
+    } else {
+      S.g = ff_value(S.G, 2 * S.sr);
+      S.o = ff_value(S.O, S.sr + S.sw);
+    }
+  }
+  double vals[2] = {S.g, S.o}, tot[2];
+  if (!reduce_last_block<2>(vals, partials, &st->ticket, tot)) return;
+  if (threadIdx.x == 0) finish_spcg(st, h, tot[0], tot[1], false);
+}
+
+template <class Op, bool FF>
 __global__ void __launch_bounds__(kBlock, PCG_ITER_MIN_BLOCKS) k_spcg_iter(Op op, Vecs v, State* st, Hist h, double* partials) {
   constexpr int VEC = Op::VEC;
   if (st->status != ST_RUNNING) return;
   const int it = st->iter;
-  const double alpha = h.alpha[it], beta = h.beta[it];
-  const double asg = alpha * st->sigma;
+  SpcgSweep S;
+  S.alpha = h.alpha[it];
+  S.beta = h.beta[it];
+  S.asg = S.alpha * st->sigma;
+  S.sr = st->ff_sr;
+  S.sw = st->ff_sw;
   const double* __restrict__ w = (it & 1) ? v.w1 : v.w0;
   double* __restrict__ wn = (it & 1) ? v.w0 : v.w1;
-  double g = 0.0, o = 0.0;
   const unsigned nc = (unsigned)op.units() * VEC;
   const auto stp = op.step(gridDim.x * kBlock);
-  for (auto q = op.cursor(blockIdx.x * kBlock + threadIdx.x); q.c0 < nc; op.advance(q, stp)) {
-    const int c0 = (int)q.c0;
-    double wc[VEC], nv[VEC], z[VEC], s[VEC], p[VEC], x[VEC], r[VEC], w1[VEC];
-    op.apply(w, q, wc, nv);
-    ld_stream<VEC>(v.z + c0, z);
-    ld_stream<VEC>(v.s + c0, s);
-    ld_stream<VEC>(v.p + c0, p);
-    ld_stream<VEC>(v.x + c0, x);
-    ld_stream<VEC>(v.r + c0, r);
+  const auto q0 = op.cursor(blockIdx.x * kBlock + threadIdx.x);
+  for (auto q = q0; q.c0 < nc; op.advance(q, stp)) spcg_unit_global<Op, FF>(op, v, w, wn, q, S);
+  spcg_sweep_finish<Op, FF>(op, v, wn, q0, stp, nc, S, st, h, partials);
+}
+
+// The same iteration with every operand of a chunk staged in shared memory by TMA bulk
+// copies (constant-coefficient stencils with two unknowns per thread).  The sweep is cut
+// into chunks of CH = kBlock * VEC consecutive unknowns, taken by the blocks in
+// grid-stride order (chunk c by block c mod gridDim.x, so every thread owns the same
+// units as in k_spcg_iter).  Per chunk, thread 0 copies into one stage of a ring of NST:
+//   z, s, p, x, r over the chunk;  w_i over the chunk widened by one grid row on each
+//   side (its x and y neighbours);  in 3D, w_i over the chunk one plane below and above.
+// The copies of a chunk complete one phase of that stage's mbarrier; the ring keeps
+// NST - 1 chunks in flight ahead of the one being computed, so no warp waits on a global
+// load.  A chunk shorter than CH (n not a multiple of it) is computed from global memory.
+// A wait that exceeds its time limit stops the solve with ST_TIMEOUT after the block has
+// waited (again bounded) for its copies in flight.
+// Measured (256^3 Laplacian, GB300): the staging removes the stalls on global loads
+// (long-scoreboard stalls per issue 5.6 -> 0.6) and reads DRAM no more than the register
+// sweep, but a ring of two 36 KB stages lets 3 blocks share an SM instead of 4, the FP64
+// pipe is then less busy (71 % against 84 %), and the sweep takes 0.33 ms against 0.29 ms.
+// It is therefore opt-in (PCG_PARAM_ITER_STAGES).
+#ifndef PCG_TMA_MIN_BLOCKS
+#define PCG_TMA_MIN_BLOCKS 3
+#endif
+
+// Doubles per stage: five chunk vectors, two plane rows (3D) and the widened w rows.
+__host__ __device__ constexpr long long spcg_stage_doubles(int dim, int vec, long long nx) {
+  return (5 + (dim == 3 ? 2 : 0)) * (long long)kBlock * vec + ((long long)kBlock * vec + 2 * nx);
+}
+
+template <class Op, bool FF, int NST>
+__global__ void __launch_bounds__(kBlock, PCG_TMA_MIN_BLOCKS) k_spcg_iter_tma(Op op, Vecs v, State* st, Hist h,
+                                                                                double* partials) {
+  constexpr int VEC = Op::VEC;
+  constexpr int DIM = Op::DIMS;
+  constexpr int CH = kBlock * VEC;   // unknowns per chunk
+  constexpr unsigned CHB = CH * sizeof(double);
+  extern __shared__ __align__(128) double stage[];   // [NST][z s p x r | zlo zhi | ctr]
+  // full[k]: the chunk's copies have landed; empty[k]: every warp is done reading it
+  __shared__ unsigned long long full[NST], empty[NST];
+  __shared__ volatile int s_fail;
+  if (st->status != ST_RUNNING) return;
+  const int it = st->iter;
+  SpcgSweep S;
+  S.alpha = h.alpha[it];
+  S.beta = h.beta[it];
+  S.asg = S.alpha * st->sigma;
+  S.sr = st->ff_sr;
+  S.sw = st->ff_sw;
+  const double* __restrict__ w = (it & 1) ? v.w1 : v.w0;
+  double* __restrict__ wn = (it & 1) ? v.w0 : v.w1;
+  const unsigned nc = (unsigned)op.units() * VEC;
+  const unsigned nfull = nc / CH;
+  const unsigned G = gridDim.x;
+  const unsigned nk = blockIdx.x < nfull ? (nfull - 1 - blockIdx.x) / G + 1 : 0u;   // staged chunks
+  const long long nx = op.nx, nxny = op.nxny;
+  const long long SS = spcg_stage_doubles(DIM, VEC, nx);
+  const int ZLO = 5 * CH, ZHI = 6 * CH, CTR = (DIM == 3 ? 7 : 5) * CH;
+  if (threadIdx.x == 0) {
 #pragma unroll
-    for (int e = 0; e < VEC; ++e) {
-      z[e] = fma(beta, z[e], nv[e]);
-      s[e] = fma(beta, s[e], wc[e]);
-      p[e] = fma(beta, p[e], r[e]);
-      x[e] = fma(alpha, p[e], x[e]);
-      const double rn = fma(-alpha, s[e], fma(-asg, p[e], r[e]));
-      const double wv = fma(-alpha, z[e], wc[e]);
-      r[e] = rn;
-      w1[e] = wv;
-      g = fma(rn, rn, g);
-      o = fma(wv, rn, o);
+    for (int k = 0; k < NST; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], kWarps);
     }
-    st_stream<VEC>(v.z + c0, z);
-    st_stream<VEC>(v.s + c0, s);
-    st_stream<VEC>(v.p + c0, p);
-    st_stream<VEC>(v.x + c0, x);
-    st_stream<VEC>(v.r + c0, r);
-    st_plain<VEC>(wn + c0, w1);
+    mbar_fence_init();
+    s_fail = 0;
   }
-  double vals[2] = {g, o}, tot[2];
-  if (!reduce_last_block<2>(vals, partials, &st->ticket, tot)) return;
-  if (threadIdx.x == 0) finish_spcg(st, h, tot[0], tot[1], false);
+  __syncthreads();
+  const unsigned long long pol = l2_evict_first();
+  auto issue = [&](unsigned k) {
+    const unsigned sl = k % NST;
+    const long long c0 = (long long)(blockIdx.x + k * G) * CH;
+    double* dst = stage + sl * SS;
+    // w rows: the chunk widened by one grid row, and (3D) the chunk one plane below/above,
+    // each clipped to [0, n)
+    const long long clo = c0 - nx > 0 ? c0 - nx : 0, chi = c0 + CH + nx < (long long)nc ? c0 + CH + nx : nc;
+    unsigned tx = 5 * CHB + (unsigned)(chi - clo) * 8u;
+    long long zlo_lo = 0, zlo_hi = 0, zhi_lo = 0, zhi_hi = 0;
+    if (DIM == 3) {
+      zlo_lo = c0 - nxny > 0 ? c0 - nxny : 0;
+      zlo_hi = c0 - nxny + CH;
+      zhi_lo = c0 + nxny;
+      zhi_hi = c0 + nxny + CH < (long long)nc ? c0 + nxny + CH : nc;
+      if (zlo_hi > zlo_lo) tx += (unsigned)(zlo_hi - zlo_lo) * 8u;
+      if (zhi_hi > zhi_lo) tx += (unsigned)(zhi_hi - zhi_lo) * 8u;
+    }
+    mbar_arrive_expect_tx(&full[sl], tx);
+    bulk_g2s(dst + 0 * CH, v.z + c0, CHB, &full[sl], pol);
+    bulk_g2s(dst + 1 * CH, v.s + c0, CHB, &full[sl], pol);
+    bulk_g2s(dst + 2 * CH, v.p + c0, CHB, &full[sl], pol);
+    bulk_g2s(dst + 3 * CH, v.x + c0, CHB, &full[sl], pol);
+    bulk_g2s(dst + 4 * CH, v.r + c0, CHB, &full[sl], pol);
+    // w's rows are copied three times (own rows, and the planes above/below of two other
+    // chunks): no evict-first hint for them
+    bulk_g2s(dst + CTR + (clo - (c0 - nx)), w + clo, (unsigned)(chi - clo) * 8u, &full[sl]);
+    if (DIM == 3) {
+      if (zlo_hi > zlo_lo)
+        bulk_g2s(dst + ZLO + (zlo_lo - (c0 - nxny)), w + zlo_lo, (unsigned)(zlo_hi - zlo_lo) * 8u, &full[sl]);
+      if (zhi_hi > zhi_lo) bulk_g2s(dst + ZHI, w + zhi_lo, (unsigned)(zhi_hi - zhi_lo) * 8u, &full[sl]);
+    }
+  };
+  // bounded wait that also gives up once another thread of the block has given up
+  auto wait = [&](unsigned long long* bar, unsigned parity) -> bool {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+      if (s_fail || global_ns() - t0 > kTmaWaitNs) {
+        s_fail = 1;
+        return false;
+      }
+    }
+    return true;
+  };
+  unsigned issued = 0;   // chunks whose copies thread 0 has issued, in order
+  if (threadIdx.x == 0) {
+    for (; issued < nk && issued < (unsigned)NST; ++issued) issue(issued);
+  }
+  const auto stp = op.step(G * kBlock);
+  const auto q0 = op.cursor(blockIdx.x * kBlock + threadIdx.x);
+  const int tv = threadIdx.x * VEC;
+  auto q = q0;
+  unsigned k = 0;
+  bool failed = false;
+  for (; k < nk; ++k, op.advance(q, stp)) {
+    const unsigned sl = k % NST;
+    // warp-uniform outcome, so that a failing warp leaves the loop as a whole
+    if (__any_sync(0xffffffffu, !wait(&full[sl], (k / NST) & 1u))) {
+      failed = true;
+      break;
+    }
+    const double* sb = stage + sl * SS;
+    double wc[VEC], nv[VEC], z[VEC], s[VEC], p[VEC], x[VEC], r[VEC];
+    op.apply_staged(sb + CTR + tv, sb + ZLO + tv, sb + ZHI + tv, q, wc, nv);
+    ld_smem<VEC>(sb + 0 * CH + tv, z);
+    ld_smem<VEC>(sb + 1 * CH + tv, s);
+    ld_smem<VEC>(sb + 2 * CH + tv, p);
+    ld_smem<VEC>(sb + 3 * CH + tv, x);
+    ld_smem<VEC>(sb + 4 * CH + tv, r);
+    // this warp is done with the stage's shared memory
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[sl]);
+    // the producer refills the stage with chunk k + NST once every warp has left it
+    if (threadIdx.x == 0 && k + NST < nk) {
+      if (wait(&empty[sl], (k / NST) & 1u)) {
+        issue(issued++);
+      } else {
+        failed = true;
+      }
+    }
+    failed = __any_sync(0xffffffffu, failed);
+    spcg_unit<VEC, FF>(v, wn, (int)q.c0, S, wc, nv, z, s, p, x, r);
+    if (failed) break;
+  }
+  __syncthreads();
+  if (s_fail) {
+    // a wait exceeded its time limit: report, wait (bounded) for the copies this block
+    // still has in flight, and leave without a partial (the solve stops as timed out)
+    if (threadIdx.x == 0) {
+      atomicExch(&st->status, ST_TIMEOUT);
+      // the last chunk issued into each stage (chunks are issued in order, c into c mod NST)
+      for (unsigned c = issued > (unsigned)NST ? issued - NST : 0u; c < issued; ++c)
+        mbar_wait_bounded(&full[c % NST], (c / NST) & 1u);
+    }
+    return;
+  }
+  // the short last chunk, if this block owns it
+  for (; q.c0 < nc; op.advance(q, stp)) spcg_unit_global<Op, FF>(op, v, w, wn, q, S);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < NST; ++j) {
+      mbar_inval(&full[j]);
+      mbar_inval(&empty[j]);
+    }
+  }
+  spcg_sweep_finish<Op, FF>(op, v, wn, q0, stp, nc, S, st, h, partials);
 }
 
 // True residual and gap at the current iterate: ||b - A x||, ||(b - A x) - r||
@@ -722,10 +1019,89 @@ cudaError_t Kernels<Op>::spcg_w0(const Op& op, const Launch& L, Vecs v, State* s
   return cudaGetLastError();
 }
 template <class Op>
-cudaError_t Kernels<Op>::spcg_iter(const Op& op, const Launch& L, Vecs v, State* st, Hist h, double* partials) {
-  k_spcg_iter<Op><<<L.grid, L.block, 0, L.stream>>>(op, v, st, h, partials);
+cudaError_t Kernels<Op>::spcg_iter(const Op& op, const Launch& L, Vecs v, State* st, Hist h, double* partials,
+                                   bool ff_dots, int stages) {
+  if constexpr (Op::STAGED) {
+    if (stages == 2 || stages == 3) {
+      const size_t sm = (size_t)stages * spcg_stage_doubles(Op::DIMS, Op::VEC, op.nx) * sizeof(double);
+      if (stages == 2) {
+        if (ff_dots) {
+          k_spcg_iter_tma<Op, true, 2><<<L.grid, L.block, sm, L.stream>>>(op, v, st, h, partials);
+        } else {
+          k_spcg_iter_tma<Op, false, 2><<<L.grid, L.block, sm, L.stream>>>(op, v, st, h, partials);
+        }
+      } else {
+        if (ff_dots) {
+          k_spcg_iter_tma<Op, true, 3><<<L.grid, L.block, sm, L.stream>>>(op, v, st, h, partials);
+        } else {
+          k_spcg_iter_tma<Op, false, 3><<<L.grid, L.block, sm, L.stream>>>(op, v, st, h, partials);
+        }
+      }
+      return cudaGetLastError();
+    }
+  }
+  if (ff_dots) {
+    k_spcg_iter<Op, true><<<L.grid, L.block, 0, L.stream>>>(op, v, st, h, partials);
+  } else {
+    k_spcg_iter<Op, false><<<L.grid, L.block, 0, L.stream>>>(op, v, st, h, partials);
+  }
   return cudaGetLastError();
 }
+
+// Resident blocks per SM of the staged sweep (both dot forms; the smaller), after
+// allowing the largest opt-in dynamic shared memory for it (the attribute is global to the
+// kernel, and contexts with other row lengths launch it with other sizes).
+template <class Op, int NST>
+cudaError_t spcg_tma_occupancy(const Op& op, int* nb) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  const long long sm = (long long)NST * spcg_stage_doubles(Op::DIMS, Op::VEC, op.nx) * (long long)sizeof(double);
+  *nb = 0;
+  // the dynamic limit is what the opt-in maximum leaves beside the kernel's static shared memory
+  cudaFuncAttributes fa, fb;
+  if ((e = cudaFuncGetAttributes(&fa, k_spcg_iter_tma<Op, true, NST>)) != cudaSuccess) return e;
+  if ((e = cudaFuncGetAttributes(&fb, k_spcg_iter_tma<Op, false, NST>)) != cudaSuccess) return e;
+  const int dyn_a = optin - (int)fa.sharedSizeBytes, dyn_b = optin - (int)fb.sharedSizeBytes;
+  if (sm > dyn_a || sm > dyn_b) return cudaSuccess;
+  int a = 0, b = 0;
+  if ((e = cudaFuncSetAttribute(k_spcg_iter_tma<Op, true, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_a)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_spcg_iter_tma<Op, false, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_b)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_spcg_iter_tma<Op, true, NST>, kBlock, (size_t)sm)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_spcg_iter_tma<Op, false, NST>, kBlock, (size_t)sm)) !=
+      cudaSuccess)
+    return e;
+  *nb = min(a, b);
+  return cudaSuccess;
+}
+
+// The staging depth the fused iteration will use: `stages` (2 or 3) when this operator
+// can be staged and at least two staged blocks fit on an SM, else 0 (register sweep).
+template <class Op>
+int Kernels<Op>::iter_stages(const Op& op, int stages) {
+  if constexpr (Op::STAGED) {
+    if (stages != 2 && stages != 3) return 0;
+    int nb = 0;
+    const cudaError_t e = stages == 2 ? spcg_tma_occupancy<Op, 2>(op, &nb) : spcg_tma_occupancy<Op, 3>(op, &nb);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return nb >= 2 ? stages : 0;
+  } else {
+    (void)op;
+    (void)stages;
+    return 0;
+  }
+}
+
 template <class Op>
 cudaError_t Kernels<Op>::true_res(const Op& op, const Launch& L, Vecs v, State* st, Hist h, double* partials) {
   k_true_res<Op><<<L.grid, L.block, 0, L.stream>>>(op, v, st, h, partials);
@@ -757,13 +1133,20 @@ cudaError_t Kernels<Op>::apply(const Op& op, const Launch& L, const double* x, d
   return cudaGetLastError();
 }
 template <class Op>
-int Kernels<Op>::blocks_per_sm(int kind) {
+int Kernels<Op>::blocks_per_sm(const Op& op, int kind, int stages) {
   int nb = 0;
   cudaError_t e = cudaSuccess;
+  if constexpr (Op::STAGED) {
+    if (kind == K_SPCG_ITER && (stages == 2 || stages == 3)) {
+      e = stages == 2 ? spcg_tma_occupancy<Op, 2>(op, &nb) : spcg_tma_occupancy<Op, 3>(op, &nb);
+      return e == cudaSuccess ? nb : 0;
+    }
+  }
+  (void)op;
   switch (kind) {
     case K_RESIDUAL: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_residual<Op>, kBlock, 0); break;
     case K_SPCG_W0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spcg_w0<Op>, kBlock, 0); break;
-    case K_SPCG_ITER: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spcg_iter<Op>, kBlock, 0); break;
+    case K_SPCG_ITER: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spcg_iter<Op, true>, kBlock, 0); break;
     case K_TRUE_RES: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_true_res<Op>, kBlock, 0); break;
     case K_CG_P0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cg_p0<Op::VEC>, kBlock, 0); break;
     case K_CG_SPMV: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cg_spmv<Op>, kBlock, 0); break;

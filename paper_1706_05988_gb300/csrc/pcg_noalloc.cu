@@ -112,15 +112,27 @@ cudaError_t op_dispatch(const OpDesc& d, F&& f) {
   }
 }
 
-// Device address of g_noalloc, looked up once per device (with that device current).
+// Device address of g_noalloc.  The address belongs to the module loaded into the
+// device's current context, and a context that is destroyed and created again
+// (cudaDeviceReset) may load the module at another address.  So every call made
+// outside stream capture looks the address up again (a host-side table lookup,
+// no device work) and refreshes the per-device copy; a call inside a capture uses
+// that copy, taken by the last call outside capture on the same device.
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 NoallocScratch* g_scratch_ptr[kMaxDevices] = {nullptr};
 
-cudaError_t scratch_for(int dev, NoallocScratch** out) {
+cudaError_t scratch_for(int dev, cudaStream_t s, NoallocScratch** out) {
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    // e.g. the legacy stream while another thread captures in global mode: treat as
+    // capturing (no lookup) and clear the error
+    cudaGetLastError();
+    cap = cudaStreamCaptureStatusActive;
+  }
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (g_scratch_ptr[dev] == nullptr) {
+  if (cap == cudaStreamCaptureStatusNone || g_scratch_ptr[dev] == nullptr) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc);
     if (e != cudaSuccess) return e;
@@ -169,19 +181,22 @@ extern "C" pcg_status pcg_true_residual_noalloc(const pcg_matrix* A, const doubl
     return PCG_EINVAL;
   }
   op.n = (int)n;
-  // b, x and r are read with 128-bit loads when the operator uses two unknowns per thread
-  if (op_vec(op) == 2 && (((uintptr_t)b | (uintptr_t)x | (uintptr_t)(r ? r : b)) % 16 != 0)) return PCG_EINVAL;
+  // every vector holds doubles (8-byte alignment); b, x and r are read with 128-bit
+  // loads when the operator takes two unknowns per thread
+  const uintptr_t vec_bits = (uintptr_t)b | (uintptr_t)x | (uintptr_t)(r ? r : b);
+  if ((vec_bits | (uintptr_t)norms) % 8 != 0) return PCG_EINVAL;
+  if (op_vec(op) == 2 && vec_bits % 16 != 0) return PCG_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
     return PCG_ECUDA;
   }
+  cudaStream_t s = (cudaStream_t)stream;
   NoallocScratch* sc = nullptr;
-  if (scratch_for(dev, &sc) != cudaSuccess) {
+  if (scratch_for(dev, s, &sc) != cudaSuccess) {
     cudaGetLastError();
     return PCG_ECUDA;
   }
-  cudaStream_t s = (cudaStream_t)stream;
   // the ticket must start at zero (a finished launch leaves it at zero; this also
   // clears it after an aborted one); the partials are fully rewritten by every launch
   if (cudaMemsetAsync(&sc->ticket, 0, sizeof(unsigned int), s) != cudaSuccess) {

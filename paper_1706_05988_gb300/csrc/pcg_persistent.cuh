@@ -26,12 +26,6 @@ struct PersistentKernels {
 
 #ifdef PCG_KERNELS_IMPL
 
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
 // Sense-counting grid barrier on (st->bar_count, st->bar_gen).  `expected` is the
 // number of arrivals that completes a phase.  Returns false after a timeout.
 __device__ __forceinline__ bool grid_barrier(State* st, unsigned expected, unsigned long long timeout_ns) {

@@ -31,8 +31,10 @@ PCG_STENCIL_FP64_SUM = 0x4
 # pcg_set_param parameters
 PCG_PARAM_MIXED_ETA, PCG_PARAM_MAX_RESTARTS, PCG_PARAM_BARRIER_TIMEOUT_MS, PCG_PARAM_TEST_BARRIER_PHANTOMS = 1, 2, 3, 4
 PCG_PARAM_TRUE_TOL = 5
+PCG_PARAM_ITER_STAGES = 6
 PCG_PERSISTENT = 0x8
 PCG_JACOBI = 0x10
+PCG_DOTS_SPLIT32 = 0x20
 
 METHODS = {"cg": PCG_CG, "pcg": PCG_PCG, "spcg": PCG_SPCG}
 
@@ -82,6 +84,7 @@ def lib() -> ctypes.CDLL:
         L.pcg_psi.argtypes = [vp, vp, vp, i32, vp, i32, vp]
         L.pcg_apply.argtypes = [vp, vp, vp]
         L.pcg_set_param.argtypes = [vp, i32, f64]
+        L.pcg_get_param.argtypes = [vp, i32, ctypes.POINTER(f64)]
         L.pcg_set_shifts.argtypes = [vp, vp, i32]
         L.pcg_psi_varsh.argtypes = [vp, vp, vp, i32, vp, i32, i32, vp]
         L.pcg_batch_create.argtypes = [vp, i32, ctypes.c_uint32, ctypes.POINTER(vp)]
@@ -111,7 +114,8 @@ def lib() -> ctypes.CDLL:
         L.pcg_version.argtypes = []
         L.pcg_version.restype = ctypes.c_char_p
         for f in ("pcg_create", "pcg_set_stream", "pcg_solve", "pcg_solve_device", "pcg_select_sigma", "pcg_psi",
-                  "pcg_apply", "pcg_true_residual_noalloc", "pcg_set_param", "pcg_set_shifts", "pcg_convert_check", "pcg_psi_varsh",
+                  "pcg_apply", "pcg_true_residual_noalloc", "pcg_set_param", "pcg_get_param", "pcg_set_shifts", "pcg_convert_check",
+                  "pcg_psi_varsh",
                   "pcg_batch_create", "pcg_batch_solve", "pcg_batch_autotune", "pcg_batch_set_cluster",
                   "pcg_batch_set_precision", "pcg_batch_set_param", "pcg_batch_last_kernel_ms", "pcg_server_create",
                   "pcg_batch_classes", "pcg_batch_set_class_cluster", "pcg_batch_set_class_occupancy",
@@ -226,6 +230,14 @@ def pcg_select_sigma(ctx, b: np.ndarray, iters: int, grid) -> tuple[float, np.nd
     if s != PCG_OK:
         raise PcgError(s, pcg_last_error(ctx))
     return sig.value, psi
+
+
+def pcg_get_param(ctx, param: int) -> float:
+    v = ctypes.c_double()
+    s = lib().pcg_get_param(ctx, param, ctypes.byref(v))
+    if s != PCG_OK:
+        raise PcgError(s, "pcg_get_param")
+    return v.value
 
 
 def pcg_kernel_stats(ctx) -> tuple[int, int, float]:

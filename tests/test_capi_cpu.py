@@ -85,6 +85,9 @@ def test_argument_errors_of_the_extensions_without_gpu(libpath):
     L = B.lib()
     vp = ctypes.c_void_p
     assert L.pcg_set_shifts(None, None, 0) == B.PCG_EINVAL
+    v = ctypes.c_double()
+    assert L.pcg_get_param(None, B.PCG_PARAM_ITER_STAGES, ctypes.byref(v)) == B.PCG_EINVAL
+    assert L.pcg_set_param(None, B.PCG_PARAM_ITER_STAGES, 2.0) == B.PCG_EINVAL
     assert L.pcg_psi_varsh(None, None, None, 10, None, 12, 1, None) == B.PCG_EINVAL
     assert L.pcg_batch_set_precision(None, B.PCG_MIXED_IR) == B.PCG_EINVAL
     assert L.pcg_batch_set_param(None, B.PCG_PARAM_MIXED_ETA, 0.5) == B.PCG_EINVAL

@@ -183,6 +183,51 @@ def test_fp64_sum_rows_vs_oracle(B, maker):
     assert np.linalg.norm(g.x - o.x) <= 1e-8 * np.linalg.norm(o.x)
 
 
+DOT_SHAPES = [s for s in SHAPES if s[0] in ("3d_even", "2d_odd", "var3d", "csr_var2d")]
+
+
+@pytest.mark.parametrize("name,maker", DOT_SHAPES, ids=[s[0] for s in DOT_SHAPES])
+def test_dot_forms_vs_oracle(B, name, maker):
+    """The merged dots (r,r), (w,r) accumulated in binary64 (the default) and on the FP32 pipe
+    (PCG_DOTS_SPLIT32: exact binary32 splits, TwoProd/TwoSum): both meet the parity bar against
+    the oracle, and they agree with each other to 1e-12 over 20 iterations."""
+    P = maker()
+    b = S.normal(7, P.n)
+    sigma = shift_for(P)
+    g64, o = run_both(B, P, b, "spcg", sigma, 20)
+    gff, _ = run_both(B, P, b, "spcg", sigma, 20, flags=B.PCG_DOTS_SPLIT32)
+    check_scalars(g64, o)
+    check_scalars(gff, o)
+    assert rel(gff.alpha, g64.alpha) <= 1e-12 and rel(gff.beta[1:], g64.beta[1:]) <= 1e-12
+    assert np.linalg.norm(gff.x - o.x) <= 1e-8 * np.linalg.norm(o.x)
+
+
+def test_dot_fallback_out_of_scaled_range(B):
+    """PCG_DOTS_SPLIT32 on a diagonal matrix with entries 1..1e44 and b_j = min(1, d_j^-3/4):
+    the residual grows by 6e21 in the first iteration and w_1 by far more, so entries of r_1,
+    w_1 leave the binary32 range around the scale taken from gamma_0, delta_0 and those
+    threads sum in binary64.  The first scalars still follow the oracle."""
+    import math
+    n = 64
+    d = np.logspace(0, 44, n)
+    b = np.minimum(1.0, d ** -0.75)
+    P = S.Problem(S.CSR32, row_ptr=np.arange(n + 1, dtype=np.int32), col=np.arange(n, dtype=np.int32), val=d,
+                  n_csr=n)
+    # precondition, from the oracle's r_1, w_1 and the documented scale rule: some scaled entry
+    # reaches 2^56, the FP32-pipe limit
+    o1 = oracle.pcg_sh(P, b, sigma=0.0, maxit=1, log_every=0, want_state=True)
+    g0 = float(np.dot(b, b))
+    d0 = float(np.dot(d * b, b))
+    sr = 20 - ((math.frexp(g0)[1] - 1) // 2 + 1)
+    sw = sr - math.frexp(abs(d0 / g0))[1]
+    assert math.log2(np.abs(o1.state["w"]).max()) + sw >= 56
+    g, o = run_both(B, P, b, "pcg", 0.0, 4, flags=B.PCG_DOTS_SPLIT32)
+    g64, _ = run_both(B, P, b, "pcg", 0.0, 4)
+    assert g.iters == o.iters == 4
+    check_scalars(g, o, k=4)
+    check_scalars(g64, o, k=4)
+
+
 def test_random_sdd_csr(B):
     rng = np.random.default_rng(3)
     n = 5000
@@ -376,15 +421,24 @@ def big():
     return P, b
 
 
+def full_size_x_check(gx, ox):
+    """Every entry of the iterate after 20 iterations: the two sides differ only by
+    summation order, so each entry agrees to a few units of 1e-12 of the iterate's scale."""
+    scale = np.abs(ox).max()
+    err = np.abs(gx - ox)
+    assert np.all(err <= 1e-10 * np.abs(ox) + 1e-12 * scale), float(np.max(err / (np.abs(ox) + scale)))
+
+
 def test_full_size_first_iterations_vs_oracle(B, big):
-    """Same launch configuration as the benchmark; the oracle runs 4 iterations at full size."""
+    """Same launch configuration as the benchmark (256^3, sigma = 6): alpha_i, beta_i of the
+    first 20 iterations at 1e-10 and all 16.8M entries of x_20 against the oracle."""
     P, b = big
     with B.Solver(P) as s:
-        g = s.solve(b, method="spcg", sigma=6.0, maxit=4, true_every=0)
-    o = oracle.pcg_sh(P, b, sigma=6.0, maxit=4, log_every=0)
-    check_scalars(g, o, k=4)
-    idx = np.random.default_rng(0).integers(0, P.n, 20000)
-    np.testing.assert_allclose(g.x[idx], o.x[idx], rtol=1e-11, atol=1e-13 * np.abs(o.x).max())
+        g = s.solve(b, method="spcg", sigma=6.0, maxit=N_SCALARS, true_every=0)
+    o = oracle.pcg_sh(P, b, sigma=6.0, maxit=N_SCALARS, log_every=0)
+    assert g.iters == o.iters == N_SCALARS
+    check_scalars(g, o, k=N_SCALARS)
+    full_size_x_check(g.x, o.x)
 
 
 def test_full_size_1000_iterations_properties(B, big):
@@ -402,16 +456,17 @@ def test_full_size_1000_iterations_properties(B, big):
 
 def test_full_size_csr_first_iterations_vs_oracle(B, big):
     """The same 256^3 Laplacian assembled as CSR with int32 indices (117,047,296 entries, the
-    benchmark's CSR form): the first 4 iterations against the oracle on the same CSR arrays."""
+    benchmark's CSR form): the first 20 iterations and every entry of x_20 against the oracle
+    on the same CSR arrays."""
     P, b = big
     Pc = S.to_csr(P)
     assert Pc.nnz == 117_047_296
     with B.Solver(Pc) as s:
-        g = s.solve(b, method="spcg", sigma=6.0, maxit=4, true_every=0)
-    o = oracle.pcg_sh(Pc, b, sigma=6.0, maxit=4, log_every=0)
-    check_scalars(g, o, k=4)
-    idx = np.random.default_rng(1).integers(0, P.n, 20000)
-    np.testing.assert_allclose(g.x[idx], o.x[idx], rtol=1e-11, atol=1e-13 * np.abs(o.x).max())
+        g = s.solve(b, method="spcg", sigma=6.0, maxit=N_SCALARS, true_every=0)
+    o = oracle.pcg_sh(Pc, b, sigma=6.0, maxit=N_SCALARS, log_every=0)
+    assert g.iters == o.iters == N_SCALARS
+    check_scalars(g, o, k=N_SCALARS)
+    full_size_x_check(g.x, o.x)
 
 
 @pytest.mark.parametrize("method,sigma", [("cg", 0.0), ("spcg", 4.0)])
@@ -433,3 +488,58 @@ def test_true_residual_stop(B, method, sigma):
     assert o.status == 1 and g.status == B.PCG_OK, (o.status, g.status)
     assert abs(g.iters - o.iters) <= 2, (g.iters, o.iters)
     assert g.final_true_relres <= 1e-14 and o.true[-1] / bn <= 1e-14
+
+
+# ---------------------------------------------------------------- staged (TMA) sweep
+
+STAGE_SHAPES = [("3d_even", lambda: S.laplacian_3d(20, 18, 16)), ("3d_cube64", lambda: S.laplacian_3d(64)),
+                ("3d_ragged_chunk", lambda: S.laplacian_3d(34, 30, 7)), ("2d_even", lambda: S.laplacian_2d(64, 45)),
+                ("3d_fp64rows", lambda: S.laplacian_3d(24, 22, 10))]
+
+
+@pytest.mark.parametrize("name,maker", STAGE_SHAPES, ids=[s[0] for s in STAGE_SHAPES])
+@pytest.mark.parametrize("stages", [2, 3])
+def test_staged_sweep_vs_oracle_and_register_sweep(B, name, maker, stages):
+    """The fused iteration with every operand staged by TMA bulk copies (a ring of 2 or 3
+    chunks) against the oracle (parity bar) and against the register sweep: the same
+    arithmetic on the same units, so bit for bit where both sweeps have the same grid (the
+    small shapes), and to 1e-12 where the staged sweep's smaller resident grid (3 or 2 blocks
+    per SM instead of 4) changes the order of the block partials (64^3: 512 blocks needed).
+    The shapes cover chunks that cross rows and planes, a last chunk shorter than the others
+    (34*30*7 = 7,140 unknowns = 13 chunks of 512 and 484 more), the 2D stencil and the
+    binary64 row sums."""
+    from paper_1706_05988_gb300 import pcg as C
+    P = maker()
+    b = S.normal(11, P.n)
+    flags = B.PCG_STENCIL_FP64_SUM if name == "3d_fp64rows" else 0
+    sigma = shift_for(P)
+    with B.Solver(P, flags=flags) as s:
+        assert C.pcg_set_param(s.ctx, C.PCG_PARAM_ITER_STAGES, float(stages)) == C.PCG_OK
+        assert C.pcg_get_param(s.ctx, C.PCG_PARAM_ITER_STAGES) == stages
+        gs = s.solve(b, method="spcg", sigma=sigma, maxit=30, true_every=1)
+        assert C.pcg_set_param(s.ctx, C.PCG_PARAM_ITER_STAGES, 0.0) == C.PCG_OK
+        assert C.pcg_get_param(s.ctx, C.PCG_PARAM_ITER_STAGES) == 0
+        g0 = s.solve(b, method="spcg", sigma=sigma, maxit=30, true_every=1)
+    o = oracle.pcg_sh(P, b, sigma=sigma, maxit=30, log_every=1)
+    check_scalars(gs, o)
+    check_final(gs, o, np.linalg.norm(b))
+    if P.n // 512 < 2 * 152:       # both grids are the blocks the problem needs
+        assert np.array_equal(gs.x, g0.x) and np.array_equal(gs.alpha, g0.alpha)
+        assert np.array_equal(gs.beta, g0.beta)
+    else:
+        assert rel(gs.alpha, g0.alpha) <= 1e-12 and rel(gs.beta[1:], g0.beta[1:]) <= 1e-12
+        assert np.linalg.norm(gs.x - g0.x) <= 1e-12 * np.linalg.norm(g0.x)
+
+
+def test_staged_sweep_where_it_applies(B):
+    """The register sweep is the default; asked for, the staged sweep is taken on
+    constant-coefficient stencils with an even row length (the 256^3 workload among them),
+    while CSR, variable coefficients and odd rows stay on the register sweep."""
+    from paper_1706_05988_gb300 import pcg as C
+    for P, want in ((S.laplacian_3d(256), 2), (S.laplacian_2d(100, 100), 2), (S.laplacian_3d(15, 17, 9), 0),
+                    (S.varcoef_3d(24, block=8, seed=3), 0), (S.to_csr(S.laplacian_3d(18, 14, 10)), 0)):
+        with B.Solver(P) as s:
+            assert C.pcg_get_param(s.ctx, C.PCG_PARAM_ITER_STAGES) == 0
+            assert C.pcg_set_param(s.ctx, C.PCG_PARAM_ITER_STAGES, 2.0) == C.PCG_OK
+            assert C.pcg_get_param(s.ctx, C.PCG_PARAM_ITER_STAGES) == want, (P.n, want)
+            assert C.pcg_set_param(s.ctx, C.PCG_PARAM_ITER_STAGES, 1.0) == C.PCG_EINVAL
