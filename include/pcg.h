@@ -278,6 +278,17 @@ pcg_status pcg_batch_set_param(pcg_batch *batch, int32_t param, double value);
 /* CUDA-event time (ms) of the last batch kernel. */
 pcg_status pcg_batch_last_kernel_ms(const pcg_batch *batch, double *ms);
 
+/* alpha_i and beta_i (Algorithm 3, lines of the scalar step) of the first k iterations of
+ * every system in the last pcg_batch_solve: alpha[s * k + i], beta[s * k + i] (host arrays
+ * of nsys * k doubles, either may be NULL), 1 <= k <= PCG_SCALAR_LOG.  Entries past the
+ * iterations a system ran are NaN; beta_0 = 0.  With PCG_MIXED_IR, i counts the inner
+ * iterations across restarts, and a restart starts again from beta = 0.  The per-cluster
+ * solvers record these values as they run (one store per iteration, i < PCG_SCALAR_LOG),
+ * so they can be compared with a reference implementation iteration by iteration.
+ * Waits for the batch's stream.  Errors: PCG_EINVAL, PCG_ECUDA. */
+#define PCG_SCALAR_LOG 32
+pcg_status pcg_batch_scalars(const pcg_batch *batch, int32_t k, double *alpha, double *beta);
+
 void pcg_batch_destroy(pcg_batch *batch);
 
 /* ---- Serving: continuous batching of solve requests ----------------------------
@@ -330,7 +341,10 @@ pcg_status pcg_submit_ex(pcg_server *server, const pcg_matrix *A, const double *
 /* PCG_PENDING until the request is done; then x_out (host, n doubles, may be NULL) and
  * res (iters, status, final_true_relres; may be NULL) are filled, the request's memory
  * is released and its status is returned (PCG_OK, PCG_ENOTCONV, PCG_EBREAKDOWN); the
- * ticket is then no longer valid (PCG_EINVAL). */
+ * ticket is then no longer valid (PCG_EINVAL).  When res->alpha_hist / res->beta_hist
+ * are set, their first min(iters, PCG_SCALAR_LOG) entries receive alpha_i and beta_i of
+ * the request's solve (as pcg_batch_scalars reports them); the other histories are not
+ * kept for served requests. */
 pcg_status pcg_poll(pcg_server *server, uint64_t ticket, double *x_out, pcg_result *res);
 
 /* Requests waiting for admission, requests admitted and not yet polled, free arena bytes. */

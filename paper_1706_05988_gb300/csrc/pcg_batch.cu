@@ -65,6 +65,8 @@ struct GraphKey {
 
 }  // namespace
 
+static_assert(kScalarLog == PCG_SCALAR_LOG, "scalar log length in pcg.h");
+
 struct pcg_batch {
   int device = 0;
   int family = -1;
@@ -80,6 +82,7 @@ struct pcg_batch {
   cudaGraphExec_t graph = nullptr;
   GraphKey graph_key;
   BatchOut* d_out = nullptr;
+  double* d_log = nullptr;        // [nsys][2][kScalarLog]: alpha_i, beta_i of the last solve
   double* d_vec = nullptr;        // b, x, r, w0, w1, z, s, p (+ u, q, t, m0, m1, u64, dinv, dinv32)
   bool jacobi = false;
   int precision = PCG_FP64;
@@ -337,6 +340,11 @@ pcg_status pcg_batch_create(const pcg_matrix* systems, int32_t nsys, uint32_t fl
     B->host_sys[k] = d;
   }
   void* p;
+  if (balloc(B, &p, (size_t)nsys * 2 * kScalarLog * sizeof(double)) != PCG_OK) return bail(PCG_ENOMEM);
+  B->d_log = (double*)p;
+  if (cudaMemset(B->d_log, 0xFF, (size_t)nsys * 2 * kScalarLog * sizeof(double)) != cudaSuccess)   // NaN
+    return bail(PCG_ECUDA);
+  for (int k = 0; k < nsys; ++k) B->host_sys[k].log = B->d_log + (size_t)k * 2 * kScalarLog;
   if (balloc(B, &p, nsys * sizeof(BatchSys)) != PCG_OK) return bail(PCG_ENOMEM);
   B->d_sys = (BatchSys*)p;
   if (balloc(B, &p, nsys * sizeof(BatchOut)) != PCG_OK) return bail(PCG_ENOMEM);
@@ -604,6 +612,25 @@ pcg_status pcg_batch_set_cluster(pcg_batch* B, int32_t cluster_size) {
 pcg_status pcg_batch_last_kernel_ms(const pcg_batch* B, double* ms) {
   if (!B || !ms) return PCG_EINVAL;
   *ms = B->last_kernel_ms;
+  return PCG_OK;
+}
+
+pcg_status pcg_batch_scalars(const pcg_batch* B, int32_t k, double* alpha, double* beta) {
+  if (!B || k < 1 || k > PCG_SCALAR_LOG || (!alpha && !beta)) return PCG_EINVAL;
+  if (cudaSetDevice(B->device) != cudaSuccess) return PCG_ECUDA;
+  std::vector<double> h((size_t)B->nsys * 2 * kScalarLog);
+  if (cudaStreamSynchronize(B->stream) != cudaSuccess ||
+      cudaMemcpy(h.data(), B->d_log, h.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return PCG_ECUDA;
+  }
+  for (int s = 0; s < B->nsys; ++s) {
+    const double* l = h.data() + (size_t)s * 2 * kScalarLog;
+    for (int i = 0; i < k; ++i) {
+      if (alpha) alpha[(size_t)s * k + i] = l[i];
+      if (beta) beta[(size_t)s * k + i] = l[kScalarLog + i];
+    }
+  }
   return PCG_OK;
 }
 

@@ -90,6 +90,7 @@ __device__ __forceinline__ void cluster_solve_jac(cg::cluster_group& cl, double 
   const auto stp = op.step(C * kBlock);
   const int first = (int)(rank * kBlock + threadIdx.x);
 
+  scalar_log_clear(d, rank);
   // r_0 = b (x_0 = 0), u_0 = D^{-1} r_0, ||b||
   double bb = 0.0;
   for (unsigned i = first; i < nc; i += C * kBlock) {
@@ -141,6 +142,7 @@ __device__ __forceinline__ void cluster_solve_jac(cg::cluster_group& cl, double 
     status = ST_BREAKDOWN;
   } else {
     alpha = gamma / delta;
+    scalar_log(d, rank, 0, alpha, 0.0);
   }
   while (status == ST_RUNNING) {
     const double asg = alpha * sigma;
@@ -206,6 +208,7 @@ __device__ __forceinline__ void cluster_solve_jac(cg::cluster_group& cl, double 
       } else {
         alpha = 1.0 / den;
         beta = bt;
+        scalar_log(d, rank, it, alpha, beta);
       }
     }
     gamma = gn;
@@ -248,6 +251,7 @@ __device__ __forceinline__ void cluster_solve_mx(cg::cluster_group& cl, double (
   const auto stp32 = op32.step(C * kBlock);
   const int first = (int)(rank * kBlock + threadIdx.x);
 
+  scalar_log_clear(d, rank);
   double bb = 0.0;
   double* const x0 = dv(1);
   for (unsigned i = first; i < nc; i += C * kBlock) {
@@ -326,6 +330,7 @@ __device__ __forceinline__ void cluster_solve_mx(cg::cluster_group& cl, double (
       break;
     }
     double alpha = gamma / delta, beta = 0.0;
+    scalar_log(d, rank, it, alpha, beta);
     // inner iterations
     for (;;) {
       const double asg = alpha * sigma;
@@ -423,6 +428,7 @@ __device__ __forceinline__ void cluster_solve_mx(cg::cluster_group& cl, double (
       if (!(den > 0.0) || !isfinite(den)) break;
       alpha = 1.0 / den;
       beta = bt;
+      scalar_log(d, rank, it, alpha, beta);
       gamma = gn;
     }
     if (it >= maxit) {

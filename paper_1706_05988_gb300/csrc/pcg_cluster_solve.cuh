@@ -28,7 +28,26 @@ struct BatchSys {
   const float *diag32, *ax32, *ay32, *az32, *val32;   // binary32 copies (mixed precision)
   long long off;                       // offset of the system's unknowns in every batch vector
   double sigma;
+  double* log;                         // alpha_i, beta_i of iterations i < kScalarLog (nullptr: none)
 };
+
+// alpha_i, beta_i recorded per system and solve: log[i] = alpha_i, log[kScalarLog + i] =
+// beta_i (NaN where the solve did not reach iteration i).  With mixed precision, i counts
+// the inner iterations across restarts (a restart starts again from beta = 0).
+constexpr int kScalarLog = 32;
+
+__device__ __forceinline__ void scalar_log_clear(const BatchSys& d, unsigned rank) {
+  if (d.log != nullptr && rank == 0 && threadIdx.x == 0) {
+    for (int i = 0; i < 2 * kScalarLog; ++i) d.log[i] = __longlong_as_double(0x7FF8000000000000LL);
+  }
+}
+
+__device__ __forceinline__ void scalar_log(const BatchSys& d, unsigned rank, int i, double alpha, double beta) {
+  if (d.log != nullptr && rank == 0 && threadIdx.x == 0 && i >= 0 && i < kScalarLog) {
+    d.log[i] = alpha;
+    d.log[kScalarLog + i] = beta;
+  }
+}
 
 // Per-system results written by the kernel.
 struct BatchOut {
@@ -155,6 +174,7 @@ __device__ __forceinline__ void cluster_solve(cg::cluster_group& cl, double (*pa
   const auto stp = op.step(C * kBlock);
   const int first = (int)(rank * kBlock + threadIdx.x);
 
+  scalar_log_clear(d, rank);
   // r_0 = b (x_0 = 0), ||b||
   double bb = 0.0;
   for (unsigned i = first; i < nc; i += C * kBlock) {
@@ -198,6 +218,7 @@ __device__ __forceinline__ void cluster_solve(cg::cluster_group& cl, double (*pa
     status = ST_BREAKDOWN;
   } else {
     alpha = gamma / delta;
+    scalar_log(d, rank, 0, alpha, 0.0);
   }
   while (status == ST_RUNNING) {
     const double asg = alpha * sigma;
@@ -243,6 +264,7 @@ __device__ __forceinline__ void cluster_solve(cg::cluster_group& cl, double (*pa
       } else {
         alpha = 1.0 / den;
         beta = bt;
+        scalar_log(d, rank, it, alpha, beta);
       }
     }
     gamma = gn;

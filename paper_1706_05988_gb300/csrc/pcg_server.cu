@@ -62,6 +62,7 @@ struct Request {
   // device lane: the whole GPU, the single-system solver, a host worker thread
   bool device = false, device_done = false;
   std::vector<double> x_host;
+  std::vector<double> alpha_log, beta_log;   // device lane: alpha_i, beta_i of the solve
   pcg_result device_res{};
   pcg_status device_status = PCG_OK;
   cudaEvent_t uploaded = nullptr;   // staged admission: the copies' completion
@@ -203,13 +204,16 @@ void arena_free(pcg_server* S, size_t off, size_t bytes) {
 
 size_t pad256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// The request's alpha_i, beta_i log (i < kScalarLog) at the end of its arena block.
+constexpr size_t kLogBytes = (2 * kScalarLog * sizeof(double) + 255) & ~(size_t)255;
+
 size_t request_bytes(const Request& R) {
   const size_t n = (size_t)R.n, npad = (n + 31) & ~(size_t)31;
   const bool jac = R.mode & 1, mixed = R.mode >= 2;
   size_t b = (jac ? 16 : 8) * npad * sizeof(double);   // b, x, r, w0, w1, z, s, p (+ Jacobi vectors)
   if (R.family == 4) b += pad256((n + 1) * 4) + pad256(R.nnz * 4) + pad256(R.nnz * 8) + (mixed ? pad256(R.nnz * 4) : 0);
   if (R.family == 1 || R.family == 3) b += 4 * pad256(n * 8) + (mixed ? 4 * pad256(n * 4) : 0);
-  return b;
+  return b + kLogBytes;
 }
 
 int family_of(const pcg_matrix& A) {
@@ -290,6 +294,7 @@ pcg_status upload(pcg_server* S, Request* R, bool staged) {
   d.layout = R->A.layout;
   d.n = (int)R->n;
   d.off = 0;
+  d.log = (double*)(base + R->bytes - kLogBytes);
   d.sigma = R->method == PCG_SPCG ? R->sigma : 0.0;
   if (R->family == 4) {
     d.row_ptr = (const int*)put(R->row_ptr_src, (n + 1) * 4);
@@ -526,6 +531,11 @@ void device_worker(pcg_server* S) {
     A.ay = R->ay.empty() ? nullptr : R->ay.data();
     A.az = R->az.empty() ? nullptr : R->az.data();
     R->x_host.assign((size_t)R->n, 0.0);
+    R->alpha_log.assign((size_t)R->maxit + 1, NAN);
+    R->beta_log.assign((size_t)R->maxit + 1, NAN);
+    R->device_res = pcg_result{};
+    R->device_res.alpha_hist = R->alpha_log.data();
+    R->device_res.beta_hist = R->beta_log.data();
     pcg_ctx* c = nullptr;
     pcg_status st = pcg_create(&A, R->flags, &c);
     if (st == PCG_OK) {
@@ -797,6 +807,11 @@ pcg_status pcg_poll(pcg_server* S, uint64_t ticket, double* x_out, pcg_result* r
         res->status = st;
         res->final_true_relres = R->device_res.final_true_relres;
         res->final_rec_relres = R->device_res.final_rec_relres;
+        const int m = res->iters < kScalarLog ? res->iters : kScalarLog;
+        for (int i = 0; i < m && i < (int)R->alpha_log.size(); ++i) {
+          if (res->alpha_hist) res->alpha_hist[i] = R->alpha_log[i];
+          if (res->beta_hist) res->beta_hist[i] = R->beta_log[i];
+        }
       }
     }
     S->all.erase(it);
@@ -812,6 +827,10 @@ pcg_status pcg_poll(pcg_server* S, uint64_t ticket, double* x_out, pcg_result* r
   const WorkItem& w = L.items[k];
   if (x_out && cudaMemcpyAsync(x_out, w.vec.x, (size_t)R->n * 8, cudaMemcpyDeviceToHost, S->cstream) != cudaSuccess)
     return PCG_ECUDA;
+  double log[2 * kScalarLog];
+  const bool want_log = res && (res->alpha_hist || res->beta_hist);
+  if (want_log && cudaMemcpyAsync(log, w.sys.log, sizeof log, cudaMemcpyDeviceToHost, S->cstream) != cudaSuccess)
+    return PCG_ECUDA;
   if (cudaStreamSynchronize(S->cstream) != cudaSuccess) return PCG_ECUDA;
   const pcg_status code = o.status == ST_CONVERGED ? PCG_OK : o.status == ST_BREAKDOWN ? PCG_EBREAKDOWN : PCG_ENOTCONV;
   if (res) {
@@ -819,6 +838,13 @@ pcg_status pcg_poll(pcg_server* S, uint64_t ticket, double* x_out, pcg_result* r
     res->status = code;
     res->final_true_relres = o.bnorm > 0 ? o.true_res / o.bnorm : o.true_res;
     res->final_rec_relres = NAN;
+    if (want_log) {
+      const int m = o.iters < kScalarLog ? o.iters : kScalarLog;
+      for (int i = 0; i < m; ++i) {
+        if (res->alpha_hist) res->alpha_hist[i] = log[i];
+        if (res->beta_hist) res->beta_hist[i] = log[kScalarLog + i];
+      }
+    }
   }
   arena_free(S, R->arena_off, R->bytes);
   L.occupied[k] = 0;

@@ -32,6 +32,7 @@ PCG_STENCIL_FP64_SUM = 0x4
 PCG_PARAM_MIXED_ETA, PCG_PARAM_MAX_RESTARTS, PCG_PARAM_BARRIER_TIMEOUT_MS, PCG_PARAM_TEST_BARRIER_PHANTOMS = 1, 2, 3, 4
 PCG_PARAM_TRUE_TOL = 5
 PCG_PARAM_ITER_STAGES = 6
+PCG_SCALAR_LOG = 32
 PCG_PERSISTENT = 0x8
 PCG_JACOBI = 0x10
 PCG_DOTS_SPLIT32 = 0x20
@@ -97,6 +98,7 @@ def lib() -> ctypes.CDLL:
         L.pcg_batch_set_class_occupancy.argtypes = [vp, i32, i32]
         L.pcg_batch_set_param.argtypes = [vp, i32, f64]
         L.pcg_batch_last_kernel_ms.argtypes = [vp, ctypes.POINTER(f64)]
+        L.pcg_batch_scalars.argtypes = [vp, i32, vp, vp]
         L.pcg_batch_destroy.argtypes = [vp]
         L.pcg_batch_destroy.restype = None
         L.pcg_server_create.argtypes = [ctypes.c_size_t, i32, ctypes.POINTER(vp)]
@@ -117,7 +119,8 @@ def lib() -> ctypes.CDLL:
                   "pcg_apply", "pcg_true_residual_noalloc", "pcg_set_param", "pcg_get_param", "pcg_set_shifts", "pcg_convert_check",
                   "pcg_psi_varsh",
                   "pcg_batch_create", "pcg_batch_solve", "pcg_batch_autotune", "pcg_batch_set_cluster",
-                  "pcg_batch_set_precision", "pcg_batch_set_param", "pcg_batch_last_kernel_ms", "pcg_server_create",
+                  "pcg_batch_set_precision", "pcg_batch_set_param", "pcg_batch_last_kernel_ms", "pcg_batch_scalars",
+                  "pcg_server_create",
                   "pcg_batch_classes", "pcg_batch_set_class_cluster", "pcg_batch_set_class_occupancy",
                   "pcg_submit", "pcg_submit_ex", "pcg_poll", "pcg_server_stats",
                   "pcg_kernel_stats", "pcg_kernel_stats_reset"):
@@ -443,6 +446,15 @@ class Batch:
         lib().pcg_batch_last_kernel_ms(self.h, ctypes.byref(v))
         return v.value
 
+    def scalars(self, k: int = PCG_SCALAR_LOG):
+        """alpha_i, beta_i (i < k) of every system of the last solve: two (nsys, k) arrays."""
+        a = np.empty((len(self.n), k))
+        b = np.empty((len(self.n), k))
+        s = lib().pcg_batch_scalars(self.h, k, a.ctypes.data, b.ctypes.data)
+        if s != PCG_OK:
+            raise PcgError(s, "pcg_batch_scalars")
+        return a, b
+
 
 class Server:
     """pcg_server: continuous batching of solve requests (host arrays in and out)."""
@@ -480,16 +492,24 @@ class Server:
         self.n[t.value] = P.n
         return t.value
 
-    def poll(self, ticket: int):
-        """None while pending, else (status, x, iters, true_relres)."""
+    def poll(self, ticket: int, scalars: bool = False):
+        """None while pending, else (status, x, iters, true_relres), and with scalars=True
+        also alpha_i, beta_i (i < min(iters, PCG_SCALAR_LOG)) as two arrays."""
         x = np.empty(self.n[ticket])
         res = pcg_result()
+        if scalars:
+            al = np.full(PCG_SCALAR_LOG, np.nan)
+            be = np.full(PCG_SCALAR_LOG, np.nan)
+            res.alpha_hist, res.beta_hist = al.ctypes.data, be.ctypes.data
         s = lib().pcg_poll(self.h, ticket, x.ctypes.data, ctypes.byref(res))
         if s == PCG_PENDING:
             return None
         if s not in (PCG_OK, PCG_ENOTCONV, PCG_EBREAKDOWN):
             raise PcgError(s, "pcg_poll")
         del self.n[ticket]
+        if scalars:
+            m = min(res.iters, PCG_SCALAR_LOG)
+            return s, x, res.iters, res.final_true_relres, al[:m], be[:m]
         return s, x, res.iters, res.final_true_relres
 
     def stats(self):

@@ -92,6 +92,7 @@ def test_argument_errors_of_the_extensions_without_gpu(libpath):
     assert L.pcg_batch_set_precision(None, B.PCG_MIXED_IR) == B.PCG_EINVAL
     assert L.pcg_batch_set_param(None, B.PCG_PARAM_MIXED_ETA, 0.5) == B.PCG_EINVAL
     assert L.pcg_batch_classes(None, None, None, None) == B.PCG_EINVAL
+    assert L.pcg_batch_scalars(None, 4, None, None) == B.PCG_EINVAL
     assert L.pcg_batch_set_class_cluster(None, 0, 2) == B.PCG_EINVAL
     assert L.pcg_batch_set_class_occupancy(None, 0, 4) == B.PCG_EINVAL
     out = vp(1)
