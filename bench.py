@@ -158,11 +158,15 @@ def job_throughput(units_per_rank: float, world: int, ms_max: float) -> float:
     return units_per_rank * world / (ms_max / 1e3)
 
 
-def cpu_oracle_rate(P, b, iters: int) -> tuple[float, float]:
+def cpu_oracle_rate(P, b, iters: int, omp: bool = False) -> tuple[float, float]:
+    """Iterations/s of the oracle's Algorithm 3 on (P, b): the single-threaded parity build,
+    or (omp) the same source built with OpenMP, on every host core."""
     import oracle
-    oracle.build()
+    oracle.build(omp=omp)
+    if omp:
+        oracle.threads(os.cpu_count() or 1)
     t0 = time.perf_counter()
-    oracle.pcg_sh(P, b, sigma=SIGMA, maxit=iters, log_every=0)
+    oracle.pcg_sh(P, b, sigma=SIGMA, maxit=iters, log_every=0, omp=omp)
     dt = time.perf_counter() - t0
     return iters / dt, dt
 
@@ -298,8 +302,24 @@ def serving_trace(nreq: int, rate: float, seed: int = 0, n_max_exp: float = 5.0,
     return reqs
 
 
-def serve_stream(pkg, reqs, flags: int, precision: int):
-    """Runs the request stream through one server; returns (latencies, span)."""
+def request_policy(P, form: str):
+    """Per-request (flags, precision) of a served form.  `fp64`: binary64, M = I.
+    `mixed`: mixed precision with binary64 refinement; M = I on the constant-coefficient
+    stencils (their diagonal is constant, so Jacobi would only rescale them while adding
+    the D^-1 traffic), Jacobi M^-1 on CSR (diagonals that vary from row to row).
+    `mixed_jacobi`: mixed precision with Jacobi on every request."""
+    import paper_1706_05988_gb300 as pkg
+    from paper_1706_05988_gb300 import pcg as C
+    if form == "fp64":
+        return 0, C.PCG_FP64
+    if form == "mixed_jacobi" or P.layout == 2:
+        return pkg.PCG_JACOBI, C.PCG_MIXED_IR
+    return 0, C.PCG_MIXED_IR
+
+
+def serve_stream(pkg, reqs, form: str):
+    """Runs the request stream through one server with the form's per-request policy;
+    returns (latencies, span)."""
     import numpy as np
     nreq = len(reqs)
     lat = np.zeros(nreq)
@@ -311,7 +331,8 @@ def serve_stream(pkg, reqs, flags: int, precision: int):
         while done < nreq:
             now = time.perf_counter() - t0
             while i < nreq and reqs[i][0] <= now:
-                pending[srv.submit(reqs[i][1], reqs[i][2], tol=reqs[i][3], flags=flags, precision=precision)] = i
+                flags, prec = request_policy(reqs[i][1], form)
+                pending[srv.submit(reqs[i][1], reqs[i][2], tol=reqs[i][3], flags=flags, precision=prec)] = i
                 i += 1
             for t in list(pending):
                 r = srv.poll(t)
@@ -325,27 +346,29 @@ def serve_stream(pkg, reqs, flags: int, precision: int):
     return lat, span
 
 
-def serving_measure(pkg, nreq: int, rate: float, tol=None, n_max_exp: float = 5.0) -> dict:
+def serving_measure(pkg, nreq: int, rate: float, tol=None, n_max_exp: float = 5.0,
+                    forms=("fp64", "mixed")) -> dict:
     """p50/p99 latency and solves/s of the request stream through the continuous-batching
-    server, in FP64 (M = I) and in mixed precision with FP64 refinement and Jacobi M^-1, against
-    the same stream served one request at a time by plain FP64 solves of the single-system
-    solver (same shift rule and tolerances).  tol: one tolerance for every request instead of
-    the trace's own."""
+    server, per served form (request_policy), against the same stream served one request at a
+    time by plain FP64 solves of the single-system solver (same shift rule and tolerances).
+    tol: one tolerance for every request instead of the trace's own."""
     import numpy as np
-    from paper_1706_05988_gb300 import pcg as C
     reqs = serving_trace(nreq, rate, n_max_exp=n_max_exp)
     if tol is not None:
         reqs = [(a, P, b, tol) for a, P, b, _ in reqs]
     tol_text = "tol log-uniform [1e-10, 1e-6]" if tol is None else f"tol {tol:g} for every request"
     out = {"workload": f"{nreq} requests, Poisson arrivals {rate:g}/s, n log-uniform [1e3, 1e{n_max_exp:g}], half 2D/3D "
-                       f"Laplacian stencils, half random SDD CSR (7-27 nnz/row), {tol_text}"}
+                       f"Laplacian stencils, half random SDD CSR (7-27 nnz/row), {tol_text}",
+           "unknowns_total": int(sum(P.n for _, P, _, _ in reqs)),
+           "policy": "served_mixed: mixed precision + FP64 refinement; M = I on the Laplacian stencils, Jacobi on "
+                     "CSR; served_mixed_jacobi: Jacobi on every request"}
 
     def summary(lat, span):
         return {"solves_per_s": nreq / span, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
-                "p99_ms": 1e3 * float(np.percentile(lat, 99))}
+                "p99_ms": 1e3 * float(np.percentile(lat, 99)), "span_s": span}
 
-    out["served_fp64"] = summary(*serve_stream(pkg, reqs, 0, C.PCG_FP64))
-    out["served_mixed_jacobi"] = summary(*serve_stream(pkg, reqs, pkg.PCG_JACOBI, C.PCG_MIXED_IR))
+    for form in forms:
+        out[f"served_{form}"] = summary(*serve_stream(pkg, reqs, form))
     # one at a time: each request starts when it has arrived and the previous one is done
     lat1 = np.zeros(nreq)
     t0 = time.perf_counter()
@@ -357,6 +380,11 @@ def serving_measure(pkg, nreq: int, rate: float, tol=None, n_max_exp: float = 5.
             one.solve(b, method="spcg", sigma=request_sigma(P), tol=tol, maxit=100000)
         lat1[k] = time.perf_counter() - t0 - arr
     out["one_at_a_time_fp64"] = summary(lat1, time.perf_counter() - t0)
+    base = out["one_at_a_time_fp64"]
+    for form in forms:
+        f = out[f"served_{form}"]
+        f["vs_one_at_a_time_fp64"] = {"solves_per_s_ratio": f["solves_per_s"] / base["solves_per_s"],
+                                      "p99_ratio": f["p99_ms"] / base["p99_ms"]}
     return out
 
 
@@ -409,17 +437,19 @@ def cpu_side_baselines(S, args, batch, varcoef) -> dict:
             "iters_per_s": k / t, "est_solve_ms": 1e3 * varcoef["fp64"]["iters"] * t / k,
             "sample": f"{k} iterations of the FP64 Jacobi solve ({t:.1f} s)"}
     if not args.no_serving:
+        # the n <= 1e5 stream (a request of the full range alone can keep one core busy for
+        # many minutes)
         budget, cnt, t0 = 5.0, 0, time.perf_counter()
-        for _, P, b, tol in serving_trace(args.serving_requests, args.serving_rate, n_max_exp=args.serving_n_max_exp,
+        for _, P, b, tol in serving_trace(max(args.serving_small_requests, 64), args.serving_rate, n_max_exp=5.0,
                                           first=64):
             oracle.pcg_sh(P, b, sigma=request_sigma(P), rtol=tol, maxit=100000, log_every=0)
             cnt += 1
             if time.perf_counter() - t0 > budget:
                 break
         t = time.perf_counter() - t0
-        out["serving_fp64"] = {"solves_per_s": cnt / t,
-                               "sample": f"the trace's first {cnt} requests back to back ({t:.1f} s), FP64, "
-                                         "the one-at-a-time shift rule and tolerances"}
+        out["serving_n_le_1e5_fp64"] = {"solves_per_s": cnt / t,
+                                        "sample": f"the n <= 1e5 stream's first {cnt} requests back to back "
+                                                  f"({t:.1f} s), FP64, the one-at-a-time shift rule and tolerances"}
     return out
 
 
@@ -543,6 +573,17 @@ def run_ours(args):
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{args.ref_iters} iterations of the same {N_SIDE}^3 shifted p-CG solve, single-threaded "
                          f"FP64 oracle ({dt:.1f} s; the host has {os.cpu_count()} cores)"}
+        # the same source built with OpenMP on its vector loops, on every host core
+        try:
+            import oracle
+            k_omp = 4 * args.ref_iters
+            rate_omp, dt_omp = cpu_oracle_rate(P, b_host, k_omp, omp=True)
+            cpu["openmp"] = {"value": rate_omp, "unit": UNIT, "cores": oracle.threads(0),
+                             "nproc": os.cpu_count(), "speedup_vs_one_core": rate_omp / rate,
+                             "sample": f"{k_omp} iterations of the same solve, the oracle's source built with "
+                                       f"-fopenmp ({dt_omp:.1f} s)"}
+        except Exception as e:   # no OpenMP runtime on this host
+            cpu["openmp"] = {"unavailable": str(e)[:200]}
 
     solver.close()
 
@@ -579,11 +620,19 @@ def run_ours(args):
     if not args.no_varcoef and world == 1:   # side measurements: single-GPU runs only
         varcoef = varcoef_measure(pkg, S)
 
-    serving = serving_1e8 = None
+    serving = serving_1e8 = serving_small = serving_small_1e8 = None
     if not args.no_serving and world == 1:   # side measurements: single-GPU runs only
-        serving = serving_measure(pkg, args.serving_requests, args.serving_rate, n_max_exp=args.serving_n_max_exp)
+        # the serving workload's full size range, on a bounded number of requests
         serving_1e8 = serving_measure(pkg, args.serving_requests, args.serving_rate, tol=1e-8,
                                       n_max_exp=args.serving_n_max_exp)
+        serving = serving_measure(pkg, args.serving_requests, args.serving_rate, n_max_exp=args.serving_n_max_exp)
+        # many small requests: n up to 1e5, where the cluster lanes carry everything
+        if args.serving_small_requests > 0:
+            small = ("fp64", "mixed", "mixed_jacobi")
+            serving_small_1e8 = serving_measure(pkg, args.serving_small_requests, args.serving_rate, tol=1e-8,
+                                                n_max_exp=5.0, forms=small)
+            serving_small = serving_measure(pkg, args.serving_small_requests, args.serving_rate, n_max_exp=5.0,
+                                            forms=small)
 
     # the same workload as CSR (int32 indices): config's second form, one timed step
     csr = None
@@ -627,7 +676,8 @@ def run_ours(args):
                                       "peak_sustained)"},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
                 "csr_int32": csr, "persistent": persistent, "varcoef_128": varcoef, "batch": batch,
-                "serving": serving, "serving_tol_1e-8": serving_1e8}
+                "serving": serving, "serving_tol_1e-8": serving_1e8,
+                "serving_n_le_1e5": serving_small, "serving_n_le_1e5_tol_1e-8": serving_small_1e8}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -714,10 +764,13 @@ def main():
     ap.add_argument("--batch-systems", type=int, default=512, help="systems in the batched-solve measurement")
     ap.add_argument("--batch-side-max", type=int, default=512, help="batched systems have sides U{32..this}")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
-    ap.add_argument("--serving-requests", type=int, default=400)
+    ap.add_argument("--serving-requests", type=int, default=48,
+                    help="requests of the full-range serving stream (n log-uniform in [1e3, 1e7])")
+    ap.add_argument("--serving-small-requests", type=int, default=400,
+                    help="requests of the extra serving stream with n <= 1e5 (0: skip it)")
     ap.add_argument("--serving-rate", type=float, default=2000.0, help="Poisson arrival rate, requests/s")
-    ap.add_argument("--serving-n-max-exp", type=float, default=5.0,
-                    help="serving requests have n log-uniform in [1e3, 10^this] (the full serving workload goes to 7)")
+    ap.add_argument("--serving-n-max-exp", type=float, default=7.0,
+                    help="serving requests have n log-uniform in [1e3, 10^this] (the serving workload's range: 7)")
     ap.add_argument("--size", type=int, default=N_SIDE, help="grid side (default: the 256^3 workload)")
     args = ap.parse_args()
     if args.profile_case:

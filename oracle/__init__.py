@@ -7,7 +7,9 @@ import it.  It shares no code with the CUDA path; the only module both sides
 use is `synthetic` (seeded problem data, none of the solver's arithmetic).
 
 Contents
-  build()          compile pcg_oracle.c with gcc (-O2 -ffp-contract=off)
+  build()          compile pcg_oracle.c with gcc (-O2 -ffp-contract=off); build(omp=True)
+                   also with -fopenmp, a second library used only to time the oracle on
+                   every host core (threads() sets its thread count)
   apply(P, x)      y = A x                         (operator of the model problem)
   cg(...)          Algorithm 1, classic CG
   pcg(...)         Algorithm 2, pipelined CG (written out without shift terms)
@@ -36,20 +38,26 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pcg_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
+_LIB_OMP = os.path.join(_BUILD, "liboracle_omp.so")
 _lib = None
+_lib_omp = None
 
 OP_CSR, OP_STENCIL2D, OP_STENCIL3D = 0, 1, 2
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle shared library (plain C, no vectorisation tricks)."""
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle shared library (plain C, no vectorisation tricks; single-threaded).
+    omp=True: the same source built a second time with -fopenmp (its vector loops and
+    reductions on all host cores), for timing only -- its reductions sum in another order,
+    and nothing compares against it."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
+    lib = _LIB_OMP if omp else _LIB
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+        tmp = lib + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-                               "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+                               *(["-fopenmp"] if omp else []), "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, lib)
+    return lib
 
 
 class _Op(ctypes.Structure):
@@ -67,18 +75,33 @@ class _State(ctypes.Structure):
     _fields_ = [(k, ctypes.c_void_p) for k in ("x", "r", "u", "w", "z", "q", "s", "t", "p")]
 
 
-def _load():
-    global _lib
+def _declare(lib):
+    vp, i32, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+    lib.oracle_apply.argtypes = [vp, vp, vp]
+    lib.oracle_cg.argtypes = [vp, vp, vp, vp, i32, f64, f64, i32, vp, vp, vp, vp, vp, vp]
+    lib.oracle_pcg_sh.argtypes = [vp, vp, vp, vp, f64, i32, f64, f64, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                  vp, vp, vp]
+    lib.oracle_pcg.argtypes = [vp, vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp]
+    lib.oracle_pcg_varsh.argtypes = [vp, vp, vp, vp, vp, i32, f64, i32, vp, vp, vp, vp, vp, vp]
+    lib.oracle_threads.argtypes = [i32]
+    for f in (lib.oracle_cg, lib.oracle_pcg_sh, lib.oracle_pcg, lib.oracle_pcg_varsh, lib.oracle_threads):
+        f.restype = ctypes.c_int
+    return lib
+
+
+def threads(n: int = 0, omp: bool = True) -> int:
+    """Set (n > 0) and return the thread count of the OpenMP build (1 for the serial one)."""
+    return _load(omp).oracle_threads(n)
+
+
+def _load(omp: bool = False):
+    global _lib, _lib_omp
+    if omp:
+        if _lib_omp is None:
+            _lib_omp = _declare(ctypes.CDLL(build(omp=True)))
+        return _lib_omp
     if _lib is None:
-        _lib = ctypes.CDLL(build())
-        vp, i32, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
-        _lib.oracle_apply.argtypes = [vp, vp, vp]
-        _lib.oracle_cg.argtypes = [vp, vp, vp, vp, i32, f64, f64, i32, vp, vp, vp, vp, vp, vp]
-        _lib.oracle_pcg_sh.argtypes = [vp, vp, vp, vp, f64, i32, f64, f64, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
-        _lib.oracle_pcg.argtypes = [vp, vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp]
-        _lib.oracle_pcg_varsh.argtypes = [vp, vp, vp, vp, vp, i32, f64, i32, vp, vp, vp, vp, vp, vp]
-        for f in (_lib.oracle_cg, _lib.oracle_pcg_sh, _lib.oracle_pcg, _lib.oracle_pcg_varsh):
-            f.restype = ctypes.c_int
+        _lib = _declare(ctypes.CDLL(build()))
     return _lib
 
 
@@ -131,6 +154,9 @@ class Run:
     gamma: Optional[np.ndarray] = None
     delta: Optional[np.ndarray] = None
     state: Optional[dict] = None
+    gap_g: Optional[np.ndarray] = None     # ||(A p_i - sigma t_i) - s_i||   (Section 3.1; NaN where not logged)
+    gap_h: Optional[np.ndarray] = None     # ||(A u_i - sigma r_i) - w_i||
+    gap_j: Optional[np.ndarray] = None     # ||A q_i - z_i||
 
 
 def apply(P, x: np.ndarray) -> np.ndarray:
@@ -170,9 +196,11 @@ def cg(P, b, x0=None, maxit=100, rtol=0.0, ttol=0.0, log_every=1, minv=None) -> 
 
 
 def pcg_sh(P, b, x0=None, sigma=0.0, maxit=100, rtol=0.0, ttol=0.0, log_every=1, minv=None,
-           want_state=False) -> Run:
-    """Algorithm 3 (shifted pipelined CG); sigma = 0 gives Algorithm 2's recurrences."""
-    lib = _load()
+           want_state=False, omp=False, gaps=False) -> Run:
+    """Algorithm 3 (shifted pipelined CG); sigma = 0 gives Algorithm 2's recurrences.
+    gaps=True also logs ||g_i||, ||h_i||, ||j_i|| (Section 3.1) where the true residual is
+    logged.  omp=True runs the OpenMP build (timing only; see build)."""
+    lib = _load(omp)
     h = _OpHolder(P)
     b = np.ascontiguousarray(b, dtype=np.float64)
     x = np.zeros(P.n) if x0 is None else np.array(x0, dtype=np.float64)
@@ -187,13 +215,18 @@ def pcg_sh(P, b, x0=None, sigma=0.0, maxit=100, rtol=0.0, ttol=0.0, log_every=1,
         cs = _State(**{k: v.ctypes.data for k, v in st.items()})
         stp = ctypes.byref(cs)
     mv = _minv(minv)
+    gg, hh, jj = (np.full(maxit + 1, np.nan) for _ in range(3))
+    want = gaps and log_every > 0
     rc = lib.oracle_pcg_sh(h.ref, _ptr(mv), b.ctypes.data, x.ctypes.data, float(sigma), maxit, rtol, ttol,
                            log_every, al.ctypes.data, be.ctypes.data, rec.ctypes.data, tru.ctypes.data,
-                           gap.ctypes.data, ga.ctypes.data, de.ctypes.data, ctypes.byref(info), stp)
+                           gap.ctypes.data, ga.ctypes.data, de.ctypes.data, ctypes.byref(info), stp,
+                           gg.ctypes.data if want else None, hh.ctypes.data if want else None,
+                           jj.ctypes.data if want else None)
     if rc != 0:
         raise MemoryError("oracle_pcg_sh allocation failed")
     k = info.iters
-    return Run(x, k, info.status, al[:k], be[:k], rec[:k + 1], tru[:k + 1], gap[:k + 1], ga[:k], de[:k], st)
+    return Run(x, k, info.status, al[:k], be[:k], rec[:k + 1], tru[:k + 1], gap[:k + 1], ga[:k], de[:k], st,
+               gg[:k + 1] if want else None, hh[:k + 1] if want else None, jj[:k + 1] if want else None)
 
 
 def pcg(P, b, x0=None, maxit=100, log_every=1, minv=None) -> Run:

@@ -54,8 +54,12 @@ def cg(A, b, x0=None, iters: int = 10, minv: Optional[Sequence[F]] = None):
     return alphas, betas[:len(alphas)], x, xs
 
 
-def pcg_sh(A, b, x0=None, sigma=F(0), iters: int = 10, minv: Optional[Sequence[F]] = None):
-    """Algorithm 3 (Algorithm 2 for sigma = 0).  Same return convention as cg()."""
+def pcg_sh(A, b, x0=None, sigma=F(0), iters: int = 10, minv: Optional[Sequence[F]] = None, gap_log=None):
+    """Algorithm 3 (Algorithm 2 for sigma = 0).  Same return convention as cg().
+    gap_log (a list): receives, per iteration i, the largest entry magnitudes of the gaps of
+    Section 3.1: f_i = (b - A x_i) - r_i, h_i = (A u_i - sigma r_i) - w_i (at the start of
+    the iteration), g_i = (A p_i - sigma t_i) - s_i and j_i = A q_i - z_i (once p_i, t_i,
+    s_i, q_i, z_i are formed)."""
     n = len(b)
     sigma = F(sigma)
     x = [F(0)] * n if x0 is None else [F(v) for v in x0]
@@ -87,6 +91,14 @@ def pcg_sh(A, b, x0=None, sigma=F(0), iters: int = 10, minv: Optional[Sequence[F
         s = [wi + bt * si for wi, si in zip(w, s)]
         t = [ri + bt * ti for ri, ti in zip(r, t)]
         p = [ui + bt * pi for ui, pi in zip(u, p)]
+        if gap_log is not None:
+            def mx(v):
+                return max((abs(e) for e in v), default=F(0))
+            f_i = [bi - ai - ri for bi, ai, ri in zip(b, _mv(A, x), r)]
+            h_i = [ai - sigma * ri - wi for ai, ri, wi in zip(_mv(A, u), r, w)]
+            g_i = [ai - sigma * ti - si for ai, ti, si in zip(_mv(A, p), t, s)]
+            j_i = [ai - zi for ai, zi in zip(_mv(A, q), z)]
+            gap_log.append({"f": mx(f_i), "g": mx(g_i), "h": mx(h_i), "j": mx(j_i)})
         x = [xi + a * pi for xi, pi in zip(x, p)]
         r = [ri - (a * si + a * sigma * ti) for ri, si, ti in zip(r, s, t)]
         u = [ui - (a * qi + a * sigma * pi) for ui, qi, pi in zip(u, q, p)]

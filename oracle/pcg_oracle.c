@@ -5,6 +5,11 @@
  * cpu_baseline / reference legs of bench.py may load this library.  It shares
  * no code, header or helper with the CUDA path.
  *
+ * The vector loops carry OpenMP pragmas.  The library the tests and the parity checks
+ * use is built without -fopenmp, so the pragmas are ignored and every loop runs in the
+ * order written.  bench.py also times a second build with -fopenmp (a baseline on all
+ * host cores); its reductions sum in another order, so it is never used as a reference.
+ *
  * Source: S. Cools, W. Vanroose, "Numerically stable variants of the
  * communication-hiding pipelined Conjugate Gradients algorithm for the parallel
  * solution of large scale symmetric linear systems" (arXiv 1706.05988).
@@ -45,7 +50,22 @@
 #include <stdlib.h>
 #include <string.h>
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 enum { OP_CSR = 0, OP_STENCIL2D = 1, OP_STENCIL3D = 2 };
+
+/* Threads of the OpenMP build (returns the count in use; 1 in the serial build). */
+int oracle_threads(int32_t nthreads) {
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+  return omp_get_max_threads();
+#else
+  (void)nthreads;
+  return 1;
+#endif
+}
 
 typedef struct {
   int32_t kind;
@@ -74,6 +94,7 @@ typedef struct {
    neighbours -x, +x, -y, +y, -z, +z that lie inside the Dirichlet domain. */
 void oracle_apply(const oracle_op *A, const double *x, double *y) {
   if (A->kind == OP_CSR) {
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < A->n; ++i) {
       double acc = 0.0;
       for (int32_t k = A->row_ptr[i]; k < A->row_ptr[i + 1]; ++k) acc += A->val[k] * x[A->col[k]];
@@ -84,6 +105,7 @@ void oracle_apply(const oracle_op *A, const double *x, double *y) {
   const int64_t nx = A->nx, ny = A->ny, nz = (A->kind == OP_STENCIL3D) ? A->nz : 1;
   const int is3d = (A->kind == OP_STENCIL3D);
   const double centre = is3d ? 6.0 : 4.0;
+#pragma omp parallel for collapse(2) schedule(static)
   for (int64_t k = 0; k < nz; ++k)
     for (int64_t j = 0; j < ny; ++j)
       for (int64_t i = 0; i < nx; ++i) {
@@ -112,6 +134,7 @@ void oracle_apply(const oracle_op *A, const double *x, double *y) {
 
 double oracle_dot(int64_t n, const double *a, const double *b) {
   double s = 0.0;
+#pragma omp parallel for reduction(+ : s) schedule(static)
   for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
   return s;
 }
@@ -120,6 +143,7 @@ double oracle_nrm2(int64_t n, const double *a) { return sqrt(oracle_dot(n, a, a)
 
 /* M^{-1} v (identity when minv == NULL). */
 static void apply_minv(int64_t n, const double *minv, const double *v, double *out) {
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) out[i] = minv ? minv[i] * v[i] : v[i];
 }
 
@@ -129,6 +153,7 @@ static void log_true(const oracle_op *A, const double *b, const double *x, const
   const int64_t n = A->n;
   oracle_apply(A, x, work);
   double s1 = 0.0, s2 = 0.0;
+#pragma omp parallel for reduction(+ : s1, s2) schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     const double e = b[i] - work[i];
     const double g = e - r[i];
@@ -164,6 +189,7 @@ int oracle_cg(const oracle_op *A, const double *minv, const double *b, double *x
   const double bnorm = oracle_nrm2(n, b);
 
   oracle_apply(A, x, work);                         /* r_0 := b - A x_0 */
+  #pragma omp parallel for schedule(static)
   for (int64_t j = 0; j < n; ++j) r[j] = b[j] - work[j];
   apply_minv(n, minv, r, u);                        /* u_0 := M^{-1} r_0 */
   memcpy(p, u, (size_t)n * sizeof(double));         /* p_0 := u_0 */
@@ -183,12 +209,15 @@ int oracle_cg(const oracle_op *A, const double *minv, const double *b, double *x
     if (!(sp > 0.0) || !isfinite(sp)) { status = 2; break; }
     const double a = gamma / sp;                    /* alpha_i := (r_i,u_i)/(s_i,p_i) */
     if (alpha) alpha[i] = a;
+    #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) x[j] = x[j] + a * p[j];
+    #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) r[j] = r[j] - a * s[j];
     apply_minv(n, minv, r, u);
     const double gamma_new = oracle_dot(n, r, u);
     const double bt = gamma_new / gamma;            /* beta_{i+1} */
     if (beta) beta[i + 1] = bt;
+    #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) p[j] = u[j] + bt * p[j];
     gamma = gamma_new;
   }
@@ -201,22 +230,46 @@ int oracle_cg(const oracle_op *A, const double *minv, const double *b, double *x
 
 /* ---- Algorithm 3: shifted pipelined CG (Algorithm 2 when sigma == 0) ------ */
 
+/* ||A a - sigma c - d||_2 (c may be NULL: no shift term); work holds A a afterwards. */
+static double gap_norm(const oracle_op *A, const double *a, double sigma, const double *c, const double *d,
+                       double *work) {
+  const int64_t n = A->n;
+  oracle_apply(A, a, work);
+  double s = 0.0;
+#pragma omp parallel for reduction(+ : s) schedule(static)
+  for (int64_t j = 0; j < n; ++j) {
+    const double e = (c ? work[j] - sigma * c[j] : work[j]) - d[j];
+    s += e * e;
+  }
+  return sqrt(s);
+}
+
+/* Algorithm 3.  gg, hh, jj (optional, maxit+1 entries): the norms of the gaps of Section
+   3.1 at the logged iterations (NaN elsewhere):
+     hh[i] = ||(A u_i - sigma r_i) - w_i||   (at the start of iteration i),
+     gg[i] = ||(A p_i - sigma t_i) - s_i||   (after p_i, t_i, s_i are formed),
+     jj[i] = ||A q_i - z_i||                 (after q_i, z_i are formed);
+   the final iterate logs hh only. */
 int oracle_pcg_sh(const oracle_op *A, const double *minv, const double *b, double *x, double sigma, int32_t maxit,
                   double rtol, double ttol, int32_t log_every, double *alpha, double *beta, double *rec, double *tru,
-                  double *gap, double *gamma_h, double *delta_h, oracle_info *info, oracle_state *state) {
+                  double *gap, double *gamma_h, double *delta_h, oracle_info *info, oracle_state *state,
+                  double *gg, double *hh, double *jj) {
   const int64_t n = A->n;
   double *r = zeros(n), *u = zeros(n), *w = zeros(n), *m = zeros(n), *nn = zeros(n), *z = zeros(n), *q = zeros(n),
          *s = zeros(n), *t = zeros(n), *p = zeros(n), *work = zeros(n);
   if (!r || !u || !w || !m || !nn || !z || !q || !s || !t || !p || !work) return -1;
   fill_nan(alpha, maxit + 1); fill_nan(beta, maxit + 1); fill_nan(rec, maxit + 1);
   fill_nan(tru, maxit + 1); fill_nan(gap, maxit + 1); fill_nan(gamma_h, maxit + 1); fill_nan(delta_h, maxit + 1);
+  fill_nan(gg, maxit + 1); fill_nan(hh, maxit + 1); fill_nan(jj, maxit + 1);
   const double bnorm = oracle_nrm2(n, b);
 
   /* r_0 := b - A x_0; u_0 := M^{-1} r_0; w_0 := A u_0 - sigma r_0 */
   oracle_apply(A, x, work);
+  #pragma omp parallel for schedule(static)
   for (int64_t j = 0; j < n; ++j) r[j] = b[j] - work[j];
   apply_minv(n, minv, r, u);
   oracle_apply(A, u, work);
+  #pragma omp parallel for schedule(static)
   for (int64_t j = 0; j < n; ++j) w[j] = work[j] - sigma * r[j];
 
   double gamma_prev = 0.0, alpha_prev = 0.0;
@@ -224,12 +277,14 @@ int oracle_pcg_sh(const oracle_op *A, const double *minv, const double *b, doubl
   for (;; ++i) {
     if (rec) rec[i] = oracle_nrm2(n, r);
     if (want_log(i, log_every)) log_true(A, b, x, r, work, tru ? &tru[i] : NULL, gap ? &gap[i] : NULL);
+    if (hh && want_log(i, log_every)) hh[i] = gap_norm(A, u, sigma, r, w, work);
     if (rtol > 0 && oracle_nrm2(n, r) <= rtol * bnorm) { status = 1; break; }
     if (ttol > 0 && want_log(i, log_every) && tru && tru[i] <= ttol * bnorm) { status = 1; break; }
     if (i >= maxit) break;
 
     const double gamma = oracle_dot(n, r, u);       /* gamma_i := (r_i, u_i) */
     double delta = 0.0;                             /* delta := (w_i + sigma r_i, u_i) */
+#pragma omp parallel for reduction(+ : delta) schedule(static)
     for (int64_t j = 0; j < n; ++j) delta += (w[j] + sigma * r[j]) * u[j];
     if (gamma_h) gamma_h[i] = gamma;
     if (delta_h) delta_h[i] = delta;
@@ -250,20 +305,33 @@ int oracle_pcg_sh(const oracle_op *A, const double *minv, const double *b, doubl
     if (alpha) alpha[i] = a;
     if (beta) beta[i] = bt;
     const double as = a * sigma;
+    #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) z[j] = nn[j] + bt * z[j];   /* z_i */
+    #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) q[j] = m[j] + bt * q[j];    /* q_i */
+    #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) s[j] = w[j] + bt * s[j];    /* s_i */
+    #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) t[j] = r[j] + bt * t[j];    /* t_i */
+    #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) p[j] = u[j] + bt * p[j];    /* p_i */
+    if (gg && want_log(i, log_every)) gg[i] = gap_norm(A, p, sigma, t, s, work);
+    if (jj && want_log(i, log_every)) jj[i] = gap_norm(A, q, 0.0, NULL, z, work);
+    #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) x[j] = x[j] + a * p[j];     /* x_{i+1} */
+    #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) r[j] = r[j] - (a * s[j] + as * t[j]);   /* r_{i+1} */
+    #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) u[j] = u[j] - (a * q[j] + as * p[j]);   /* u_{i+1} */
+    #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) w[j] = w[j] - a * z[j];     /* w_{i+1} */
     gamma_prev = gamma;
     alpha_prev = a;
   }
-  if (log_every > 0 && !want_log(i, log_every))   /* the final iterate is always logged */
+  if (log_every > 0 && !want_log(i, log_every)) {   /* the final iterate is always logged */
     log_true(A, b, x, r, work, tru ? &tru[i] : NULL, gap ? &gap[i] : NULL);
+    if (hh) hh[i] = gap_norm(A, u, sigma, r, w, work);
+  }
   if (info) { info->iters = i; info->status = status; }
   if (state) {
     const size_t bytes = (size_t)n * sizeof(double);
@@ -293,6 +361,7 @@ int oracle_pcg(const oracle_op *A, const double *minv, const double *b, double *
   fill_nan(tru, maxit + 1); fill_nan(gap, maxit + 1);
 
   oracle_apply(A, x, work);                         /* r_0 := b - A x_0 */
+  #pragma omp parallel for schedule(static)
   for (int64_t j = 0; j < n; ++j) r[j] = b[j] - work[j];
   apply_minv(n, minv, r, u);                        /* u_0 := M^{-1} r_0 */
   oracle_apply(A, u, w);                            /* w_0 := A u_0 */
@@ -320,14 +389,23 @@ int oracle_pcg(const oracle_op *A, const double *minv, const double *b, double *
     }
     if (alpha) alpha[i] = a;
     if (beta) beta[i] = bt;
+    #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) z[j] = nn[j] + bt * z[j];
+    #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) q[j] = m[j] + bt * q[j];
+    #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) s[j] = w[j] + bt * s[j];
+    #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) t[j] = r[j] + bt * t[j];
+    #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) p[j] = u[j] + bt * p[j];
+    #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) x[j] = x[j] + a * p[j];
+    #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) r[j] = r[j] - a * s[j];
+    #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) u[j] = u[j] - a * q[j];
+    #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) w[j] = w[j] - a * z[j];
     gamma_prev = gamma;
     alpha_prev = a;
@@ -358,9 +436,11 @@ int oracle_pcg_varsh(const oracle_op *A, const double *minv, const double *b, do
 
   /* r_0 := b - A x_0; u_0 := M^{-1} r_0; w_0 := A u_0 - sigma_{-1} r_0 */
   oracle_apply(A, x, work);
+  #pragma omp parallel for schedule(static)
   for (int64_t j = 0; j < n; ++j) r[j] = b[j] - work[j];
   apply_minv(n, minv, r, u);
   oracle_apply(A, u, work);
+  #pragma omp parallel for schedule(static)
   for (int64_t j = 0; j < n; ++j) w[j] = work[j] - shifts[0] * r[j];
 
   double gamma_prev = 0.0, alpha_prev = 0.0;
@@ -374,6 +454,7 @@ int oracle_pcg_varsh(const oracle_op *A, const double *minv, const double *b, do
     const double ds = scur - sprev;
     const double gamma = oracle_dot(n, r, u);        /* gamma_i := (r_i, u_i) */
     double delta = 0.0;                              /* delta := (w_i + sigma_{i-1} r_i, u_i) */
+#pragma omp parallel for reduction(+ : delta) schedule(static)
     for (int64_t j = 0; j < n; ++j) delta += (w[j] + sprev * r[j]) * u[j];
     if (gamma == 0.0) { status = 1; break; }
     apply_minv(n, minv, w, m);                       /* m_i := M^{-1} w_i */
@@ -392,14 +473,23 @@ int oracle_pcg_varsh(const oracle_op *A, const double *minv, const double *b, do
     if (alpha) alpha[i] = a;
     if (beta) beta[i] = bt;
     const double as = a * scur;
+    #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) t[j] = r[j] + bt * t[j];                    /* t_i */
+    #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) p[j] = u[j] + bt * p[j];                    /* p_i */
+    #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) s[j] = (w[j] + bt * s[j]) - ds * t[j];      /* s_i */
+    #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) q[j] = (m[j] + bt * q[j]) - ds * p[j];      /* q_i */
+    #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) z[j] = (nn[j] + bt * z[j]) - ds * (s[j] + scur * t[j]);   /* z_i */
+    #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) x[j] = x[j] + a * p[j];                     /* x_{i+1} */
+    #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) w[j] = (w[j] - a * z[j]) - ds * r[j];       /* w_{i+1} (before r) */
+    #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) r[j] = r[j] - (a * s[j] + as * t[j]);       /* r_{i+1} */
+    #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) u[j] = u[j] - (a * q[j] + as * p[j]);       /* u_{i+1} */
     gamma_prev = gamma;
     alpha_prev = a;

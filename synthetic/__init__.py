@@ -244,20 +244,160 @@ def to_csr(p: Problem) -> Problem:
                    meta={"from": p.name, "nx": nx, "ny": ny, "nz": nz})
 
 
-def random_sdd_csr(n: int, seed: int = 0, nnz_lo: int = 7, nnz_hi: int = 27, margin: float = 1e-2) -> Problem:
-    """Random symmetric strictly diagonally dominant CSR matrix (SPD).
-
-    Each row draws a target count d ~ U{nnz_lo..nnz_hi} of entries; (d - 1) // 2 partner
-    columns are drawn uniformly among the other rows and the pattern is mirrored, so rows
-    hold about nnz_lo..nnz_hi entries.  Off-diagonals ~ U[-1, 0]; the diagonal is
-    (1 + margin) * sum |off-diagonals| of its row (strict dominance makes A SPD)."""
-    import scipy.sparse as sp
+def _sdd_draws(n: int, seed: int, nnz_lo: int, nnz_hi: int):
+    """The random draws of random_sdd_csr: upper partners and their values."""
     d = nnz_lo + (splitmix64(seed, n) % np.uint64(nnz_hi - nnz_lo + 1)).astype(np.int64)
     k = (d - 1) // 2
     rows = np.repeat(np.arange(n, dtype=np.int64), k)
     cols = (splitmix64(seed + 1, rows.size) % np.uint64(max(n - 1, 1))).astype(np.int64)
     cols = cols + (cols >= rows)                     # never the diagonal
     vals = -uniform01(seed + 2, rows.size)
+    return rows, cols, vals
+
+
+def _i64(u: int) -> int:
+    """The int64 with the bits of uint64 u."""
+    return int(np.array(u, dtype=np.uint64).view(np.int64))
+
+
+def _splitmix64_t(seed: int, count: int, dev):
+    """splitmix64(seed, count) as an int64 torch tensor holding the same 64 bits (wrapping
+    int64 arithmetic; >> made logical with a mask)."""
+    import torch
+
+    def lsr(z, sh):
+        return (z >> sh) & ((1 << (64 - sh)) - 1)
+
+    z = torch.arange(1, count + 1, dtype=torch.int64, device=dev) * _i64(int(GOLDEN)) + _i64(seed)
+    z = (z ^ lsr(z, 30)) * _i64(int(_M1))
+    z = (z ^ lsr(z, 27)) * _i64(int(_M2))
+    return z ^ lsr(z, 31)
+
+
+def _umod_t(z, m: int):
+    """(uint64 bits of z) mod m for 0 < m < 2^31, in int64 arithmetic."""
+    hi = (z >> 32) & 0xFFFFFFFF
+    lo = z & 0xFFFFFFFF
+    return ((hi % m) * ((1 << 32) % m) + lo) % m
+
+
+def _seq_segment_sum(v, start, length, maxlen: int):
+    """Sum of each segment v[start : start + length], added left to right (the order of
+    numpy's reduceat), with elementwise passes only: the same bits on any device."""
+    import torch
+    acc = v[start].clone()
+    last = v.numel() - 1
+    for j in range(1, maxlen):
+        idx = torch.clamp(start + j, max=last)
+        acc = acc + torch.where(length > j, v[idx], torch.zeros_like(acc))
+    return acc
+
+
+def random_sdd_csr(n: int, seed: int = 0, nnz_lo: int = 7, nnz_hi: int = 27, margin: float = 1e-2) -> Problem:
+    """Random symmetric strictly diagonally dominant CSR matrix (SPD).
+
+    Each row draws a target count d ~ U{nnz_lo..nnz_hi} of entries; (d - 1) // 2 partner
+    columns are drawn uniformly among the other rows and the pattern is mirrored, so rows
+    hold about nnz_lo..nnz_hi entries.  Off-diagonals ~ U[-1, 0] (a pair drawn twice is
+    summed); the diagonal is (1 + margin) * sum |off-diagonals| of its row (strict
+    dominance makes A SPD).  Columns are sorted within each row.
+
+    Assembly (torch, on a GPU when one is present): the draws are grouped by unordered pair
+    with a stable sort and a pair drawn more than once is summed in draw order (so (i, j) and
+    (j, i) hold the same bits); the mirrored entries and one diagonal slot per row are then
+    ordered by their (row, column) keys, and each row's absolute sum is added left to right.
+    Every sum is an explicit left-to-right pass, so the result has the same bits on any
+    device and equals random_sdd_csr_numpy's (tested)."""
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    d = nnz_lo + _umod_t(_splitmix64_t(seed, n, dev), nnz_hi - nnz_lo + 1)
+    k = (d - 1) // 2
+    rows = torch.repeat_interleave(torch.arange(n, dtype=torch.int64, device=dev), k)
+    m = rows.numel()
+    cols = _umod_t(_splitmix64_t(seed + 1, m, dev), max(n - 1, 1))
+    cols = cols + (cols >= rows).to(torch.int64)
+    vals = -(((_splitmix64_t(seed + 2, m, dev) >> 11) & ((1 << 53) - 1)).to(torch.float64) * (2.0 ** -53))
+    # one value per unordered pair {i, j}: pairs drawn more than once are summed first, in
+    # draw order, so that (i, j) and (j, i) hold the same bits
+    lo = torch.minimum(rows, cols)
+    hi = torch.maximum(rows, cols)
+    pkey, perm = torch.sort(lo * n + hi, stable=True)
+    pval = vals[perm]
+    first = torch.ones_like(pkey, dtype=torch.bool)
+    first[1:] = pkey[1:] != pkey[:-1]
+    pstart = torch.nonzero(first).flatten()
+    plen = torch.diff(pstart, append=torch.tensor([pkey.numel()], device=dev))
+    pval = _seq_segment_sum(pval, pstart, plen, int(plen.max()) if plen.numel() else 1)
+    pkey = pkey[pstart]
+    lo = pkey // n
+    hi = pkey - lo * n
+    # mirror, add one diagonal slot per row, and order by (row, column)
+    diag_idx = torch.arange(n, dtype=torch.int64, device=dev)
+    key = torch.cat([lo * n + hi, hi * n + lo, diag_idx * (n + 1)])
+    val = torch.cat([pval, pval, torch.zeros(n, dtype=torch.float64, device=dev)])
+    key, perm = torch.sort(key)            # keys are unique now
+    val = val[perm]
+    row = key // n
+    col = key - row * n
+    counts = torch.bincount(row, minlength=n)
+    row_ptr = torch.zeros(n + 1, dtype=torch.int64, device=dev)
+    row_ptr[1:] = torch.cumsum(counts, 0)
+    offsum = _seq_segment_sum(val.abs(), row_ptr[:-1], counts, int(counts.max()))   # diagonal slot is 0
+    diag = (1.0 + margin) * offsum
+    diag[diag == 0] = 1.0
+    on_diag = col == row
+    val[on_diag] = diag[row[on_diag]]
+    assert int(row_ptr[-1]) < 2 ** 31
+    return Problem(CSR32, row_ptr=row_ptr.to(torch.int32).cpu().numpy(), col=col.to(torch.int32).cpu().numpy(),
+                   val=np.ascontiguousarray(val.cpu().numpy(), dtype=np.float64), n_csr=n, name=f"sdd_{n}")
+
+
+def _seq_segment_sum_np(v, start, length):
+    """_seq_segment_sum in numpy: each segment added left to right."""
+    acc = v[start].copy()
+    for j in range(1, int(length.max())):
+        idx = np.minimum(start + j, v.size - 1)
+        acc = acc + np.where(length > j, v[idx], 0.0)
+    return acc
+
+
+def random_sdd_csr_numpy(n: int, seed: int = 0, nnz_lo: int = 7, nnz_hi: int = 27, margin: float = 1e-2) -> Problem:
+    """random_sdd_csr in plain numpy (single-threaded; the reference for its bits)."""
+    rows, cols, vals = _sdd_draws(n, seed, nnz_lo, nnz_hi)
+    lo = np.minimum(rows, cols)
+    hi = np.maximum(rows, cols)
+    perm = np.argsort(lo * n + hi, kind="stable")
+    pkey = (lo * n + hi)[perm]
+    pval = vals[perm]
+    pstart = np.flatnonzero(np.r_[True, pkey[1:] != pkey[:-1]])
+    pval = _seq_segment_sum_np(pval, pstart, np.diff(np.r_[pstart, pkey.size]))
+    pkey = pkey[pstart]
+    lo = pkey // n
+    hi = pkey - lo * n
+    diag_idx = np.arange(n, dtype=np.int64)
+    key = np.concatenate([lo * n + hi, hi * n + lo, diag_idx * (n + 1)])
+    val = np.concatenate([pval, pval, np.zeros(n)])
+    perm = np.argsort(key, kind="stable")
+    key = key[perm]
+    val = val[perm]
+    row = key // n
+    col = key - row * n
+    counts = np.bincount(row, minlength=n)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    offsum = _seq_segment_sum_np(np.abs(val), row_ptr[:-1], counts)
+    diag = (1.0 + margin) * offsum
+    diag[diag == 0] = 1.0
+    on_diag = col == row
+    val[on_diag] = diag[row[on_diag]]
+    return Problem(CSR32, row_ptr=row_ptr.astype(np.int32), col=col.astype(np.int32),
+                   val=np.ascontiguousarray(val, dtype=np.float64), n_csr=n, name=f"sdd_{n}")
+
+
+def random_sdd_csr_scipy(n: int, seed: int = 0, nnz_lo: int = 7, nnz_hi: int = 27, margin: float = 1e-2) -> Problem:
+    """The same matrix assembled with scipy.sparse (slow; a cross-check of random_sdd_csr)."""
+    import scipy.sparse as sp
+    rows, cols, vals = _sdd_draws(n, seed, nnz_lo, nnz_hi)
     U = sp.coo_matrix((vals, (rows, cols)), shape=(n, n)).tocsr()
     A = (U + U.T).tocsr()
     A.sum_duplicates()

@@ -35,12 +35,22 @@ def test_request_sigma():
 
 def test_cpu_side_baselines_small():
     a = argparse.Namespace(batch_systems=8, batch_side_max=40, no_serving=False, serving_requests=30,
-                           serving_rate=2000.0, serving_n_max_exp=3.3)
+                           serving_small_requests=30, serving_rate=2000.0, serving_n_max_exp=3.3)
     work = 8 * 1000 * 100.0
     out = bench.cpu_side_baselines(S, a, {"fp64_jacobi": {"unknown_iterations": work}}, None)
     bt = out["batch_fp64_jacobi"]
     assert bt["solves_per_s"] > 0 and bt["est_batch_s"] > 0
     assert abs(bt["solves_per_s"] * bt["est_batch_s"] - 8) < 1e-9
-    sv = out["serving_fp64"]
+    sv = out["serving_n_le_1e5_fp64"]
     assert sv["solves_per_s"] > 0 and "requests back to back" in sv["sample"]
     assert "varcoef_128_fp64_jacobi" not in out
+
+
+def test_request_policy():
+    """served_mixed: mixed precision everywhere, Jacobi only on CSR; fp64: binary64, M = I."""
+    from paper_1706_05988_gb300 import pcg as C
+    lap, csr = S.laplacian_2d(10), S.random_sdd_csr(50, seed=2)
+    assert bench.request_policy(lap, "fp64") == (0, C.PCG_FP64)
+    assert bench.request_policy(lap, "mixed") == (0, C.PCG_MIXED_IR)
+    assert bench.request_policy(csr, "mixed") == (C.PCG_JACOBI, C.PCG_MIXED_IR)
+    assert bench.request_policy(lap, "mixed_jacobi") == (C.PCG_JACOBI, C.PCG_MIXED_IR)

@@ -413,6 +413,21 @@ def test_select_sigma_lapl200(B):
     assert sg == 4.0
 
 
+def test_select_sigma_lapl3d_matches_oracle(B):
+    """The second selection case (32^3 Laplacian, 100-iteration unshifted pilot): the device's
+    pilot and psi evaluation pick the oracle's shift, with psi on the grid to 1e-6."""
+    from oracle import psi as PS
+    from paper_1706_05988_gb300 import pcg as C
+    P, b, _ = S.poisson3d_manufactured(32)
+    grid = np.linspace(0.5, 12.0, 24)
+    pil = oracle.pcg_sh(P, b, sigma=0.0, maxit=100, log_every=0)
+    so, vo = PS.select_sigma(pil.alpha, pil.beta, 99, grid)
+    with B.Solver(P) as s:
+        sg, psi = C.pcg_select_sigma(s.ctx, b, 100, grid)
+    assert sg == so == 1.0
+    assert rel(psi, vo) < 1e-6
+
+
 # ---------------------------------------------------------------- full size: 256^3 stencil (n = 16.8M)
 
 @pytest.fixture(scope="module")

@@ -332,14 +332,35 @@ def test_psi_product_order_matters():
 
 
 def test_select_sigma_lapl200(lapl200_runs):
-    """The a-posteriori shift from the coefficient history reproduces Table 1's sigma* = 4.00."""
-    sh = lapl200_runs["pcgsh"]
+    """The a-posteriori shift from the coefficient history of an unshifted p-CG pilot run
+    (Section 5.1; 300 iterations, before that run breaks down near 450) reproduces Table 1's
+    sigma* = 4.00, and so does the p-CG-sh(4) history of 500 iterations."""
+    P, b = S.lapl200()
+    pil = oracle.pcg_sh(P, b, sigma=0.0, maxit=300, log_every=0)
     grid = np.linspace(0.5, 8.0, 16)
-    s, vals = PS.select_sigma(sh.alpha, sh.beta, 499, grid)
+    s, vals = PS.select_sigma(pil.alpha, pil.beta, 299, grid)
     assert s == 4.0
     assert vals[0] > 5 * vals.min()
     # beyond the top of the spectrum (lambda_max < 8) psi explodes: the cliff the rule avoids
-    assert PS.psi(sh.alpha, sh.beta, 499, 9.0) > 1e6 * vals.min()
+    assert PS.psi(pil.alpha, pil.beta, 299, 9.0) > 1e6 * vals.min()
+    sh = lapl200_runs["pcgsh"]
+    assert PS.select_sigma(sh.alpha, sh.beta, 499, grid)[0] == 4.0
+
+
+def test_select_sigma_second_case_lapl3d():
+    """A second case for the selection rule: the 32^3 Laplacian with a manufactured solution.
+    The shift chosen from a 100-iteration unshifted pilot brings p-CG-sh to CG's attainable
+    accuracy, while unshifted p-CG stalls at least 100 times above it (Table 1's pattern)."""
+    P, b, _ = S.poisson3d_manufactured(32)
+    bn = np.linalg.norm(b)
+    pil = oracle.pcg_sh(P, b, sigma=0.0, maxit=100, log_every=0)
+    s, vals = PS.select_sigma(pil.alpha, pil.beta, 99, np.linspace(0.5, 12.0, 24))
+    assert 0.5 <= s <= 6.0
+    cg = oracle.cg(P, b, maxit=1500, log_every=100)
+    p0 = oracle.pcg_sh(P, b, sigma=0.0, maxit=1500, log_every=100)
+    ps = oracle.pcg_sh(P, b, sigma=s, maxit=1500, log_every=100)
+    assert ps.true[-1] / bn <= 10 * cg.true[-1] / bn
+    assert np.nanmin(p0.true) / bn >= 100 * cg.true[-1] / bn
 
 
 # ---------------------------------------------------------------- Algorithm 4 (variable shift)
@@ -397,3 +418,110 @@ def test_varsh_constant_shift_is_algorithm3_bitwise():
     r3 = oracle.pcg_sh(P, b, sigma=4.0, maxit=80)
     r4 = oracle.pcg_varsh(P, b, [4.0] * 81, maxit=80)
     assert np.array_equal(r3.alpha, r4.alpha) and np.array_equal(r3.x, r4.x)
+
+
+# ---------------------------------------------------------------- gaps g, h, j (Section 3.1)
+
+@pytest.mark.parametrize("sigma,precond", [(F(0), False), (F(3, 2), False), (F(4), True)])
+def test_exact_gaps_vanish(sigma, precond):
+    """In exact arithmetic the recurrences of Algorithm 3 keep every auxiliary vector equal to
+    its definition (Eq. (pipe_cg_shift_aux)): the gaps f, g, h, j are exactly zero."""
+    n = 6
+    A = spd_int(n, 11)
+    Af = [[F(int(v)) for v in row] for row in A]
+    b = [F(int(v)) for v in np.random.default_rng(12).integers(-4, 5, n)]
+    minv = [F(1, int(A[i, i])) for i in range(n)] if precond else None
+    log = []
+    EX.pcg_sh(Af, b, sigma=sigma, iters=n, minv=minv, gap_log=log)
+    assert len(log) >= 3
+    for e in log:
+        assert e["f"] == 0 and e["g"] == 0 and e["h"] == 0 and e["j"] == 0
+
+
+def gap_states(sigma, ks=(120, 121, 122)):
+    """lapl200 with shift sigma: the exported vectors after iterations ks, and a run of
+    ks[-1] iterations with the gaps logged at every iteration."""
+    P, b = S.lapl200()
+    st = {k: oracle.pcg_sh(P, b, sigma=sigma, maxit=k, log_every=1, want_state=True).state for k in ks}
+    run = oracle.pcg_sh(P, b, sigma=sigma, maxit=ks[-1], log_every=1, gaps=True)
+    return P, b, [st[k] for k in ks], run
+
+
+@pytest.fixture(scope="module")
+def gaps_sigma0():
+    return gap_states(0.0)
+
+
+@pytest.fixture(scope="module")
+def gaps_sigma4():
+    return gap_states(4.0)
+
+
+def test_logged_gaps_match_their_definitions(gaps_sigma0, gaps_sigma4):
+    """||g||, ||h||, ||j|| as logged by the oracle against the definitions recomputed with a
+    scipy operator from the exported vectors (iteration 121's p, t, s, q, z; the final u, r,
+    w).  Unshifted p-CG has amplified g and h far above rounding (agreement to 1e-5); the
+    other gaps sit at rounding level, where the recomputation's own rounding of A v is a
+    few percent of them."""
+    for (P, b, (_, _, s), run), sigma, tg, th in ((gaps_sigma0, 0.0, 1e-5, 1e-5), (gaps_sigma4, 4.0, 2e-2, 2e-2)):
+        A = scipy_of(P)
+        g = A @ s["p"] - sigma * s["t"] - s["s"]
+        j = A @ s["q"] - s["z"]
+        h = A @ s["u"] - sigma * s["r"] - s["w"]
+        assert abs(np.linalg.norm(g) - run.gap_g[121]) <= tg * run.gap_g[121], sigma
+        assert abs(np.linalg.norm(h) - run.gap_h[122]) <= th * run.gap_h[122], sigma
+        assert abs(np.linalg.norm(j) - run.gap_j[121]) <= 2e-2 * run.gap_j[121], sigma
+    assert gaps_sigma0[3].gap_g[121] > 100 * gaps_sigma4[3].gap_g[121]     # amplified without the shift
+
+
+def test_gap_recurrences_of_section_3(gaps_sigma0, gaps_sigma4):
+    """The coupled gap recurrences of Section 3.1 on the vectors of consecutive iterations
+    (i = 120, 121): each right-hand side reproduces the left-hand side to a few percent of
+    the terms it couples, so the local rounding terms are small next to them.
+      recur_f: f_{i+1} = f_i - alpha_i g_i + local      (sigma = 0, where g is amplified)
+      recur_g: g_i = h_i + beta_i g_{i-1} + local       (sigma = 0 and 4)
+      recur_h: h_{i+1} = h_i - alpha_i j_i - alpha_i sigma g_i + local   (sigma = 4)"""
+    def parts(data, sigma):
+        P, b, (s0, s1, s2), run = data
+        A = scipy_of(P)
+
+        def f_of(s):
+            return (b - A @ s["x"]) - s["r"]
+
+        def h_of(s):
+            return A @ s["u"] - sigma * s["r"] - s["w"]
+
+        def g_of(s):
+            return A @ s["p"] - sigma * s["t"] - s["s"]
+
+        return f_of, h_of, g_of, A, (s0, s1, s2), run
+
+    n = np.linalg.norm
+    # sigma = 0
+    f_of, h_of, g_of, A, (s0, s1, s2), run = parts(gaps_sigma0, 0.0)
+    a1, b2 = run.alpha[120], run.beta[121]
+    g1, g2 = g_of(s1), g_of(s2)
+    assert n(f_of(s1) - (f_of(s0) - a1 * g1)) <= 0.05 * n(a1 * g1)
+    assert n(g2 - (h_of(s1) + b2 * g1)) <= 0.05 * (n(h_of(s1)) + n(b2 * g1))
+    # sigma = 4: the shift terms of recur_g and recur_h
+    f_of, h_of, g_of, A, (s0, s1, s2), run = parts(gaps_sigma4, 4.0)
+    a1, b2 = run.alpha[120], run.beta[121]
+    g1, g2 = g_of(s1), g_of(s2)
+    j1 = A @ s1["q"] - s1["z"]
+    assert n(g2 - (h_of(s1) + b2 * g1)) <= 0.1 * (n(h_of(s1)) + n(b2 * g1))
+    dh = h_of(s1) - h_of(s0)
+    assert n(dh - (-a1 * j1 - a1 * 4.0 * g1)) <= 0.1 * n(dh)
+    assert n(a1 * 4.0 * g1) > 0.5 * n(dh)            # the shift's coupling term carries the change
+
+
+def test_shift_keeps_the_auxiliary_gaps_small():
+    """lapl200, 500 iterations: unshifted p-CG amplifies the gap g (Section 3: the propagation
+    matrices' norms grow); the shift sigma = 4 of Table 1 keeps every logged gap near the
+    rounding level of its first iterations."""
+    P, b = S.lapl200()
+    p0 = oracle.pcg_sh(P, b, sigma=0.0, maxit=500, log_every=25, gaps=True)
+    p4 = oracle.pcg_sh(P, b, sigma=4.0, maxit=500, log_every=25, gaps=True)
+    assert np.nanmax(p0.gap_g) > 50 * np.nanmax(p4.gap_g)
+    assert np.nanmax(p0.gap) > 1e3 * np.nanmax(p4.gap)
+    for v in (p4.gap_g, p4.gap_h, p4.gap_j):
+        assert np.nanmax(v) < 1e-12
