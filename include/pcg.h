@@ -391,6 +391,67 @@ pcg_status pcg_convert_check(const double *d_in, float *f_out, const float *f_in
 pcg_status pcg_true_residual_noalloc(const pcg_matrix *A, const double *b, const double *x, const double *r,
                                      double *norms, void *stream);
 
+/* ---- one rank's share of a single system on several GPUs (Section 1; Section 5.2's MPI
+ * setting).  The global grid is the 3D 7-point constant-coefficient Laplacian of
+ * pcg_matrix (PCG_STENCIL7_3D, no coefficients), cut into slabs of whole z planes, one per
+ * rank.  The SpMV of a rank needs its neighbours' boundary planes (one plane below, one
+ * above); the dot products need one global reduction of two scalars per iteration.
+ * A slab runs the phases of Algorithm 3 as kernels on its stream; the caller moves the
+ * halo planes and reduces the dots (torch.distributed / NCCL, or copies between slabs in
+ * one process) between the phases, so that the reduction overlaps the SpMV:
+ *
+ *   pcg_slab_start(local)           r = b, x = z = s = p = 0; local (b, b)
+ *   reduce(local -> global); pcg_slab_set_bnorm(global)
+ *   halo <- neighbours' boundary planes of r; pcg_slab_spmv(R, W, all planes)
+ *   pcg_slab_w0(local)              w_0 = A r_0 - sigma r_0; local (r, r), (w_0, r)
+ *   for i = 0, 1, ...:
+ *     start reduce(local -> global); start halo <- neighbours' boundary planes of w
+ *     pcg_slab_spmv(W, N, interior planes); wait halo; pcg_slab_spmv(W, N, boundary planes)
+ *     wait reduce; pcg_slab_scalars(global, i == 0)      alpha_i, beta_i, stop tests
+ *     pcg_slab_update(local)       z, s, p, x, r, w (in place); local (r, r), (w, r)
+ *
+ * All vectors are caller-owned device arrays of nx*ny*nz_local doubles (8-byte aligned;
+ * 16-byte aligned with an even nx for two unknowns per thread), the halos nx*ny doubles;
+ * the dots are device arrays of 2 doubles.  Plane k of a vector starts at k*nx*ny. */
+typedef struct pcg_slab pcg_slab;
+typedef struct {
+  double *x, *r, *w, *z, *s, *p, *n;    /* n receives A w (or A x for the true residual) */
+  const double *b;
+  const double *halo_below, *halo_above;   /* the neighbour's plane next to this slab */
+} pcg_slab_vectors;
+#define PCG_SLAB_X 0
+#define PCG_SLAB_R 1
+#define PCG_SLAB_W 2
+#define PCG_SLAB_N 3
+#define PCG_SLAB_ALL_PLANES 0
+#define PCG_SLAB_INTERIOR_PLANES 1   /* planes 1 .. nz_local - 2: no halo needed */
+#define PCG_SLAB_BOUNDARY_PLANES 2   /* planes 0 and nz_local - 1 */
+
+/* A slab of nz_local planes of an nx x ny grid; has_below / has_above: a neighbour slab
+ * exists on that side (else the Dirichlet boundary of the global grid); maxit: the most
+ * iterations (histories of maxit + 1 entries are kept on the device).
+ * Errors: PCG_EINVAL (sizes, NULL or misaligned vectors), PCG_ENOMEM, PCG_ECUDA. */
+pcg_status pcg_slab_create(int64_t nx, int64_t ny, int64_t nz_local, int32_t has_below, int32_t has_above,
+                           const pcg_slab_vectors *v, int32_t maxit, pcg_slab **out);
+pcg_status pcg_slab_set_stream(pcg_slab *slab, void *stream);
+/* sigma >= 0: the shift; tol: stop once ||r_i|| <= tol ||b|| (0: run maxit iterations). */
+pcg_status pcg_slab_start(pcg_slab *slab, double sigma, double tol, double *local_dots);
+pcg_status pcg_slab_set_bnorm(pcg_slab *slab, const double *global_dots);
+/* dst = A src on the given planes (src, dst: PCG_SLAB_*; dst is W or N and differs from src). */
+pcg_status pcg_slab_spmv(pcg_slab *slab, int32_t src, int32_t dst, int32_t planes);
+pcg_status pcg_slab_w0(pcg_slab *slab, double *local_dots);
+pcg_status pcg_slab_scalars(pcg_slab *slab, const double *global_dots, int32_t first);
+pcg_status pcg_slab_update(pcg_slab *slab, double *local_dots);
+/* After pcg_slab_spmv(X, N, ...): local ||b - A x||^2 and ||(b - A x) - r||^2. */
+pcg_status pcg_slab_true_residual(pcg_slab *slab, double *local_sums);
+/* Waits for the slab's stream; status: PCG_PENDING while running, then PCG_OK /
+ * PCG_ENOTCONV (maxit) / PCG_EBREAKDOWN; iter: the last iteration's index; bnorm: ||b||. */
+pcg_status pcg_slab_state(pcg_slab *slab, int32_t *iter, int32_t *status, double *bnorm);
+/* The first k entries of alpha_i, beta_i and ||r_i|| (host arrays, any may be NULL). */
+pcg_status pcg_slab_history(pcg_slab *slab, int32_t k, double *alpha, double *beta, double *rec);
+const char *pcg_slab_last_error(const pcg_slab *slab);
+void pcg_slab_destroy(pcg_slab *slab);
+
 /* Variable shift, Algorithm 4 (Section 4.1): later PCG_SPCG solves on this context use
  * shifts[0] = sigma_{-1} (the shift of w_0) and shifts[k + 1] = sigma_k for iteration k,
  * with the correction terms of Algorithm 4 in s, q, z and w; the sigma argument of the
