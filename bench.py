@@ -481,12 +481,72 @@ def run_reference(args):
     return 0
 
 
+def run_sharded(args, rank: int, world: int, local: int) -> int:
+    """One system split over the ranks (weak scaling): the 256 x 256 x (256 N) Laplacian,
+    a 256^3 z-slab per GPU, the phases of Algorithm 3 with NCCL halo exchanges and one
+    2-scalar all-reduce per iteration (sharded.solve_rank).  `value` is in 256^3
+    slab-iterations per second summed over the ranks, the unit of the single-GPU line."""
+    import torch
+    import synthetic as S
+    from paper_1706_05988_gb300 import sharded as SH
+    nx = ny = N_SIDE
+    nz = N_SIDE * world
+    k0, k1 = SH.z_slabs(nz, world)[rank]
+    b_local = S.poisson3d_manufactured_slab(nx, ny, nz, k0, k1)
+    slab = SH.CudaSlab(nx, ny, k0, k1, nz, b_local, ITERS_PER_STEP)
+    comm = SH.DistComm(rank, world)
+
+    def step():
+        return SH.solve_rank(slab, comm, SIGMA, 0.0, ITERS_PER_STEP, check_every=0)
+
+    for _ in range(args.warmup):
+        res = step()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            res = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    ms_max = max_over_ranks(world, ev0.elapsed_time(ev1))
+    value = job_throughput(ITERS_PER_STEP * args.steps, world, ms_max)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"one 7-point Laplacian of {nx}x{ny}x{nz} (x* dyadic U[-1,1] seed 0, b = A x*, "
+                                       f"x0 = 0) in {world} z-slabs of {N_SIDE}^3, shifted p-CG sigma={SIGMA}, "
+                                       f"{ITERS_PER_STEP} iterations per step; value in {N_SIDE}^3 slab-iterations/s",
+                           "n_global": nx * ny * nz, "parallelism": f"z-slabs x{world}",
+                           "l2_flush": "not needed: the slab's vectors exceed L2"},
+                "sharded": {"iters_per_s_global_system": ITERS_PER_STEP * args.steps / (ms_max / 1e3),
+                            "final_true_relres": res["true_relres"], "iters": res["iters"]},
+                "e2e": None, "gpu_launches": None, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    slab.close()
+    import torch.distributed as dist
+    dist.destroy_process_group()
+    return 0
+
+
 def run_ours(args):
     import numpy as np
     import torch
 
     rank, world, local = dist_setup(args.gpus)
     torch.cuda.set_device(local)
+    if args.sharded and world > 1:
+        import paper_1706_05988_gb300 as pkg
+        if local == 0:
+            pkg.build.build()
+        barrier(world)
+        if local != 0:
+            pkg.build.build()
+        return run_sharded(args, rank, world, local)
     import paper_1706_05988_gb300 as pkg
     from paper_1706_05988_gb300 import pcg as C
     import synthetic as S
@@ -752,6 +812,9 @@ def main():
                     default=None,
                     help="run one short solve of --size^3 for an ncu capture, then exit")
     ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--sharded", action="store_true",
+                    help="with N > 1 GPUs: one 256x256x(256N) system in z-slabs (halo exchange and an all-reduce "
+                         "per iteration) instead of N independent 256^3 systems")
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")

@@ -65,9 +65,10 @@ def uniform_pm1(seed: int, count: int, offset: int = 0) -> np.ndarray:
     return 2.0 * uniform01(seed, count, offset) - 1.0
 
 
-def dyadic_uniform_pm1(seed: int, count: int, bits: int = DYADIC_BITS) -> np.ndarray:
-    """U[-1,1) rounded down to the grid 2^-bits (exactly representable, |v| <= 1)."""
-    u = splitmix64(seed, count) >> np.uint64(64 - (bits + 1))          # integer in [0, 2^(bits+1))
+def dyadic_uniform_pm1(seed: int, count: int, bits: int = DYADIC_BITS, offset: int = 0) -> np.ndarray:
+    """U[-1,1) rounded down to the grid 2^-bits (exactly representable, |v| <= 1); values
+    offset .. offset+count-1 of the stream."""
+    u = splitmix64(seed, count, offset) >> np.uint64(64 - (bits + 1))   # integer in [0, 2^(bits+1))
     return (u.astype(np.int64) - (1 << bits)).astype(np.float64) * (2.0 ** -bits)
 
 
@@ -444,6 +445,23 @@ def poisson3d_manufactured(n: int = 256, seed: int = 0):
     p = laplacian_3d(n)
     xs = dyadic_uniform_pm1(seed, p.n)
     return p, laplacian_rhs(p, xs), xs
+
+
+def poisson3d_manufactured_slab(nx: int, ny: int, nz: int, k0: int, k1: int, seed: int = 0) -> np.ndarray:
+    """b = A x* on planes [k0, k1) of the nx x ny x nz Laplacian with the dyadic x* of
+    seed (the values the whole-grid laplacian_rhs gives there, bit for bit: every term
+    is exact), computed from x* on those planes and one plane on each side."""
+    lo, hi = max(k0 - 1, 0), min(k1 + 1, nz)
+    plane = nx * ny
+    x = dyadic_uniform_pm1(seed, (hi - lo) * plane, offset=lo * plane).reshape(hi - lo, ny, nx)
+    b = 6.0 * x
+    b[1:] -= x[:-1]
+    b[:-1] -= x[1:]
+    b[:, 1:] -= x[:, :-1]
+    b[:, :-1] -= x[:, 1:]
+    b[:, :, 1:] -= x[:, :, :-1]
+    b[:, :, :-1] -= x[:, :, 1:]
+    return np.ascontiguousarray(b[k0 - lo:k0 - lo + (k1 - k0)].reshape(-1))
 
 
 def lapl200():

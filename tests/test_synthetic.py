@@ -37,3 +37,10 @@ def test_random_sdd_csr_on_gpu_matches_numpy():
     a = S.random_sdd_csr(300001, seed=11)        # assembled on the GPU
     b = S.random_sdd_csr_numpy(300001, seed=11)
     assert np.array_equal(a.row_ptr, b.row_ptr) and np.array_equal(a.col, b.col) and np.array_equal(a.val, b.val)
+
+
+def test_manufactured_slab_rhs_is_the_whole_grids():
+    """The slab-local b = A x* of a z-slab has the bits of the whole grid's b there."""
+    P, b, xs = S.poisson3d_manufactured(16)
+    for k0, k1 in ((0, 5), (5, 11), (11, 16), (0, 16), (7, 8)):
+        assert np.array_equal(S.poisson3d_manufactured_slab(16, 16, 16, k0, k1), b[k0 * 256:k1 * 256])
