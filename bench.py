@@ -39,7 +39,8 @@ FALLBACK_HBM_GBS = 6800.0
 # SHA-256 of the kernel source it was measured on; a changed kernel reports null.
 # k_spcg_iter<StencilOp<3, ST_LAP_FIXED, 2>> on 256^3: dram__bytes_read.sum + dram__bytes_write.sum of one launch
 # (a one-pass capture, profiles/spcg_iter_stencil7_256cubed_traffic.md), keyed by the source it was taken on
-NCU_TRAFFIC = {"db28dd47f9fa25b7": 1561.35e6, "e9be0f27e77e4297": 1561.47e6, "9a4ca33e0286f39c": 1561.25e6}
+NCU_TRAFFIC = {"db28dd47f9fa25b7": 1561.35e6, "e9be0f27e77e4297": 1561.47e6, "9a4ca33e0286f39c": 1561.25e6,
+               "a8b0005e527d5aff": 1561.77e6}
 
 
 def kernel_source_sha() -> str:
@@ -803,6 +804,37 @@ def profile_case(kind: str, n: int) -> int:
     return 0
 
 
+def compare_iter_forms(n: int) -> int:
+    """Event-timed A/B of the forms of the fused iteration on the n^3 Laplacian (1,000
+    iterations each, best of 3): the register sweep and the TMA-staged sweep (rings of 2
+    and 3 chunks), each with binary64 dots and with the dots on the FP32 pipe; prints one
+    JSON line of kernel ms per launch and algorithmic GB/s (96 B per unknown)."""
+    import torch
+    import synthetic as S
+    import paper_1706_05988_gb300 as pkg
+    from paper_1706_05988_gb300 import pcg as C
+    pkg.build.build()
+    P, b, _ = S.poisson3d_manufactured(n)
+    bd = torch.from_numpy(b).cuda()
+    out = {"workload": f"{n}^3 Laplacian, shifted p-CG sigma={SIGMA}, 1000 iterations"}
+    for dots, fl in (("fp64_dots", 0), ("split32_dots", C.PCG_DOTS_SPLIT32)):
+        with pkg.Solver(P, flags=C.PCG_PROFILE | fl) as s:
+            for stages in (0, 2, 3):
+                C.pcg_set_param(s.ctx, C.PCG_PARAM_ITER_STAGES, float(stages))
+                got = int(C.pcg_get_param(s.ctx, C.PCG_PARAM_ITER_STAGES))
+                s.solve(bd, method="spcg", sigma=SIGMA, maxit=50, device=True)
+                best = None
+                for _ in range(3):
+                    C.pcg_kernel_stats_reset(s.ctx)
+                    s.solve(bd, method="spcg", sigma=SIGMA, maxit=1000, device=True)
+                    _, il, ims = C.pcg_kernel_stats(s.ctx)
+                    best = ims / il if best is None else min(best, ims / il)
+                key = f"{'register' if got == 0 else f'staged{got}'}_{dots}"
+                out[key] = {"kernel_ms": best, "algorithmic_gbs": BYTES_PER_DOF * P.n / best / 1e6}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--profile-case", choices=["spcg", "spcg-split32", "spcg-staged", "spcg-staged-split32",
@@ -811,6 +843,8 @@ def main():
                                                "batch-large-mixed-jacobi", "batch-large-mixed-jacobi-occ4"],
                     default=None,
                     help="run one short solve of --size^3 for an ncu capture, then exit")
+    ap.add_argument("--compare-iter-forms", action="store_true",
+                    help="time the register and TMA-staged sweeps with both dot forms on --size^3, then exit")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--sharded", action="store_true",
                     help="with N > 1 GPUs: one 256x256x(256N) system in z-slabs (halo exchange and an all-reduce "
@@ -838,6 +872,8 @@ def main():
     args = ap.parse_args()
     if args.profile_case:
         return profile_case(args.profile_case, args.size)
+    if args.compare_iter_forms:
+        return compare_iter_forms(args.size)
     globals()["N_SIDE"] = args.size
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
