@@ -70,6 +70,7 @@ __global__ void __launch_bounds__(kBlock, OCC) k_batch(const BatchSys* __restric
     BatchOut res;
     solve_one<F, MODE>(cl, part, slot, d, V, prm, res);
     if (rank == 0 && threadIdx.x == 0) out[k] = res;
+    scalar_log_flush(sys[k].log);
   }
 }
 

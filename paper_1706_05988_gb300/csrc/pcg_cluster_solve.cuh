@@ -36,16 +36,43 @@ struct BatchSys {
 // the inner iterations across restarts (a restart starts again from beta = 0).
 constexpr int kScalarLog = 32;
 
+// The values are collected in the block's shared memory while the solve runs (a constant
+// address, and the cluster rank read from its special register: no register stays live
+// for them across the iteration loop); the caller copies them to the system's log after
+// the solve (scalar_log_flush), reading the log's address from global memory then.
+__device__ __forceinline__ double* scalar_log_smem() {
+  __shared__ double s[2 * kScalarLog];
+  return s;
+}
+
+__device__ __forceinline__ bool scalar_log_owner() {
+  return threadIdx.x == 0 && cg::this_cluster().block_rank() == 0;
+}
+
 __device__ __forceinline__ void scalar_log_clear(const BatchSys& d, unsigned rank) {
-  if (d.log != nullptr && rank == 0 && threadIdx.x == 0) {
-    for (int i = 0; i < 2 * kScalarLog; ++i) d.log[i] = __longlong_as_double(0x7FF8000000000000LL);
+  (void)d;
+  (void)rank;
+  if (scalar_log_owner()) {
+    double* s = scalar_log_smem();
+    for (int i = 0; i < 2 * kScalarLog; ++i) s[i] = __longlong_as_double(0x7FF8000000000000LL);
   }
 }
 
 __device__ __forceinline__ void scalar_log(const BatchSys& d, unsigned rank, int i, double alpha, double beta) {
-  if (d.log != nullptr && rank == 0 && threadIdx.x == 0 && i >= 0 && i < kScalarLog) {
-    d.log[i] = alpha;
-    d.log[kScalarLog + i] = beta;
+  (void)d;
+  (void)rank;
+  if (i < kScalarLog && scalar_log_owner()) {
+    double* s = scalar_log_smem();
+    s[i] = alpha;
+    s[kScalarLog + i] = beta;
+  }
+}
+
+// Copies the last solve's values to `log` (nullptr: none); thread 0 of the cluster's first block.
+__device__ __forceinline__ void scalar_log_flush(double* log) {
+  if (log != nullptr && scalar_log_owner()) {
+    const double* s = scalar_log_smem();
+    for (int i = 0; i < 2 * kScalarLog; ++i) log[i] = s[i];
   }
 }
 

@@ -177,7 +177,8 @@ __global__ void __launch_bounds__(kBlock, PCG_SERVER_MIN_BLOCKS) k_server(Server
       case 3: solve_item<3, WIDE>(cl, part, slot, w, res); break;
       default: solve_item<4, WIDE>(cl, part, slot, w, res); break;
     }
-    cl.sync();   // every block's writes to x are done before the flag is raised
+    scalar_log_flush(s_item.sys.log);
+    cl.sync();   // every block's writes to x (and the scalar log) are done before the flag is raised
     if (rank == 0 && threadIdx.x == 0) {
       results[task % cap] = res;
       __threadfence_system();
