@@ -765,8 +765,11 @@ def profile_case(kind: str, n: int) -> int:
         bs = [S.normal(1000 + i, P.n) for i, P in enumerate(probs)]
         prec = C.PCG_MIXED_IR if kind.startswith("batch-large-mixed-jacobi") else C.PCG_FP64
         with pkg.Batch(probs, flags=pkg.PCG_JACOBI, precision=prec) as bt:
-            bt.set_cluster(2)
-            if kind.endswith("-occ4"):
+            # cluster size 2 (the shape the autotuner takes for the large class of the
+            # 512-system batch); -c16: 16 blocks per system and the 4-block variant, the
+            # fastest shape for these 64 systems alone
+            bt.set_cluster(16 if kind.endswith("-c16") else 2)
+            if kind.endswith("-occ4") or kind.endswith("-c16"):
                 bt.set_class_occupancy(2, 4)      # the 64-register kernel variant, forced
             for _ in range(2):
                 _, it, st, _ = bt.solve(bs, [1.0] * len(probs), tol=1e-8, maxit=500)
@@ -840,7 +843,8 @@ def main():
     ap.add_argument("--profile-case", choices=["spcg", "spcg-split32", "spcg-staged", "spcg-staged-split32",
                                                "jacobi-fp64", "jacobi-mixed", "batch-fp64",
                                                "batch-mixed-jacobi", "batch-large-fp64-jacobi",
-                                               "batch-large-mixed-jacobi", "batch-large-mixed-jacobi-occ4"],
+                                               "batch-large-mixed-jacobi", "batch-large-mixed-jacobi-occ4", "batch-large-mixed-jacobi-c16",
+                                               "batch-large-fp64-jacobi-c16"],
                     default=None,
                     help="run one short solve of --size^3 for an ncu capture, then exit")
     ap.add_argument("--compare-iter-forms", action="store_true",
