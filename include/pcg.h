@@ -501,6 +501,16 @@ pcg_status pcg_get_param(const pcg_ctx *ctx, int32_t param, double *value);
 pcg_status pcg_kernel_stats(pcg_ctx *ctx, int64_t *launches_total, int64_t *iter_launches, double *iter_ms);
 pcg_status pcg_kernel_stats_reset(pcg_ctx *ctx);
 
+/* Index checks of the checked build (libpcg_checked.so, compiled with -DPCG_CHECKED; the
+ * paper has no counterpart: a stand-in for a memory checker).  The kernels of that build
+ * check every index they turn into an address (stencil neighbours and coefficients, CSR
+ * rows and columns, bulk copies, halo planes); a failed check records its code and skips
+ * the access.  This call waits for the device, reports the first recorded code since the
+ * last call in *code (0: none; the codes are listed in csrc/pcg_check.cuh) and clears it;
+ * *checked (may be NULL) is 1 in the checked build, 0 in others (where *code is always 0).
+ * Errors: PCG_EINVAL (code NULL), PCG_ECUDA. */
+pcg_status pcg_check_status(uint32_t *code, int32_t *checked);
+
 /* Version string of the library build. */
 const char *pcg_version(void);
 

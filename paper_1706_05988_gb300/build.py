@@ -12,6 +12,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpcg.so")
+BUILD_CHECKED = os.path.join(PKG, "_build_checked")
+LIB_CHECKED = os.path.join(PKG, "libpcg_checked.so")   # -DPCG_CHECKED: index checks in the kernels
 HEADER = os.path.join(ROOT, "include", "pcg.h")
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
@@ -31,24 +33,28 @@ def _deps() -> list[str]:
     return sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + [HEADER]
 
 
-def needs_build() -> bool:
-    if not os.path.exists(LIB):
+def needs_build(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:
-    """Compile every CUDA source and link libpcg.so next to this file."""
-    if not force and not needs_build():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None,
+          checked: bool = False) -> str:
+    """Compile every CUDA source and link libpcg.so next to this file (checked=True: the
+    same sources with -DPCG_CHECKED into libpcg_checked.so, see pcg_check_status)."""
+    LIBX = LIB_CHECKED if checked else LIB
+    BUILDX = BUILD_CHECKED if checked else BUILD
+    if not force and not needs_build(LIBX):
+        return LIBX
+    os.makedirs(BUILDX, exist_ok=True)
     nvcc = _nvcc()
-    flags = NVCC_FLAGS + list(extra_flags or [])
+    flags = NVCC_FLAGS + (["-DPCG_CHECKED"] if checked else []) + list(extra_flags or [])
     procs = []
     objs = []
     for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(BUILDX, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         cmd = [nvcc, *flags, "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj]
         if verbose:
@@ -63,11 +69,11 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
             print(out.decode(errors="replace"), file=sys.stderr)
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = LIBX + f".tmp{os.getpid()}"
     subprocess.check_call([nvcc, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", tmp, *objs,
                            "-lpthread"])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, LIBX)
+    return LIBX
 
 
 if __name__ == "__main__":

@@ -186,9 +186,39 @@ Launch launch_of(pcg_ctx* c, int kind) { return Launch{c->grid[kind], kBlockThre
 
 }  // namespace
 
+namespace pcgk {
+// Readers of the checked build's per-translation-unit failure words (pcg_check.cuh),
+// registered by static initialisers when the library loads.
+std::vector<unsigned (*)(bool)>& check_readers() {
+  static std::vector<unsigned (*)(bool)> readers;
+  return readers;
+}
+void register_check_reader(unsigned (*reader)(bool)) { check_readers().push_back(reader); }
+}  // namespace pcgk
+
 extern "C" {
 
 const char* pcg_version(void) { return kVersion; }
+
+pcg_status pcg_check_status(uint32_t* code, int32_t* checked) {
+  if (!code) return PCG_EINVAL;
+#ifdef PCG_CHECKED
+  if (checked) *checked = 1;
+#else
+  if (checked) *checked = 0;
+#endif
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return PCG_ECUDA;
+  }
+  unsigned first = 0;
+  for (auto reader : pcgk::check_readers()) {
+    const unsigned v = reader(true);
+    if (first == 0) first = v;
+  }
+  *code = first;
+  return PCG_OK;
+}
 
 const char* pcg_last_error(const pcg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 

@@ -14,6 +14,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "pcg_check.cuh"
 #include "pcg_ffdot.cuh"
 #include "pcg_tma.cuh"
 #include "pcg_fixedsum.cuh"
@@ -95,16 +96,18 @@ struct StencilOp {
     const bool has_ym = j > 0, has_yp = j + 1 < (unsigned)ny;
     const bool has_zm = DIM == 3 && k > 0, has_zp = DIM == 3 && k + 1 < (unsigned)nz;
     double c[VEC], ym[VEC], yp[VEC], zm[VEC], zp[VEC];
-    ldg<VEC>(w + c0, c);
-    ldg_if<VEC>(has_ym, w + c0 - nx, ym);
-    ldg_if<VEC>(has_yp, w + c0 + nx, yp);
+    const unsigned un = (unsigned)n;
+    const bool in = pcg_check(c0 + VEC <= un, CHK_STENCIL_CENTRE);
+    ldg_if<VEC>(in, w + c0, c);
+    ldg_if<VEC>(has_ym && pcg_check(in && c0 >= (unsigned)nx, CHK_STENCIL_Y), w + c0 - nx, ym);
+    ldg_if<VEC>(has_yp && pcg_check(c0 + VEC + nx <= un, CHK_STENCIL_Y), w + c0 + nx, yp);
     if (DIM == 3) {
-      ldg_if<VEC>(has_zm, w + c0 - nxny, zm);
-      ldg_if<VEC>(has_zp, w + c0 + nxny, zp);
+      ldg_if<VEC>(has_zm && pcg_check(in && c0 >= (unsigned)nxny, CHK_STENCIL_Z), w + c0 - nxny, zm);
+      ldg_if<VEC>(has_zp && pcg_check(c0 + VEC + nxny <= un, CHK_STENCIL_Z), w + c0 + nxny, zp);
     }
     // x neighbours of the unit: left of the first, right of the last unknown
-    const double xl = i0 > 0 ? __ldg(w + c0 - 1) : 0.0;
-    const double xr = i0 + VEC < (unsigned)nx ? __ldg(w + c0 + VEC) : 0.0;
+    const double xl = i0 > 0 && pcg_check(in && c0 >= 1, CHK_STENCIL_X) ? __ldg(w + c0 - 1) : 0.0;
+    const double xr = i0 + VEC < (unsigned)nx && pcg_check(c0 + VEC < un, CHK_STENCIL_X) ? __ldg(w + c0 + VEC) : 0.0;
     row(q, c, xl, xr, ym, yp, zm, zp, wc, aw);
   }
 
@@ -191,18 +194,19 @@ struct StencilOp {
         aw[e] = fma(C, c[e], -s);
       }
     } else {
-      const unsigned c0 = q.c0, i0 = q.i0;
+      const unsigned c0 = q.c0, i0 = q.i0, un = (unsigned)n;
       const bool has_yp = q.j + 1 < (unsigned)ny, has_zp = DIM == 3 && q.k + 1 < (unsigned)nz;
+      const bool in = pcg_check(c0 + VEC <= un, CHK_COEFF);
       double d[VEC], fx[VEC], fy[VEC], fyp[VEC], fz[VEC], fzp[VEC];
-      ldg<VEC>(diag + c0, d);
-      ldg<VEC>(ax + c0, fx);
-      ldg<VEC>(ay + c0, fy);
-      ldg_if<VEC>(has_yp, ay + c0 + nx, fyp);
+      ldg_if<VEC>(in, diag + c0, d);
+      ldg_if<VEC>(in, ax + c0, fx);
+      ldg_if<VEC>(in, ay + c0, fy);
+      ldg_if<VEC>(has_yp && pcg_check(c0 + VEC + nx <= un, CHK_COEFF), ay + c0 + nx, fyp);
       if (DIM == 3) {
-        ldg<VEC>(az + c0, fz);
-        ldg_if<VEC>(has_zp, az + c0 + nxny, fzp);
+        ldg_if<VEC>(in, az + c0, fz);
+        ldg_if<VEC>(has_zp && pcg_check(c0 + VEC + nxny <= un, CHK_COEFF), az + c0 + nxny, fzp);
       }
-      const double fxr = i0 + VEC < (unsigned)nx ? __ldg(ax + c0 + VEC) : 0.0;
+      const double fxr = i0 + VEC < (unsigned)nx && pcg_check(c0 + VEC < un, CHK_COEFF) ? __ldg(ax + c0 + VEC) : 0.0;
 #pragma unroll
       for (int e = 0; e < VEC; ++e) {
         const double fxp = e == VEC - 1 ? fxr : fx[e + 1];
@@ -286,11 +290,19 @@ struct CsrOp {
   __device__ __forceinline__ void apply(const double* __restrict__ w, const Cursor& q, double (&wc)[1],
                                         double (&aw)[1]) const {
     const int u = (int)q.c0;
-    const int beg = __ldg(row_ptr + u), end = __ldg(row_ptr + u + 1);
+    const bool in = pcg_check(u >= 0 && u < n, CHK_CSR_ROW);
+    const int beg = in ? __ldg(row_ptr + u) : 0;
+    int end = in ? __ldg(row_ptr + u + 1) : 0;
+#ifdef PCG_CHECKED
+    if (!pcg_check(beg >= 0 && beg <= end && end <= __ldg(row_ptr + n), CHK_CSR_ROW)) end = beg;
+#endif
     double a = 0.0;
-    for (int k = beg; k < end; ++k) a = fma(__ldg(val + k), __ldg(w + __ldg(col + k)), a);
+    for (int k = beg; k < end; ++k) {
+      const int c = __ldg(col + k);
+      if (pcg_check(c >= 0 && c < n, CHK_CSR_COL)) a = fma(__ldg(val + k), __ldg(w + c), a);
+    }
     aw[0] = a;
-    wc[0] = __ldg(w + u);
+    wc[0] = in ? __ldg(w + u) : 0.0;
   }
 #endif
 };
@@ -748,6 +760,16 @@ __global__ void __launch_bounds__(kBlock, PCG_TMA_MIN_BLOCKS) k_spcg_iter_tma(Op
       if (zlo_hi > zlo_lo) tx += (unsigned)(zlo_hi - zlo_lo) * 8u;
       if (zhi_hi > zhi_lo) tx += (unsigned)(zhi_hi - zhi_lo) * 8u;
     }
+#ifdef PCG_CHECKED
+    // every copy inside [0, n) with 16-byte sizes and addresses; a failing chunk is not
+    // copied at all (its wait then runs out and the solve stops as timed out)
+    auto ok16 = [](long long lo, long long hi) { return lo >= 0 && hi >= lo && ((hi - lo) & 1) == 0 && (lo & 1) == 0; };
+    if (!pcg_check(c0 >= 0 && c0 + CH <= (long long)nc && ok16(clo, chi) && chi <= (long long)nc &&
+                       (DIM != 3 || ((zlo_hi <= zlo_lo || ok16(zlo_lo, zlo_hi)) &&
+                                     (zhi_hi <= zhi_lo || (ok16(zhi_lo, zhi_hi) && zhi_hi <= (long long)nc)))),
+                   CHK_BULK_COPY))
+      return;
+#endif
     mbar_arrive_expect_tx(&full[sl], tx);
     bulk_g2s(dst + 0 * CH, v.z + c0, CHB, &full[sl], pol);
     bulk_g2s(dst + 1 * CH, v.s + c0, CHB, &full[sl], pol);

@@ -59,12 +59,15 @@ __global__ void __launch_bounds__(kBlock) k_slab_spmv(SlabGeom g, const double* 
     if (k > 0) {
       Op::template ldg<VEC>(src + c0 - g.nxny, zm);
     } else {
-      Op::template ldg_if<VEC>(g.has_lo != 0, halo_lo + c0, zm);
+      Op::template ldg_if<VEC>(g.has_lo != 0 && pcg_check(c0 + VEC <= (unsigned)g.nxny, CHK_SLAB_HALO), halo_lo + c0,
+                               zm);
     }
     if (k + 1 < (unsigned)g.nzl) {
       Op::template ldg<VEC>(src + c0 + g.nxny, zp);
     } else {
-      Op::template ldg_if<VEC>(g.has_hi != 0, halo_hi + (c0 - (unsigned)((g.nzl - 1) * g.nxny)), zp);
+      const unsigned hc = c0 - (unsigned)((g.nzl - 1) * g.nxny);
+      Op::template ldg_if<VEC>(g.has_hi != 0 && pcg_check(hc + VEC <= (unsigned)g.nxny, CHK_SLAB_HALO),
+                               halo_hi + hc, zp);
     }
     const double xl = i0 > 0 ? __ldg(src + c0 - 1) : 0.0;
     const double xr = i0 + VEC < (unsigned)g.nx ? __ldg(src + c0 + VEC) : 0.0;

@@ -14,7 +14,9 @@ from typing import Optional
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libpcg.so")
+# PCG_LIBRARY selects another build of the same C ABI (libpcg_checked.so, the index-checked
+# build); it must exist -- there is no fallback of any kind
+LIB_PATH = os.environ.get("PCG_LIBRARY") or os.path.join(_HERE, "libpcg.so")
 
 # pcg_status
 PCG_OK, PCG_EINVAL, PCG_ENOMEM, PCG_ECUDA, PCG_EBREAKDOWN, PCG_ENOTCONV, PCG_ETIMEOUT, PCG_PENDING, PCG_ENOTIMPL = range(9)
@@ -68,7 +70,7 @@ def lib() -> ctypes.CDLL:
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise RuntimeError(f"libpcg.so not found at {LIB_PATH}: run __graft_entry__.build() first "
+            raise RuntimeError(f"{os.path.basename(LIB_PATH)} not found at {LIB_PATH}: run __graft_entry__.build() first "
                                "(there is no CPU fallback)")
         L = ctypes.CDLL(LIB_PATH)
         vp, i32, i64, f64, st = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_int
@@ -113,6 +115,7 @@ def lib() -> ctypes.CDLL:
         L.pcg_true_residual_noalloc.argtypes = [ctypes.POINTER(pcg_matrix), vp, vp, vp, vp, vp]
         L.pcg_kernel_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(f64)]
         L.pcg_kernel_stats_reset.argtypes = [vp]
+        L.pcg_check_status.argtypes = [ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(i32)]
         L.pcg_version.argtypes = []
         L.pcg_version.restype = ctypes.c_char_p
         for f in ("pcg_create", "pcg_set_stream", "pcg_solve", "pcg_solve_device", "pcg_select_sigma", "pcg_psi",
@@ -123,7 +126,7 @@ def lib() -> ctypes.CDLL:
                   "pcg_server_create",
                   "pcg_batch_classes", "pcg_batch_set_class_cluster", "pcg_batch_set_class_occupancy",
                   "pcg_submit", "pcg_submit_ex", "pcg_poll", "pcg_server_stats",
-                  "pcg_kernel_stats", "pcg_kernel_stats_reset"):
+                  "pcg_kernel_stats", "pcg_kernel_stats_reset", "pcg_check_status"):
             getattr(L, f).restype = st
         _lib = L
     return _lib
@@ -241,6 +244,15 @@ def pcg_get_param(ctx, param: int) -> float:
     if s != PCG_OK:
         raise PcgError(s, "pcg_get_param")
     return v.value
+
+
+def pcg_check_status() -> tuple[int, bool]:
+    """(first failed index-check code since the last call or 0, whether this is the checked build)."""
+    code, checked = ctypes.c_uint32(), ctypes.c_int32()
+    s = lib().pcg_check_status(ctypes.byref(code), ctypes.byref(checked))
+    if s != PCG_OK:
+        raise PcgError(s, "pcg_check_status")
+    return code.value, bool(checked.value)
 
 
 def pcg_kernel_stats(ctx) -> tuple[int, int, float]:
