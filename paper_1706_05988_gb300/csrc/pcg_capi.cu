@@ -14,6 +14,7 @@
 #include "../../include/pcg.h"
 #include "pcg_internal.h"
 #include "pcg_general.cuh"
+#include "pcg_host_parallel.h"
 
 using namespace pcgk;
 
@@ -253,10 +254,27 @@ pcg_status pcg_create(const pcg_matrix* A, uint32_t flags, pcg_ctx** out) {
     nnz = A->nnz;
     if (!(flags & PCG_DEVICE_PTRS)) {   // host arrays can be validated here
       if (A->row_ptr[0] != 0 || A->row_ptr[n] != nnz) return PCG_EINVAL;
-      for (int64_t i = 0; i < n; ++i)
-        if (A->row_ptr[i + 1] < A->row_ptr[i]) return PCG_EINVAL;
-      for (int64_t k = 0; k < nnz; ++k)
-        if (A->col[k] < 0 || A->col[k] >= n) return PCG_EINVAL;
+      // every row's range inside [0, nnz] and ordered, every column index in [0, n)
+      // (chunks of rows on several threads)
+      std::vector<char> bad((size_t)pcgk::host::row_chunks(n), 0);
+      pcgk::host::for_chunks((long long)bad.size(), [&](long long ch) {
+        const int64_t i1 = std::min<int64_t>(n, (ch + 1) * pcgk::host::kRowsPerChunk);
+        for (int64_t i = ch * pcgk::host::kRowsPerChunk; i < i1; ++i) {
+          const int64_t beg = A->row_ptr[i], end = A->row_ptr[i + 1];
+          if (beg < 0 || end < beg || end > nnz) {
+            bad[(size_t)ch] = 1;
+            return;
+          }
+          for (int64_t k = beg; k < end; ++k) {
+            if (A->col[k] < 0 || A->col[k] >= n) {
+              bad[(size_t)ch] = 1;
+              return;
+            }
+          }
+        }
+      });
+      for (char b : bad)
+        if (b) return PCG_EINVAL;
     }
   } else {
     return PCG_EINVAL;
@@ -320,25 +338,27 @@ pcg_status pcg_create(const pcg_matrix* A, uint32_t flags, pcg_ctx** out) {
     if (bad) return bail(fail(c, PCG_EINVAL, "PCG_JACOBI needs a positive diagonal"));
   } else if (flags & PCG_JACOBI) {
     // M^{-1} = diag(A)^{-1}, formed on the host from the operator's description
-    std::vector<double> dinv(n);
-    bool ok = true;
-    if (A->layout == PCG_CSR32) {
-      for (int64_t i = 0; i < n; ++i) {
-        double d = 0.0;
-        for (int32_t k = A->row_ptr[i]; k < A->row_ptr[i + 1]; ++k)
-          if (A->col[k] == i) d += A->val[k];
-        ok = ok && d > 0.0;
+    pcgk::host::buffer<double> dinv((size_t)n);
+    std::vector<char> bad((size_t)pcgk::host::row_chunks(n), 0);
+    pcgk::host::for_chunks((long long)bad.size(), [&](long long ch) {
+      const int64_t i0 = ch * pcgk::host::kRowsPerChunk, i1 = std::min<int64_t>(n, i0 + pcgk::host::kRowsPerChunk);
+      for (int64_t i = i0; i < i1; ++i) {
+        double d;
+        if (A->layout == PCG_CSR32) {
+          d = 0.0;
+          for (int32_t k = A->row_ptr[i]; k < A->row_ptr[i + 1]; ++k)
+            if (A->col[k] == i) d += A->val[k];
+        } else if (A->diag) {
+          d = A->diag[i];
+        } else {
+          d = A->layout == PCG_STENCIL7_3D ? 6.0 : 4.0;
+        }
+        if (!(d > 0.0)) bad[(size_t)ch] = 1;
         dinv[i] = 1.0 / d;
       }
-    } else if (A->diag) {
-      for (int64_t i = 0; i < n; ++i) {
-        ok = ok && A->diag[i] > 0.0;
-        dinv[i] = 1.0 / A->diag[i];
-      }
-    } else {
-      std::fill(dinv.begin(), dinv.end(), A->layout == PCG_STENCIL7_3D ? 1.0 / 6.0 : 1.0 / 4.0);
-    }
-    if (!ok) return bail(fail(c, PCG_EINVAL, "PCG_JACOBI needs a positive diagonal"));
+    });
+    for (char b : bad)
+      if (b) return bail(fail(c, PCG_EINVAL, "PCG_JACOBI needs a positive diagonal"));
     const double* dd = nullptr;
     c->flags &= ~PCG_DEVICE_PTRS;
     if ((s = place<double>(c, dinv.data(), n, &dd)) != PCG_OK) return bail(s);

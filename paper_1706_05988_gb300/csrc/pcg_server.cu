@@ -29,6 +29,7 @@
 #define PCG_KERNELS_IMPL
 #include "../../include/pcg.h"
 
+#include "pcg_host_parallel.h"
 #include "pcg_server_kernel.cuh"
 
 using namespace pcgk::srv;
@@ -45,9 +46,9 @@ struct Request {
   const double* b_src = nullptr;
   const int32_t *row_ptr_src = nullptr, *col_src = nullptr;
   const double *val_src = nullptr, *diag_src = nullptr, *ax_src = nullptr, *ay_src = nullptr, *az_src = nullptr;
-  std::vector<double> b;
-  std::vector<int32_t> row_ptr, col;
-  std::vector<double> val, diag, ax, ay, az;
+  host::buffer<double> b;
+  host::buffer<int32_t> row_ptr, col;
+  host::buffer<double> val, diag, ax, ay, az;
   double tol, sigma;
   int method, maxit, family;
   int mode;                         // 0 binary64, 1 + Jacobi, 2 mixed, 3 mixed + Jacobi
@@ -61,6 +62,8 @@ struct Request {
   int precision = PCG_FP64;
   // device lane: the whole GPU, the single-system solver, a host worker thread
   bool device = false, device_done = false;
+  pcg_ctx* ctx = nullptr;           // created ahead of the solve by the preparing thread
+  pcg_status prep_status = PCG_OK;
   std::vector<double> x_host;
   std::vector<double> alpha_log, beta_log;   // device lane: alpha_i, beta_i of the solve
   pcg_result device_res{};
@@ -69,27 +72,34 @@ struct Request {
   size_t stage_off = 0, stage_end = 0;
 };
 
+// One chunk of rows of a request's validation pass.
+struct RowPass {
+  double diag_sum = 0.0;   // sum of the rows' diagonals, left to right
+  bool diag_ok = true;     // every diagonal positive and finite
+  bool bad = false;        // a row_ptr range or a column index out of range
+};
+
 // Keeps the request's own copies of its arrays (it waits for memory; the caller's may go).
 void own_arrays(Request* R) {
   const long long n = R->n;
-  if (R->b.empty()) R->b.assign(R->b_src, R->b_src + n);
+  if (R->b.empty()) host::assign(R->b, R->b_src, (size_t)n);
   R->b_src = R->b.data();
   if (R->family == 4) {
-    R->row_ptr.assign(R->row_ptr_src, R->row_ptr_src + n + 1);
-    R->col.assign(R->col_src, R->col_src + R->nnz);
-    R->val.assign(R->val_src, R->val_src + R->nnz);
+    host::assign(R->row_ptr, R->row_ptr_src, (size_t)n + 1);
+    host::assign(R->col, R->col_src, (size_t)R->nnz);
+    host::assign(R->val, R->val_src, (size_t)R->nnz);
     R->row_ptr_src = R->row_ptr.data();
     R->col_src = R->col.data();
     R->val_src = R->val.data();
   } else if (R->family == 1 || R->family == 3) {
-    R->diag.assign(R->diag_src, R->diag_src + n);
-    R->ax.assign(R->ax_src, R->ax_src + n);
-    R->ay.assign(R->ay_src, R->ay_src + n);
+    host::assign(R->diag, R->diag_src, (size_t)n);
+    host::assign(R->ax, R->ax_src, (size_t)n);
+    host::assign(R->ay, R->ay_src, (size_t)n);
     R->diag_src = R->diag.data();
     R->ax_src = R->ax.data();
     R->ay_src = R->ay.data();
     if (R->family == 3) {
-      R->az.assign(R->az_src, R->az_src + n);
+      host::assign(R->az, R->az_src, (size_t)n);
       R->az_src = R->az.data();
     }
   }
@@ -99,10 +109,9 @@ void release_arrays(Request* R) {
   R->b_src = nullptr;
   R->row_ptr_src = R->col_src = nullptr;
   R->val_src = R->diag_src = R->ax_src = R->ay_src = R->az_src = nullptr;
-  std::vector<int32_t>().swap(R->row_ptr);
-  std::vector<int32_t>().swap(R->col);
-  for (std::vector<double>* v : {&R->b, &R->val, &R->diag, &R->ax, &R->ay, &R->az})
-    std::vector<double>().swap(*v);
+  host::buffer<int32_t>().swap(R->row_ptr);
+  host::buffer<int32_t>().swap(R->col);
+  for (host::buffer<double>* v : {&R->b, &R->val, &R->diag, &R->ax, &R->ay, &R->az}) host::buffer<double>().swap(*v);
 }
 
 }  // namespace
@@ -121,6 +130,11 @@ constexpr int kLargeLaneClusters = 16;         // clusters of the large lane (8 
 // no cluster has: the lanes finish their current requests and exit, the request runs on
 // the single-system solver, and the lanes are relaunched.
 constexpr long long kDeviceN = 1LL << 19;
+// Smaller requests go first: a device request waits while the lanes hold published work
+// that no cluster has claimed yet, but at most this long (so that a steady stream of small
+// requests cannot hold it back).
+constexpr auto kDeviceDefer = std::chrono::milliseconds(100);
+constexpr int kPrepAhead = 2;   // device-lane contexts created ahead of their solve
 
 struct Lane {
   int csize = 2, clusters = 0;
@@ -152,10 +166,14 @@ struct pcg_server {
   std::map<size_t, size_t> free_blocks;   // offset -> size (first fit, coalesced)
   Lane lane[kLanes];
   cudaStream_t cstream = nullptr;   // copies
-  // device lane
-  std::thread worker;
-  std::condition_variable cv;
-  std::deque<Request*> device_queue;
+  // device lane: `prep` creates the requests' solver contexts (validation, device memory,
+  // the operator's upload) in order, at most kPrepAhead ahead of `worker`, which solves
+  // them; so the uploads of the next requests overlap the current solve
+  std::thread worker, prep;
+  std::condition_variable cv, prep_cv;
+  std::deque<Request*> prep_queue;              // submitted, context not yet created
+  std::deque<Request*> device_queue;            // context created (or failed), not yet solved
+  int prepared = 0;                             // contexts created and not yet destroyed
   bool quit = false, device_busy = false;
   pcg_status worker_error = PCG_OK;
   uint64_t next_ticket = 1;
@@ -277,7 +295,7 @@ pcg_status upload(pcg_server* S, Request* R, bool staged) {
     if (at + pad256(bytes) > R->bytes) return nullptr;   // never: the layout is request_bytes'
     void* dst = base + at;
     if (staged) {
-      if (bytes) memcpy(hs + h_op + (at - at0), src, bytes);
+      host::copy(hs + h_op + (at - at0), src, bytes);
     } else if (bytes && cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, S->cstream) != cudaSuccess) {
       return nullptr;
     }
@@ -323,7 +341,7 @@ pcg_status upload(pcg_server* S, Request* R, bool staged) {
   }
   const size_t op64 = op64_bytes(*R);
   if (staged) {
-    memcpy(hs, R->b_src, n * 8);
+    host::copy(hs, R->b_src, n * 8);
     if (cudaMemcpyAsync(v, hs, n * 8, cudaMemcpyHostToDevice, S->cstream) != cudaSuccess) return PCG_ECUDA;
     if (op64 && cudaMemcpyAsync(base + at0, hs + h_op, op64, cudaMemcpyHostToDevice, S->cstream) != cudaSuccess)
       return PCG_ECUDA;
@@ -500,28 +518,29 @@ pcg_status pump(pcg_server* S) {
   return PCG_OK;
 }
 
-// The device lane's host thread: for each request, drains the lanes (their clusters
-// finish what they hold and exit; every wait of theirs is bounded), solves the request
-// with the single-system solver on the whole GPU, then lets pump() relaunch the lanes.
-void device_worker(pcg_server* S) {
+// True while a lane has published work that no cluster has claimed.  (Requests whose
+// copies are in flight do not count: one may wait for its ring slot, which only the
+// caller's poll of an earlier request frees.)
+bool lanes_pending(const pcg_server* S) {
+  for (const Lane& L : S->lane) {
+    cuda::atomic_ref<unsigned, cuda::thread_scope_system> claimed(L.sh->claimed);
+    if (L.published > claimed.load(cuda::memory_order_acquire)) return true;
+  }
+  return false;
+}
+
+// The device lane's preparing thread: creates each request's solver context while the
+// lanes and the previous device-lane solve run, then hands the request to the worker.
+void prep_worker(pcg_server* S) {
   cudaSetDevice(S->device);
   std::unique_lock<std::mutex> lk(S->mu);
   for (;;) {
-    S->cv.wait(lk, [&] { return S->quit || !S->device_queue.empty(); });
+    S->prep_cv.wait(lk, [&] { return S->quit || (!S->prep_queue.empty() && S->prepared < kPrepAhead); });
     if (S->quit) return;
-    Request* R = S->device_queue.front();
-    S->device_queue.pop_front();
-    S->device_busy = true;
-    for (Lane& L : S->lane) {
-      cuda::atomic_ref<unsigned, cuda::thread_scope_system> stop(L.sh->stop);
-      stop.store(1u, cuda::memory_order_release);
-    }
+    Request* R = S->prep_queue.front();
+    S->prep_queue.pop_front();
+    ++S->prepared;
     lk.unlock();
-    for (Lane& L : S->lane) {
-      cuda::atomic_ref<unsigned, cuda::thread_scope_system> live(L.sh->live);
-      while (live.load(cuda::memory_order_acquire) != 0) std::this_thread::sleep_for(std::chrono::microseconds(50));
-      cudaStreamSynchronize(L.kstream);
-    }
     pcg_matrix A = R->A;
     A.row_ptr = R->row_ptr.empty() ? nullptr : R->row_ptr.data();
     A.col = R->col.empty() ? nullptr : R->col.data();
@@ -530,23 +549,78 @@ void device_worker(pcg_server* S) {
     A.ax = R->ax.empty() ? nullptr : R->ax.data();
     A.ay = R->ay.empty() ? nullptr : R->ay.data();
     A.az = R->az.empty() ? nullptr : R->az.data();
+    pcg_ctx* c = nullptr;
+    R->prep_status = pcg_create(&A, R->flags, &c);
+    R->ctx = c;
+    // the operator is on the device now; b stays for pcg_solve
+    host::buffer<int32_t>().swap(R->row_ptr);
+    host::buffer<int32_t>().swap(R->col);
+    for (host::buffer<double>* v : {&R->val, &R->diag, &R->ax, &R->ay, &R->az}) host::buffer<double>().swap(*v);
     R->x_host.assign((size_t)R->n, 0.0);
     R->alpha_log.assign((size_t)R->maxit + 1, NAN);
     R->beta_log.assign((size_t)R->maxit + 1, NAN);
-    R->device_res = pcg_result{};
-    R->device_res.alpha_hist = R->alpha_log.data();
-    R->device_res.beta_hist = R->beta_log.data();
-    pcg_ctx* c = nullptr;
-    pcg_status st = pcg_create(&A, R->flags, &c);
+    lk.lock();
+    S->device_queue.push_back(R);
+    S->cv.notify_all();
+  }
+}
+
+// The device lane's solving thread: for each prepared request, lets the lanes take the
+// smaller requests already published (bounded by kDeviceDefer), drains the lanes (their
+// clusters finish what they hold and exit; every wait of theirs is bounded), solves the
+// request with the single-system solver on the whole GPU, then lets pump() relaunch the
+// lanes.
+void device_worker(pcg_server* S) {
+  cudaSetDevice(S->device);
+  std::unique_lock<std::mutex> lk(S->mu);
+  for (;;) {
+    S->cv.wait(lk, [&] { return S->quit || !S->device_queue.empty(); });
+    if (S->quit) return;
+    Request* R = S->device_queue.front();
+    S->device_queue.pop_front();
+    pcg_status st = R->prep_status;
     if (st == PCG_OK) {
-      st = pcg_solve(c, R->b.data(), nullptr, R->method, R->method == PCG_SPCG ? R->sigma : 0.0, R->tol, R->maxit,
-                     R->precision, R->x_host.data(), &R->device_res);
-      pcg_destroy(c);
+      const auto defer_end = std::chrono::steady_clock::now() + kDeviceDefer;
+      while (!S->quit && lanes_pending(S) && std::chrono::steady_clock::now() < defer_end) {
+        const pcg_status s = pump(S);   // publishes finished copies, (re)launches the lanes
+        if (s != PCG_OK) {
+          S->worker_error = s;
+          break;
+        }
+        lk.unlock();
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+        lk.lock();
+      }
+      if (S->quit) return;            // pcg_server_destroy frees the prepared context
+      S->device_busy = true;
+      for (Lane& L : S->lane) {
+        cuda::atomic_ref<unsigned, cuda::thread_scope_system> stop(L.sh->stop);
+        stop.store(1u, cuda::memory_order_release);
+      }
+      lk.unlock();
+      for (Lane& L : S->lane) {
+        cuda::atomic_ref<unsigned, cuda::thread_scope_system> live(L.sh->live);
+        while (live.load(cuda::memory_order_acquire) != 0) std::this_thread::sleep_for(std::chrono::microseconds(50));
+        cudaStreamSynchronize(L.kstream);
+      }
+      R->device_res = pcg_result{};
+      R->device_res.alpha_hist = R->alpha_log.data();
+      R->device_res.beta_hist = R->beta_log.data();
+      st = pcg_solve(R->ctx, R->b.data(), nullptr, R->method, R->method == PCG_SPCG ? R->sigma : 0.0, R->tol,
+                     R->maxit, R->precision, R->x_host.data(), &R->device_res);
+    } else {
+      lk.unlock();
     }
+    // freeing device memory waits for the whole device, so the context goes while the
+    // lanes are down
+    pcg_destroy(R->ctx);
+    R->ctx = nullptr;
     lk.lock();
     R->device_status = st;
     R->device_done = true;
     release_arrays(R);
+    --S->prepared;
+    S->prep_cv.notify_all();
     S->device_busy = false;
     const pcg_status s = pump(S);     // the lanes come back for published work
     if (s != PCG_OK) S->worker_error = s;
@@ -616,6 +690,7 @@ pcg_status pcg_server_create(size_t hbm_budget_bytes, int32_t max_slots, pcg_ser
   }
   try {
     S->worker = std::thread(device_worker, S);
+    S->prep = std::thread(prep_worker, S);
   } catch (...) {
     return bail(PCG_ENOMEM);
   }
@@ -625,14 +700,14 @@ pcg_status pcg_server_create(size_t hbm_budget_bytes, int32_t max_slots, pcg_ser
 
 void pcg_server_destroy(pcg_server* S) {
   if (!S) return;
-  if (S->worker.joinable()) {
-    {
-      std::lock_guard<std::mutex> lock(S->mu);
-      S->quit = true;
-    }
-    S->cv.notify_all();
-    S->worker.join();
+  {
+    std::lock_guard<std::mutex> lock(S->mu);
+    S->quit = true;
   }
+  S->cv.notify_all();
+  S->prep_cv.notify_all();
+  if (S->worker.joinable()) S->worker.join();
+  if (S->prep.joinable()) S->prep.join();
   for (Lane& L : S->lane) {
     if (L.sh) {
       cuda::atomic_ref<unsigned, cuda::thread_scope_system> stop(L.sh->stop);
@@ -644,6 +719,7 @@ void pcg_server_destroy(pcg_server* S) {
   if (S->cstream) cudaStreamSynchronize(S->cstream);
   for (auto& kv : S->all) {
     if (kv.second->uploaded) cudaEventDestroy(kv.second->uploaded);
+    if (kv.second->ctx) pcg_destroy(kv.second->ctx);   // prepared, never solved
     delete kv.second;
   }
   for (cudaEvent_t e : S->free_events) cudaEventDestroy(e);
@@ -697,18 +773,41 @@ pcg_status pcg_submit_ex(pcg_server* S, const pcg_matrix* A, const double* b, do
     R->row_ptr_src = A->row_ptr;
     R->col_src = A->col;
     R->val_src = A->val;
-    bool diag_ok = true;
-    for (long long i = 0; i < n; ++i) {
-      double dg = 0.0;
-      for (int k = A->row_ptr[i]; k < A->row_ptr[i + 1]; ++k) {
-        if (A->col[k] < 0 || A->col[k] >= n) {
-          delete R;
-          return PCG_EINVAL;
+    // one pass over the rows (chunks of rows on several threads): row_ptr ranges, column
+    // indices, and each row's diagonal (the sum of its diagonal entries)
+    const long long nnz = A->nnz;
+    std::vector<RowPass> part((size_t)host::row_chunks(n));
+    host::for_chunks((long long)part.size(), [&](long long c) {
+      RowPass r;
+      const long long i1 = std::min(n, (c + 1) * host::kRowsPerChunk);
+      for (long long i = c * host::kRowsPerChunk; i < i1 && !r.bad; ++i) {
+        const long long beg = A->row_ptr[i], end = A->row_ptr[i + 1];
+        if (beg < 0 || end < beg || end > nnz) {
+          r.bad = true;
+          break;
         }
-        if (A->col[k] == i) dg += A->val[k];
+        double dg = 0.0;
+        for (long long k = beg; k < end; ++k) {
+          const int32_t cj = A->col[k];
+          if (cj < 0 || cj >= n) {
+            r.bad = true;
+            break;
+          }
+          if (cj == i) dg += A->val[k];
+        }
+        r.diag_sum += dg;
+        r.diag_ok = r.diag_ok && dg > 0.0 && isfinite(dg);
       }
-      diag_sum += dg;
-      diag_ok = diag_ok && dg > 0.0 && isfinite(dg);
+      part[(size_t)c] = r;
+    });
+    bool diag_ok = true;
+    for (const RowPass& r : part) {              // in chunk order
+      if (r.bad) {
+        delete R;
+        return PCG_EINVAL;
+      }
+      diag_sum += r.diag_sum;
+      diag_ok = diag_ok && r.diag_ok;
     }
     if (jac && !diag_ok) {                       // Jacobi needs a positive diagonal
       delete R;
@@ -730,10 +829,20 @@ pcg_status pcg_submit_ex(pcg_server* S, const pcg_matrix* A, const double* b, do
       R->ax_src = A->ax;
       R->ay_src = A->ay;
       R->az_src = fam == 3 ? A->az : nullptr;
+      std::vector<RowPass> part((size_t)host::row_chunks(n));
+      host::for_chunks((long long)part.size(), [&](long long c) {
+        RowPass r;
+        const long long i1 = std::min(n, (c + 1) * host::kRowsPerChunk);
+        for (long long i = c * host::kRowsPerChunk; i < i1; ++i) {
+          r.diag_sum += A->diag[i];
+          r.diag_ok = r.diag_ok && A->diag[i] > 0.0 && isfinite(A->diag[i]);
+        }
+        part[(size_t)c] = r;
+      });
       bool diag_ok = true;
-      for (long long i = 0; i < n; ++i) {
-        diag_sum += A->diag[i];
-        diag_ok = diag_ok && A->diag[i] > 0.0 && isfinite(A->diag[i]);
+      for (const RowPass& r : part) {            // in chunk order
+        diag_sum += r.diag_sum;
+        diag_ok = diag_ok && r.diag_ok;
       }
       if (jac && !diag_ok) {
         delete R;
@@ -763,9 +872,9 @@ pcg_status pcg_submit_ex(pcg_server* S, const pcg_matrix* A, const double* b, do
     }
     R->ticket = S->next_ticket++;
     S->all[R->ticket] = R;
-    S->device_queue.push_back(R);
+    S->prep_queue.push_back(R);
     *ticket = R->ticket;
-    S->cv.notify_one();
+    S->prep_cv.notify_all();
     return PCG_OK;
   }
   std::lock_guard<std::mutex> lock(S->mu);
@@ -859,7 +968,7 @@ pcg_status pcg_poll(pcg_server* S, uint64_t ticket, double* x_out, pcg_result* r
 pcg_status pcg_server_stats(pcg_server* S, int64_t* waiting, int64_t* inflight, size_t* free_bytes) {
   if (!S) return PCG_EINVAL;
   std::lock_guard<std::mutex> lock(S->mu);
-  if (waiting) *waiting = (int64_t)(S->waiting.size() + S->device_queue.size());
+  if (waiting) *waiting = (int64_t)(S->waiting.size() + S->prep_queue.size() + S->device_queue.size());
   if (inflight) *inflight = (int64_t)S->inflight.size();
   if (free_bytes) {
     size_t f = 0;

@@ -251,3 +251,32 @@ def test_device_lane_requests(B):
         assert r[0] == B.PCG_OK, r[0]
         tr = np.linalg.norm(b - oracle.apply(P, r[1])) / np.linalg.norm(b)
         assert tr <= (1e-8 if pr == B.PCG_MIXED_IR else 3e-8) and abs(tr - r[3]) <= 1e-3 * tr + 1e-15, (tr, r[3])
+
+
+def test_smaller_requests_go_first(B):
+    """Small requests that arrive while a whole-GPU request runs are taken by the cluster
+    lanes before the next whole-GPU request starts: they finish before it."""
+    d1 = S.laplacian_2d(1024)                                    # n = 1,048,576: long enough to
+    d2 = S.laplacian_3d(81)                                      # hold the small submissions
+    small = [S.laplacian_2d(30, 20), random_sdd(1500, 11), S.laplacian_3d(12), S.laplacian_2d(64),
+             random_sdd(800, 12), S.laplacian_3d(20, 18, 9)]
+    reqs = [(d1, S.normal(80, d1.n), 1e-10), (d2, S.normal(81, d2.n), 1e-8)]
+    reqs += [(P, S.normal(82 + i, P.n), 1e-8) for i, P in enumerate(small)]
+    with B.Server(256 << 20, 16) as srv:
+        t0 = time.time()
+        pending = {srv.submit(P, b, tol=tol): k for k, (P, b, tol) in enumerate(reqs)}
+        fin, res = {}, {}
+        while pending:
+            assert time.time() - t0 < 120.0, "requests did not finish"
+            for t in list(pending):
+                r = srv.poll(t)
+                if r is not None:
+                    k = pending.pop(t)
+                    fin[k], res[k] = time.time(), r
+            time.sleep(0.0005)
+    for k, (P, b, tol) in enumerate(reqs):
+        assert res[k][0] == B.PCG_OK, (k, res[k][0])
+        tr = np.linalg.norm(b - oracle.apply(P, res[k][1])) / np.linalg.norm(b)
+        assert tr <= 3 * tol, (k, tr)
+    assert fin[0] < fin[1]                                        # whole-GPU requests in order
+    assert max(fin[k] for k in range(2, len(reqs))) < fin[1]      # the small ones before the second

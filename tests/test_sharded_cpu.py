@@ -173,7 +173,7 @@ def test_sharded_gloo_ranks_vs_oracle(world):
     import torch.multiprocessing as mp
     import oracle
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_rank_main, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
