@@ -39,7 +39,8 @@ FALLBACK_HBM_GBS = 6800.0
 # (a one-pass capture, profiles/spcg_iter_stencil7_256cubed_traffic.md), keyed by the SHA-256 of the kernel
 # source it was taken on; a changed kernel reports null
 NCU_TRAFFIC = {"db28dd47f9fa25b7": 1561.35e6, "e9be0f27e77e4297": 1561.47e6, "9a4ca33e0286f39c": 1561.25e6,
-               "a8b0005e527d5aff": 1561.77e6, "ed0a31d47b72680c": 1561.46e6}
+               "a8b0005e527d5aff": 1561.77e6, "ed0a31d47b72680c": 1561.46e6,
+               "bbd2e5118c8fc4ca": 1561.30e6}
 
 
 def kernel_source_sha() -> str:
@@ -750,7 +751,7 @@ def run_ours(args):
 
 def profile_case(kind: str, n: int) -> int:
     """A short solve for an ncu capture (no timing, no JSON): `spcg` runs 8 iterations of the
-    main kernel on the n^3 Laplacian (`-split32`: with the dots on the FP32 pipe; `-staged`: the
+    main kernel on the n^3 Laplacian (`spcg2d`: on the n^2 Laplacian; `-split32`: with the dots on the FP32 pipe; `-staged`: the
     TMA-staged sweep with a ring of 2 chunks); `jacobi-fp64` and `jacobi-mixed` run 12 iterations of the
     Jacobi sweeps (sigma = 1; the mixed one with eta = 1e-30, so no restart interrupts);
     `batch-*` run batched launches (see below)."""
@@ -791,6 +792,12 @@ def profile_case(kind: str, n: int) -> int:
             for _ in range(2):
                 _, it, st, _ = bt.solve(bs, sig, tol=1e-8, maxit=100000)
         print(kind, int(np.sum(st == 0)), float(np.mean(it)))
+        return 0
+    if kind == "spcg2d":
+        P = S.laplacian_2d(n)
+        with pkg.Solver(P) as s:
+            r = s.solve(S.normal(0, P.n), method="spcg", sigma=4.0, maxit=8)
+        print(kind, n, r.status, r.iters)
         return 0
     P, b = S.poisson3d_manufactured(n)[:2]
     if kind.startswith("spcg"):
@@ -842,7 +849,7 @@ def compare_iter_forms(n: int) -> int:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile-case", choices=["spcg", "spcg-split32", "spcg-staged", "spcg-staged-split32",
+    ap.add_argument("--profile-case", choices=["spcg", "spcg2d", "spcg-split32", "spcg-staged", "spcg-staged-split32",
                                                "jacobi-fp64", "jacobi-mixed", "batch-fp64",
                                                "batch-mixed-jacobi", "batch-large-fp64-jacobi",
                                                "batch-large-mixed-jacobi", "batch-large-mixed-jacobi-occ4", "batch-large-mixed-jacobi-c16",

@@ -144,8 +144,26 @@ struct StencilOp {
       xp[e] = e == VEC - 1 ? xr : c[e + 1];
       wc[e] = c[e];
     }
-    if (MODE == ST_LAP_FIXED) {
-      // integer-pipe fixed-point rows (pcg_fixedsum.cuh); FP64 additions only as a fallback
+    if (MODE == ST_LAP_FIXED && !(DIM == 3 && VEC == 2)) {
+      // integer-pipe fixed-point rows, full form (pcg_fixedsum.cuh): no FP64 instruction,
+      // for any input; one row at a time, each unpacking its own terms
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        FxTerm t[DIM == 3 ? 7 : 5];
+        t[0] = fx_centre_full<DIM>(c[e]);
+        t[1] = fx_raw_full(xm[e], 1);
+        t[2] = fx_raw_full(xp[e], 1);
+        t[3] = fx_raw_full(ym[e], 1);
+        t[4] = fx_raw_full(yp[e], 1);
+        if constexpr (DIM == 3) {
+          t[5] = fx_raw_full(zm[e], 1);
+          t[6] = fx_raw_full(zp[e], 1);
+        }
+        aw[e] = fx_sum_full(t);
+      }
+    } else if (MODE == ST_LAP_FIXED) {
+      // integer-pipe fixed-point rows, fast form (pcg_fixedsum.cuh); FP64 additions for a
+      // unit with an Inf/NaN term or a row outside the normal range
       FxRaw rc[VEC], rym[VEC], ryp[VEC], rzm[VEC], rzp[VEC];
       const FxRaw rxl = fx_raw(xl), rxr = fx_raw(xr);
       int special = rxl.special | rxr.special;
