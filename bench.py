@@ -751,7 +751,8 @@ def run_ours(args):
 
 def profile_case(kind: str, n: int) -> int:
     """A short solve for an ncu capture (no timing, no JSON): `spcg` runs 8 iterations of the
-    main kernel on the n^3 Laplacian (`spcg2d`: on the n^2 Laplacian; `-split32`: with the dots on the FP32 pipe; `-staged`: the
+    main kernel on the n^3 Laplacian (`spcg2d`: on the n^2 Laplacian, `spcg2d-mixed`: its mixed-precision
+    sweep for 12 iterations with eta = 1e-30; `-split32`: with the dots on the FP32 pipe; `-staged`: the
     TMA-staged sweep with a ring of 2 chunks); `jacobi-fp64` and `jacobi-mixed` run 12 iterations of the
     Jacobi sweeps (sigma = 1; the mixed one with eta = 1e-30, so no restart interrupts);
     `batch-*` run batched launches (see below)."""
@@ -793,10 +794,14 @@ def profile_case(kind: str, n: int) -> int:
                 _, it, st, _ = bt.solve(bs, sig, tol=1e-8, maxit=100000)
         print(kind, int(np.sum(st == 0)), float(np.mean(it)))
         return 0
-    if kind == "spcg2d":
+    if kind in ("spcg2d", "spcg2d-mixed"):
         P = S.laplacian_2d(n)
         with pkg.Solver(P) as s:
-            r = s.solve(S.normal(0, P.n), method="spcg", sigma=4.0, maxit=8)
+            if kind == "spcg2d":
+                r = s.solve(S.normal(0, P.n), method="spcg", sigma=4.0, maxit=8)
+            else:
+                C.pcg_set_param(s.ctx, C.PCG_PARAM_MIXED_ETA, 1e-30)
+                r = s.solve(S.normal(0, P.n), method="spcg", sigma=4.0, maxit=12, precision=C.PCG_MIXED_IR)
         print(kind, n, r.status, r.iters)
         return 0
     P, b = S.poisson3d_manufactured(n)[:2]
@@ -849,7 +854,7 @@ def compare_iter_forms(n: int) -> int:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile-case", choices=["spcg", "spcg2d", "spcg-split32", "spcg-staged", "spcg-staged-split32",
+    ap.add_argument("--profile-case", choices=["spcg", "spcg2d", "spcg2d-mixed", "spcg-split32", "spcg-staged", "spcg-staged-split32",
                                                "jacobi-fp64", "jacobi-mixed", "batch-fp64",
                                                "batch-mixed-jacobi", "batch-large-fp64-jacobi",
                                                "batch-large-mixed-jacobi", "batch-large-mixed-jacobi-occ4", "batch-large-mixed-jacobi-c16",
