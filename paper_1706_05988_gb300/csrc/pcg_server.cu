@@ -508,7 +508,8 @@ pcg_status pump(pcg_server* S) {
   if (S->device_busy) return PCG_OK;   // the lanes stay down while the device lane runs
   for (Lane& L : S->lane) {
     cuda::atomic_ref<unsigned, cuda::thread_scope_system> live(L.sh->live);
-    if (L.published > L.sh->claimed && live.load(cuda::memory_order_acquire) == 0) {
+    cuda::atomic_ref<unsigned, cuda::thread_scope_system> claimed(L.sh->claimed);
+    if (L.published > claimed.load(cuda::memory_order_acquire) && live.load(cuda::memory_order_acquire) == 0) {
       // the lane's previous kernel (if any) has exited: wait for its stream, then relaunch
       if (cudaStreamSynchronize(L.kstream) != cudaSuccess) return PCG_ECUDA;
       const pcg_status s = launch_lane(S, L);
@@ -662,6 +663,11 @@ pcg_status pcg_server_create(size_t hbm_budget_bytes, int32_t max_slots, pcg_ser
   if (small_max <= 0 || large_max <= 0) return bail(PCG_ECUDA);
   const int blocks = small_max * kLaneCluster[0];
   const int large = std::min(kLargeLaneClusters, std::max(1, large_max / 2));
+  int host_atomics = 0;   // native atomics between the GPU and host memory (NVLink-C2C)
+  if (cudaDeviceGetAttribute(&host_atomics, cudaDevAttrHostNativeAtomicSupported, S->device) != cudaSuccess) {
+    cudaGetLastError();
+    host_atomics = 0;
+  }
   for (int l = 0; l < kLanes; ++l) {
     Lane& L = S->lane[l];
     L.csize = kLaneCluster[l];
@@ -671,6 +677,7 @@ pcg_status pcg_server_create(size_t hbm_budget_bytes, int32_t max_slots, pcg_ser
     if (cudaHostAlloc(&p, sizeof(ServerShared), cudaHostAllocMapped) != cudaSuccess) return bail(PCG_ENOMEM);
     L.sh = (ServerShared*)p;
     memset(L.sh, 0, sizeof(ServerShared));
+    L.sh->atomic_mirror = host_atomics ? 1u : 0u;
     if (cudaHostGetDevicePointer((void**)&L.d_sh, L.sh, 0) != cudaSuccess) return bail(PCG_ECUDA);
     if (cudaHostAlloc(&p, S->cap * sizeof(WorkItem), cudaHostAllocMapped) != cudaSuccess) return bail(PCG_ENOMEM);
     L.items = (WorkItem*)p;

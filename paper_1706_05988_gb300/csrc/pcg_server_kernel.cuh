@@ -27,7 +27,8 @@ struct ServerShared {
   unsigned int claimed;      // items taken by the kernel (mirror of the device counter)
   unsigned int live;         // 1 while a kernel runs (cleared by the last exiting cluster)
   unsigned int stop;         // host asks the kernel to exit
-  unsigned int pad[28];
+  unsigned int atomic_mirror;  // 1: the device may use system-scope atomics on this memory
+  unsigned int pad[27];
 };
 
 __device__ __forceinline__ unsigned long long now_ns() {
@@ -140,7 +141,14 @@ __global__ void __launch_bounds__(kBlock, PCG_SERVER_MIN_BLOCKS) k_server(Server
         if (h < t) {
           if (atomicCAS(claim, h, h + 1) == h) {
             task = h;
-            *(volatile unsigned*)&sh->claimed = h + 1 > sh->claimed ? h + 1 : sh->claimed;
+            // the mirror only grows: an atomic maximum where the host link has native
+            // atomics (two leaders' plain stores could land out of order and leave it
+            // behind the device counter, which the host would read as unclaimed work)
+            if (sh->atomic_mirror) {
+              atomicMax_system(&sh->claimed, h + 1);
+            } else {
+              *(volatile unsigned*)&sh->claimed = h + 1 > sh->claimed ? h + 1 : sh->claimed;
+            }
             break;
           }
           continue;
