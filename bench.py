@@ -348,7 +348,7 @@ def serve_stream(pkg, reqs, form: str):
 
 
 def serving_measure(pkg, nreq: int, rate: float, tol=None, n_max_exp: float = 5.0,
-                    forms=("fp64", "mixed")) -> dict:
+                    forms=("fp64", "mixed"), gpu: int = 0) -> dict:
     """p50/p99 latency and solves/s of the request stream through the continuous-batching
     server, per served form (request_policy), against the same stream served one request at a
     time by plain FP64 solves of the single-system solver (same shift rule and tolerances).
@@ -369,20 +369,25 @@ def serving_measure(pkg, nreq: int, rate: float, tol=None, n_max_exp: float = 5.
                 "p99_ms": 1e3 * float(np.percentile(lat, 99)), "span_s": span}
 
     for form in forms:
-        out[f"served_{form}"] = summary(*serve_stream(pkg, reqs, form))
+        with ClockSampler(gpu) as clk:
+            out[f"served_{form}"] = summary(*serve_stream(pkg, reqs, form))
+        out[f"served_{form}"]["clocks"] = clk.summary()
     # one at a time: each request starts when it has arrived and the previous one is done
     # (the shifts are computed before the clock starts)
     sigmas = [request_sigma(P) for _, P, _, _ in reqs]
     lat1 = np.zeros(nreq)
-    t0 = time.perf_counter()
-    for k, (arr, P, b, tol) in enumerate(reqs):
-        now = time.perf_counter() - t0
-        if now < arr:
-            time.sleep(arr - now)
-        with pkg.Solver(P) as one:
-            one.solve(b, method="spcg", sigma=sigmas[k], tol=tol, maxit=100000)
-        lat1[k] = time.perf_counter() - t0 - arr
-    out["one_at_a_time_fp64"] = summary(lat1, time.perf_counter() - t0)
+    with ClockSampler(gpu) as clk:
+        t0 = time.perf_counter()
+        for k, (arr, P, b, tol) in enumerate(reqs):
+            now = time.perf_counter() - t0
+            if now < arr:
+                time.sleep(arr - now)
+            with pkg.Solver(P) as one:
+                one.solve(b, method="spcg", sigma=sigmas[k], tol=tol, maxit=100000)
+            lat1[k] = time.perf_counter() - t0 - arr
+        span1 = time.perf_counter() - t0
+    out["one_at_a_time_fp64"] = summary(lat1, span1)
+    out["one_at_a_time_fp64"]["clocks"] = clk.summary()
     base = out["one_at_a_time_fp64"]
     for form in forms:
         f = out[f"served_{form}"]
@@ -688,15 +693,16 @@ def run_ours(args):
     if not args.no_serving and world == 1:   # side measurements: single-GPU runs only
         # the serving workload's full size range, on a bounded number of requests
         serving_1e8 = serving_measure(pkg, args.serving_requests, args.serving_rate, tol=1e-8,
-                                      n_max_exp=args.serving_n_max_exp)
-        serving = serving_measure(pkg, args.serving_requests, args.serving_rate, n_max_exp=args.serving_n_max_exp)
+                                      n_max_exp=args.serving_n_max_exp, gpu=local)
+        serving = serving_measure(pkg, args.serving_requests, args.serving_rate, n_max_exp=args.serving_n_max_exp,
+                                  gpu=local)
         # many small requests: n up to 1e5, where the cluster lanes carry everything
         if args.serving_small_requests > 0:
             small = ("fp64", "mixed", "mixed_jacobi")
             serving_small_1e8 = serving_measure(pkg, args.serving_small_requests, args.serving_rate, tol=1e-8,
-                                                n_max_exp=5.0, forms=small)
+                                                n_max_exp=5.0, forms=small, gpu=local)
             serving_small = serving_measure(pkg, args.serving_small_requests, args.serving_rate, n_max_exp=5.0,
-                                            forms=small)
+                                            forms=small, gpu=local)
 
     # the same workload as CSR (int32 indices): config's second form, one timed step
     csr = None
