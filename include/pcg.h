@@ -301,14 +301,15 @@ void pcg_batch_destroy(pcg_batch *batch);
  * two such kernels side by side on a fixed split of the GPU: requests with
  * n < 32,768 go to one with many clusters of 2 blocks, larger requests to one with
  * 16 clusters of 8 blocks (a large request on a small cluster would set the tail
- * latency).  Requests with n >= 524,288 are solved one at a time on the whole GPU by
- * pcg_create/pcg_solve from a host thread of the server, while both kernels pause
- * (they finish what they hold, exit, and are relaunched afterwards); their device
- * memory is allocated outside the arena.  A second host thread creates their solver
- * contexts (device memory, the operator's upload) in submission order, up to two ahead
- * of the one being solved, so that these uploads overlap other work.  Smaller requests
- * go first: a whole-GPU solve starts once the clusters have taken every smaller request
- * already published, or after 100 ms, whichever comes first.  Host data of an admitted request is packed
+ * latency).  Requests with n >= 524,288 are solved on the whole GPU by
+ * pcg_create/pcg_solve from host threads of the server (two such solves may run at the
+ * same time), while both kernels pause (they finish what they hold, exit, and are
+ * relaunched afterwards); their device memory is allocated outside the arena.  Another
+ * host thread creates their solver contexts (device memory, the operator's upload) in
+ * submission order, at most three at a time, so that these uploads overlap other work.
+ * Smaller requests go first: a whole-GPU solve starts once the clusters have taken every
+ * smaller request already published, or after 100 ms, whichever comes first.  Host data
+ * of an admitted request is packed
  * into a pinned staging ring and copied without blocking; a request is published to
  * its kernel when its copies are done.  A request's arithmetic is fixed by its own
  * cluster (or by the single-system solver), so its result does not depend on what

@@ -134,7 +134,8 @@ constexpr long long kDeviceN = 1LL << 19;
 // that no cluster has claimed yet, but at most this long (so that a steady stream of small
 // requests cannot hold it back).
 constexpr auto kDeviceDefer = std::chrono::milliseconds(100);
-constexpr int kPrepAhead = 2;   // device-lane contexts created ahead of their solve
+constexpr int kDeviceSolvers = 2;   // whole-GPU solves that may run at the same time
+constexpr int kPrepAhead = 3;       // device-lane contexts created and not yet destroyed
 
 struct Lane {
   int csize = 2, clusters = 0;
@@ -169,12 +170,13 @@ struct pcg_server {
   // device lane: `prep` creates the requests' solver contexts (validation, device memory,
   // the operator's upload) in order, at most kPrepAhead ahead of `worker`, which solves
   // them; so the uploads of the next requests overlap the current solve
-  std::thread worker, prep;
+  std::thread worker[kDeviceSolvers], prep;
   std::condition_variable cv, prep_cv;
   std::deque<Request*> prep_queue;              // submitted, context not yet created
   std::deque<Request*> device_queue;            // context created (or failed), not yet solved
   int prepared = 0;                             // contexts created and not yet destroyed
-  bool quit = false, device_busy = false;
+  bool quit = false;
+  int device_active = 0;                        // whole-GPU solves running (the lanes stay down)
   pcg_status worker_error = PCG_OK;
   uint64_t next_ticket = 1;
   std::deque<Request*> waiting;                 // not yet admitted
@@ -505,7 +507,7 @@ pcg_status pump(pcg_server* S) {
       publish(S, R);
     }
   }
-  if (S->device_busy) return PCG_OK;   // the lanes stay down while the device lane runs
+  if (S->device_active > 0) return PCG_OK;   // the lanes stay down while a whole-GPU solve runs
   for (Lane& L : S->lane) {
     cuda::atomic_ref<unsigned, cuda::thread_scope_system> live(L.sh->live);
     cuda::atomic_ref<unsigned, cuda::thread_scope_system> claimed(L.sh->claimed);
@@ -566,11 +568,14 @@ void prep_worker(pcg_server* S) {
   }
 }
 
-// The device lane's solving thread: for each prepared request, lets the lanes take the
-// smaller requests already published (bounded by kDeviceDefer), drains the lanes (their
-// clusters finish what they hold and exit; every wait of theirs is bounded), solves the
-// request with the single-system solver on the whole GPU, then lets pump() relaunch the
-// lanes.
+// The device lane's solving threads (kDeviceSolvers of them): each takes the next prepared
+// request and solves it with the single-system solver on the whole GPU, beside the other
+// thread's solve (two mid-size solves together use the GPU better than one after the
+// other).  The lanes stay down while any such solve runs.  Smaller requests first: when
+// the lanes hold published work that no cluster has claimed, a thread waits until no
+// whole-GPU solve runs, lets pump() relaunch the lanes and gives them up to kDeviceDefer to
+// claim it; then it stops the lanes (their clusters finish what they hold and exit; every
+// wait of theirs is bounded).
 void device_worker(pcg_server* S) {
   cudaSetDevice(S->device);
   std::unique_lock<std::mutex> lk(S->mu);
@@ -580,20 +585,27 @@ void device_worker(pcg_server* S) {
     Request* R = S->device_queue.front();
     S->device_queue.pop_front();
     pcg_status st = R->prep_status;
-    if (st == PCG_OK) {
-      const auto defer_end = std::chrono::steady_clock::now() + kDeviceDefer;
-      while (!S->quit && lanes_pending(S) && std::chrono::steady_clock::now() < defer_end) {
-        const pcg_status s = pump(S);   // publishes finished copies, (re)launches the lanes
-        if (s != PCG_OK) {
-          S->worker_error = s;
-          break;
+    const bool solve = st == PCG_OK;
+    if (solve) {
+      const pcg_status ps = pump(S);    // publishes requests whose copies have completed
+      if (ps != PCG_OK) S->worker_error = ps;
+      if (lanes_pending(S)) {
+        S->cv.wait(lk, [&] { return S->quit || S->device_active == 0; });
+        const auto defer_end = std::chrono::steady_clock::now() + kDeviceDefer;
+        while (!S->quit && S->device_active == 0 && lanes_pending(S) &&
+               std::chrono::steady_clock::now() < defer_end) {
+          const pcg_status s = pump(S);   // publishes finished copies, (re)launches the lanes
+          if (s != PCG_OK) {
+            S->worker_error = s;
+            break;
+          }
+          lk.unlock();
+          std::this_thread::sleep_for(std::chrono::microseconds(200));
+          lk.lock();
         }
-        lk.unlock();
-        std::this_thread::sleep_for(std::chrono::microseconds(200));
-        lk.lock();
       }
-      if (S->quit) return;            // pcg_server_destroy frees the prepared context
-      S->device_busy = true;
+      if (S->quit) return;              // pcg_server_destroy frees the prepared context
+      ++S->device_active;
       for (Lane& L : S->lane) {
         cuda::atomic_ref<unsigned, cuda::thread_scope_system> stop(L.sh->stop);
         stop.store(1u, cuda::memory_order_release);
@@ -609,22 +621,23 @@ void device_worker(pcg_server* S) {
       R->device_res.beta_hist = R->beta_log.data();
       st = pcg_solve(R->ctx, R->b.data(), nullptr, R->method, R->method == PCG_SPCG ? R->sigma : 0.0, R->tol,
                      R->maxit, R->precision, R->x_host.data(), &R->device_res);
-    } else {
-      lk.unlock();
+      // freeing device memory waits for the whole device, so the context goes while the
+      // lanes are down (it may wait briefly for the other thread's queued launches)
+      pcg_destroy(R->ctx);
+      R->ctx = nullptr;
+      lk.lock();
+      --S->device_active;
     }
-    // freeing device memory waits for the whole device, so the context goes while the
-    // lanes are down
-    pcg_destroy(R->ctx);
-    R->ctx = nullptr;
-    lk.lock();
     R->device_status = st;
     R->device_done = true;
     release_arrays(R);
     --S->prepared;
     S->prep_cv.notify_all();
-    S->device_busy = false;
-    const pcg_status s = pump(S);     // the lanes come back for published work
-    if (s != PCG_OK) S->worker_error = s;
+    if (S->device_active == 0) {
+      const pcg_status s = pump(S);   // the lanes come back for published work
+      if (s != PCG_OK) S->worker_error = s;
+    }
+    S->cv.notify_all();               // a thread waiting for the other's solve to end
   }
 }
 
@@ -696,7 +709,7 @@ pcg_status pcg_server_create(size_t hbm_budget_bytes, int32_t max_slots, pcg_ser
     if (cudaStreamCreateWithFlags(&L.kstream, cudaStreamNonBlocking) != cudaSuccess) return bail(PCG_ECUDA);
   }
   try {
-    S->worker = std::thread(device_worker, S);
+    for (std::thread& w : S->worker) w = std::thread(device_worker, S);
     S->prep = std::thread(prep_worker, S);
   } catch (...) {
     return bail(PCG_ENOMEM);
@@ -713,7 +726,8 @@ void pcg_server_destroy(pcg_server* S) {
   }
   S->cv.notify_all();
   S->prep_cv.notify_all();
-  if (S->worker.joinable()) S->worker.join();
+  for (std::thread& w : S->worker)
+    if (w.joinable()) w.join();
   if (S->prep.joinable()) S->prep.join();
   for (Lane& L : S->lane) {
     if (L.sh) {

@@ -256,27 +256,57 @@ def test_device_lane_requests(B):
 def test_smaller_requests_go_first(B):
     """Small requests that arrive while a whole-GPU request runs are taken by the cluster
     lanes before the next whole-GPU request starts: they finish before it."""
-    d1 = S.laplacian_2d(1024)                                    # n = 1,048,576: long enough to
-    d2 = S.laplacian_3d(81)                                      # hold the small submissions
+    d1 = S.laplacian_2d(1448)                                    # n = 2,096,704: runs long enough
+    d2 = S.laplacian_3d(81)                                      # to hold the small submissions
     small = [S.laplacian_2d(30, 20), random_sdd(1500, 11), S.laplacian_3d(12), S.laplacian_2d(64),
              random_sdd(800, 12), S.laplacian_3d(20, 18, 9)]
-    reqs = [(d1, S.normal(80, d1.n), 1e-10), (d2, S.normal(81, d2.n), 1e-8)]
+    reqs = [(d1, S.normal(80, d1.n), 1e-10)]
     reqs += [(P, S.normal(82 + i, P.n), 1e-8) for i, P in enumerate(small)]
+    reqs += [(d2, S.normal(81, d2.n), 1e-8)]
     with B.Server(256 << 20, 16) as srv:
         t0 = time.time()
-        pending = {srv.submit(P, b, tol=tol): k for k, (P, b, tol) in enumerate(reqs)}
-        fin, res = {}, {}
-        while pending:
-            assert time.time() - t0 < 120.0, "requests did not finish"
+        pending, fin, res = {}, {}, {}
+
+        def poll_all():
             for t in list(pending):
                 r = srv.poll(t)
                 if r is not None:
                     k = pending.pop(t)
                     fin[k], res[k] = time.time(), r
+
+        for k, (P, b, tol) in enumerate(reqs):
+            if k == 1:                                           # d1 taken by a solving thread
+                while srv.stats()[0] > 0:
+                    assert time.time() - t0 < 60.0
+                    time.sleep(0.001)
+                time.sleep(0.01)
+            if k == len(reqs) - 1:
+                time.sleep(0.05)                                 # the small requests' copies land
+                poll_all()
+            pending[srv.submit(P, b, tol=tol)] = k
+        while pending:
+            assert time.time() - t0 < 120.0, "requests did not finish"
+            poll_all()
             time.sleep(0.0005)
     for k, (P, b, tol) in enumerate(reqs):
         assert res[k][0] == B.PCG_OK, (k, res[k][0])
         tr = np.linalg.norm(b - oracle.apply(P, res[k][1])) / np.linalg.norm(b)
         assert tr <= 3 * tol, (k, tr)
-    assert fin[0] < fin[1]                                        # whole-GPU requests in order
-    assert max(fin[k] for k in range(2, len(reqs))) < fin[1]      # the small ones before the second
+    last = len(reqs) - 1
+    assert fin[0] < fin[last]                                     # the second whole-GPU request waits
+    assert max(fin[k] for k in range(1, last)) < fin[last]        # the small ones before it
+
+
+def test_two_whole_gpu_requests_at_once(B):
+    """Two whole-GPU requests submitted together are solved side by side; both results
+    solve their systems."""
+    reqs = [(S.laplacian_2d(1100), S.normal(90, 1100 * 1100), 1e-9, B.PCG_FP64),
+            (S.laplacian_3d(84), S.normal(91, 84 ** 3), 1e-9, B.PCG_MIXED_IR),
+            (S.varcoef_2d(760, 700, lo_exp=-1.0, hi_exp=1.0, seed=5), S.normal(92, 760 * 700), 1e-8, B.PCG_FP64)]
+    with B.Server(256 << 20, 8) as srv:
+        tickets = [srv.submit(P, b, tol=tol, precision=pr) for P, b, tol, pr in reqs]
+        out = [wait(srv, t, timeout=120.0) for t in tickets]
+    for (P, b, tol, pr), r in zip(reqs, out):
+        assert r[0] == B.PCG_OK, r[0]
+        tr = np.linalg.norm(b - oracle.apply(P, r[1])) / np.linalg.norm(b)
+        assert tr <= 3 * tol and abs(tr - r[3]) <= 1e-3 * tr + 1e-15, (tr, r[3])
