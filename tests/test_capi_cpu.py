@@ -108,3 +108,43 @@ def test_argument_errors_of_the_extensions_without_gpu(libpath):
     assert L.pcg_server_create(1024, 4, ctypes.byref(out)) == B.PCG_EINVAL       # budget below 1 MiB
     assert L.pcg_convert_check(None, None, None, None, -1) == B.PCG_EINVAL
     assert L.pcg_convert_check(None, None, None, None, 0) == B.PCG_OK
+
+
+def test_csr_validation_over_several_chunks_without_gpu(libpath):
+    """pcg_create checks a CSR matrix's row ranges and column indices in chunks of rows on
+    several host threads: a valid matrix of many chunks passes to the device step (which
+    fails without a GPU, as PCG_ECUDA or PCG_ENOMEM), and one bad entry anywhere, or a
+    row range that runs backwards or past nnz, is PCG_EINVAL before any device call."""
+    import numpy as np
+    from paper_1706_05988_gb300 import pcg as B
+    L = B.lib()
+    n = 300_001                                           # five chunks of 65,536 rows, ragged tail
+    deg = 3
+    row_ptr = np.arange(0, deg * (n + 1), deg, dtype=np.int32)
+    col = ((np.arange(n, dtype=np.int64)[:, None] + np.array([-1, 0, 1])) % n).astype(np.int32).ravel()
+    val = np.tile(np.array([-1.0, 2.5, -1.0]), n)
+
+    def create(rp, c, v):
+        m = B.pcg_matrix()
+        m.layout = B.PCG_CSR32
+        m.n, m.nnz = n, int(rp[-1])
+        m.row_ptr, m.col, m.val = rp.ctypes.data, c.ctypes.data, v.ctypes.data
+        out = ctypes.c_void_p()
+        s = L.pcg_create(ctypes.byref(m), 0, ctypes.byref(out))
+        if s == B.PCG_OK:                                  # (run where a GPU is present)
+            L.pcg_destroy(out)
+        return s
+
+    assert create(row_ptr, col, val) in (B.PCG_OK, B.PCG_ECUDA, B.PCG_ENOMEM)
+    for k in (0, 3 * 65_536 + 7, col.size - 1):           # a bad column in the first, a middle, the last chunk
+        bad = col.copy()
+        bad[k] = n
+        assert create(row_ptr, bad, val) == B.PCG_EINVAL
+        bad[k] = -1
+        assert create(row_ptr, bad, val) == B.PCG_EINVAL
+    rp = row_ptr.copy()
+    rp[200_000] = rp[200_001] + 1                          # a row range that runs backwards
+    assert create(rp, col, val) == B.PCG_EINVAL
+    rp = row_ptr.copy()
+    rp[100_000] = int(row_ptr[-1]) + 5                     # past nnz (and backwards after it)
+    assert create(rp, col, val) == B.PCG_EINVAL
