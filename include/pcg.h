@@ -300,7 +300,7 @@ void pcg_batch_destroy(pcg_batch *batch);
  * each request is solved by one cluster exactly as in pcg_batch (x_0 = 0).  There are
  * two such kernels side by side on a fixed split of the GPU: requests with
  * n < 32,768 go to one with many clusters of 2 blocks, larger requests to one with
- * 16 clusters of 8 blocks (a large request on a small cluster would set the tail
+ * 8 clusters of 16 blocks (a large request on a small cluster would set the tail
  * latency).  Requests with n >= 524,288 are solved on the whole GPU by
  * pcg_create/pcg_solve from host threads of the server (two such solves may run at the
  * same time), while both kernels pause (they finish what they hold, exit, and are
