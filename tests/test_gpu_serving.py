@@ -310,3 +310,22 @@ def test_two_whole_gpu_requests_at_once(B):
         assert r[0] == B.PCG_OK, r[0]
         tr = np.linalg.norm(b - oracle.apply(P, r[1])) / np.linalg.norm(b)
         assert tr <= 3 * tol and abs(tr - r[3]) <= 1e-3 * tr + 1e-15, (tr, r[3])
+
+
+def test_destroy_with_whole_gpu_requests_in_flight(B):
+    """Destroying a server while whole-GPU requests are being prepared, solved or wait,
+    and small ones are queued, returns (their contexts are freed) and leaves the GPU
+    usable: a new server then solves a request."""
+    big = [S.laplacian_2d(1200), S.laplacian_3d(90), S.laplacian_2d(800, 700), random_sdd(600_000, 13)]
+    small = [S.laplacian_2d(40, 30), random_sdd(2000, 14)]
+    t0 = time.time()
+    with B.Server(256 << 20, 8) as srv:
+        for i, P in enumerate(big + small):
+            srv.submit(P, S.normal(100 + i, P.n), tol=1e-10)
+        time.sleep(0.05)                                  # some are running, some prepared or queued
+    assert time.time() - t0 < 60.0
+    P = S.laplacian_3d(20)
+    b = S.normal(110, P.n)
+    with B.Server(64 << 20, 2) as srv:
+        st, x, it, tr = wait(srv, srv.submit(P, b, tol=1e-9))
+    assert st == B.PCG_OK and np.linalg.norm(b - oracle.apply(P, x)) <= 2e-9 * np.linalg.norm(b)
