@@ -320,10 +320,23 @@ def request_policy(P, form: str):
 
 def serve_stream(pkg, reqs, form: str):
     """Runs the request stream through one server with the form's per-request policy;
-    returns (latencies, span)."""
+    returns (latencies, span).  The client's garbage collector is paused inside the timed
+    loop (as in the one-at-a-time arm): a collection there would stop the submissions and
+    polls that drive the server."""
+    import gc
     import numpy as np
     nreq = len(reqs)
     lat = np.zeros(nreq)
+    gc.collect()
+    gc.disable()
+    try:
+        return _serve_stream(pkg, reqs, form, lat)
+    finally:
+        gc.enable()
+
+
+def _serve_stream(pkg, reqs, form, lat):
+    nreq = len(reqs)
     with pkg.Server(8 << 30, 512) as srv:
         pending = {}
         t0 = time.perf_counter()
@@ -376,16 +389,22 @@ def serving_measure(pkg, nreq: int, rate: float, tol=None, n_max_exp: float = 5.
     # (the shifts are computed before the clock starts)
     sigmas = [request_sigma(P) for _, P, _, _ in reqs]
     lat1 = np.zeros(nreq)
-    with ClockSampler(gpu) as clk:
-        t0 = time.perf_counter()
-        for k, (arr, P, b, tol) in enumerate(reqs):
-            now = time.perf_counter() - t0
-            if now < arr:
-                time.sleep(arr - now)
-            with pkg.Solver(P) as one:
-                one.solve(b, method="spcg", sigma=sigmas[k], tol=tol, maxit=100000)
-            lat1[k] = time.perf_counter() - t0 - arr
-        span1 = time.perf_counter() - t0
+    import gc
+    gc.collect()
+    gc.disable()
+    try:
+        with ClockSampler(gpu) as clk:
+            t0 = time.perf_counter()
+            for k, (arr, P, b, tol) in enumerate(reqs):
+                now = time.perf_counter() - t0
+                if now < arr:
+                    time.sleep(arr - now)
+                with pkg.Solver(P) as one:
+                    one.solve(b, method="spcg", sigma=sigmas[k], tol=tol, maxit=100000)
+                lat1[k] = time.perf_counter() - t0 - arr
+            span1 = time.perf_counter() - t0
+    finally:
+        gc.enable()
     out["one_at_a_time_fp64"] = summary(lat1, span1)
     out["one_at_a_time_fp64"]["clocks"] = clk.summary()
     base = out["one_at_a_time_fp64"]
