@@ -10,6 +10,11 @@
 // next free cluster: requests overlap on the device.  With no published work for
 // kIdleNs the kernel's clusters exit; the host relaunches the kernel when work arrives.
 // Every wait of the kernel is bounded by %globaltimer.
+//
+// Requests of n >= kDeviceN take the whole GPU instead (the device lane): a preparing host
+// thread creates their single-system solver contexts ahead, and two solving threads run
+// pcg_solve on them, up to two at a time, while the cluster kernels are stopped.  Host
+// passes over a request's arrays run on several threads (pcg_host_parallel.h).
 #include <cuda/atomic>
 #include <cuda_runtime.h>
 #include <math.h>
